@@ -1,0 +1,181 @@
+/*
+ * fglt.h — C ABI of the GB300 (sm_103a) Fast Graphlet Transform library.
+ *
+ * The graphlet transform (Floros, Pitsianis, Sun, "Fast Graphlet Transform of
+ * Sparse Graphs", Sec. 2, eq. graphlet-transform) maps a simple undirected
+ * graph G = (V, E) to one frequency vector per vertex over the dictionary
+ * Sigma16 of Fig. 1 (all connected graphlets on up to 4 nodes, sigma_0 ..
+ * sigma_15). This library computes both
+ *   - the raw frequencies f^(v) = [d^_0(v) .. d^_15(v)] of Table I (subgraphs,
+ *     induced or not, Sec. 4), and
+ *   - the net frequencies f(v) = U16^{-1} f^(v) of Table II (Sec. 5), which for
+ *     Sigma16 are the induced-subgraph orbit counts.
+ * All counts are exact integers (int64).
+ *
+ * Conventions shared by every entry point:
+ *  - Graph input is a symmetric CSR: row pointers (int32 or int64, n+1 entries,
+ *    rowptr[0] = 0) and int32 column indices (rowptr[n] entries). Vertex ids are
+ *    0-based (the paper numbers vertices from 1). The graph must be simple: no
+ *    self-loops, no repeated neighbour, and j in N(i) iff i in N(j) (Sec. 1,
+ *    notation: "simple, undirected ... symmetric adjacency matrix"). Rows need
+ *    not be sorted. With fglt_options.validate = 1 these preconditions are
+ *    checked on the device and a violation returns FGLT_ERR_INVALID_GRAPH;
+ *    otherwise a violating input gives unspecified counts (never a fault).
+ *  - Output is row-major int64 [n][16]: row v, column k = frequency of sigma_k
+ *    at vertex v (the orientation of the tables of Fig. 2). Either output
+ *    pointer may be NULL to skip it (not both).
+ *  - Ownership: the caller owns every buffer it passes; the library never frees
+ *    them and keeps no pointer to them after the call returns. The handle owns
+ *    its device workspace, its stream and its serving slots.
+ *  - Errors are returned as fglt_status, never thrown, printed or exited.
+ *    A call that fails leaves the outputs unspecified.
+ *  - Threading: a handle may be used by one host thread at a time, except the
+ *    fglt_stream_* entries, which are safe to call from any thread.
+ */
+#ifndef FGLT_H
+#define FGLT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FGLT_NUM_GRAPHLETS 16
+
+typedef int fglt_status;
+
+enum {
+    FGLT_OK = 0,
+    FGLT_ERR_INVALID_ARG = 1,   /* null pointer, negative size, bad flag */
+    FGLT_ERR_INVALID_GRAPH = 2, /* validate = 1 and the CSR is not a simple symmetric graph */
+    FGLT_ERR_OOM = 3,           /* device or host allocation failed */
+    FGLT_ERR_OVERFLOW = 4,      /* max degree > 2,097,151: binom(d, 3) may leave int64 */
+    FGLT_ERR_CUDA = 5,          /* a CUDA runtime call failed (see fglt_last_cuda_error) */
+    FGLT_ERR_TIMEOUT = 6,       /* a bounded wait ran out (serving poll, device spin limit) */
+    FGLT_ERR_PENDING = 7,       /* serving: the request has not finished yet */
+    FGLT_ERR_NOT_FOUND = 8,     /* serving: unknown or already collected request id */
+    FGLT_ERR_INTERNAL = 9,      /* a device-side consistency check failed */
+    FGLT_ERR_UNSUPPORTED = 10,  /* input outside the sizes this build supports */
+    FGLT_ERR_BUSY = 11,         /* serving: queue full or budget cannot ever fit the request */
+    FGLT_ERR_CANCELLED = 12     /* serving: the request was cancelled */
+};
+
+typedef struct fglt_handle* fglt_t;
+
+typedef struct {
+    /* 1: check the CSR preconditions on the device before the transform. */
+    int validate;
+    /* Serving: bytes of device memory the resident request slots may use.
+     * 0 selects half of the device memory free at fglt_create. */
+    size_t serve_memory_budget;
+    /* Serving: most requests packed into one launch (0 selects 256). */
+    int serve_max_batch;
+    /* Serving: most requests queued but not yet admitted (0 selects 65536). */
+    int serve_max_queue;
+    /* 1: record CUDA events around every stage of each transform so that
+     * fglt_stage_times can report per-stage device time. */
+    int profile_stages;
+} fglt_options;
+
+/* Fills *opt with the defaults (all fields 0 = automatic). */
+fglt_status fglt_options_default(fglt_options* opt);
+
+/* Creates a handle bound to CUDA device `device`. opt may be NULL (defaults).
+ * Allocates the handle's stream; device workspace grows on demand. */
+fglt_status fglt_create(fglt_t* handle, const fglt_options* opt, int device);
+
+/* Destroys the handle: waits for its work, frees its workspace and stream.
+ * Pending serving requests are cancelled. NULL is accepted. */
+fglt_status fglt_destroy(fglt_t handle);
+
+/* Static description of a status code. */
+const char* fglt_status_string(fglt_status status);
+
+/* Text of the last CUDA error seen by this handle ("" if none). */
+const char* fglt_last_cuda_error(fglt_t handle);
+
+/*
+ * Single-graph transform, device buffers.
+ *   rowptr          device pointer, n+1 entries, int64 if rowptr_is_64bit else int32
+ *   colidx          device pointer, rowptr[n] int32 entries (NULL allowed if no edges)
+ *   n               number of vertices (0 allowed: nothing is written)
+ *   out_raw/out_net device pointers to n*16 int64, or NULL to skip one
+ *   stream          cudaStream_t to order the work on, or NULL for the handle's stream
+ * Computes Table I (raw) and Table II's inverse (net) for every vertex:
+ * degrees and the SpMV chains of Sec. 3-4 (p1, p2, p3, d^7, d^9, d^10),
+ * per-edge triangle counts C3 = A o A^2 (Lemma 2), the 4-cycle term c4 (Lemma
+ * on c4), the diamond terms D4,c and D4,3 and the 4-clique term T (Sec. 4.3).
+ * Returns after the work has completed on `stream` (it synchronises it).
+ */
+fglt_status fglt_transform(fglt_t handle, const void* rowptr, int rowptr_is_64bit,
+                           const int32_t* colidx, int64_t n,
+                           int64_t* out_raw, int64_t* out_net, void* stream);
+
+/*
+ * Single-graph transform, host buffers: copies the CSR to the device, runs
+ * fglt_transform on the handle's stream and copies the outputs back. Same
+ * arguments as fglt_transform, with every pointer a host pointer.
+ */
+fglt_status fglt_transform_host(fglt_t handle, const void* rowptr, int rowptr_is_64bit,
+                                const int32_t* colidx, int64_t n,
+                                int64_t* out_raw, int64_t* out_net);
+
+/*
+ * Batched transform of many independent graphs packed block-diagonally.
+ *   rowptr, colidx    device CSR of the union (global vertex ids; no edge may
+ *                     join two graphs)
+ *   graph_offsets     HOST array, num_graphs+1 entries: graph g owns vertices
+ *                     [graph_offsets[g], graph_offsets[g+1]); graph_offsets[0] = 0
+ *   out_raw, out_net  device n*16 int64 (n = graph_offsets[num_graphs])
+ * The transform of a disjoint union is the concatenation of the transforms
+ * (every graphlet is connected, Fig. 1), so the whole batch runs as one
+ * sequence of launches captured once as a CUDA graph and replayed for batches
+ * of the same shape.
+ */
+fglt_status fglt_transform_batched(fglt_t handle, const void* rowptr, int rowptr_is_64bit,
+                                   const int32_t* colidx, const int64_t* graph_offsets,
+                                   int64_t num_graphs, int64_t* out_raw, int64_t* out_net,
+                                   void* stream);
+
+/* Per-stage device times (ms) of the last transform on this handle; requires
+ * fglt_options.profile_stages = 1. names[i] points to static strings.
+ * *count receives the number of stages (at most max_stages are written). */
+fglt_status fglt_stage_times(fglt_t handle, const char** names, float* ms,
+                             int max_stages, int* count);
+
+/* ---------------------------------------------------------------------------
+ * Serving: requests arrive one by one from host memory; the library admits
+ * them into resident device slots within fglt_options.serve_memory_budget,
+ * packs admitted requests into shared launches (continuous batching) and
+ * copies the results back to the caller's host buffers.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t n;              /* vertices */
+    const int64_t* rowptr;  /* host, n+1 entries */
+    const int32_t* colidx;  /* host, rowptr[n] entries */
+    int64_t* out_raw;       /* host, n*16, or NULL */
+    int64_t* out_net;       /* host, n*16, or NULL */
+} fglt_graph_host;
+
+/* Queues a request. The CSR is copied into a staging buffer before the call
+ * returns; the output buffers must stay valid until the request is collected
+ * by fglt_stream_poll or fglt_stream_cancel. */
+fglt_status fglt_stream_submit(fglt_t handle, const fglt_graph_host* graph, uint64_t* request_id);
+
+/* Waits up to timeout_ms (0 = do not wait, -1 = forever) for a request.
+ * FGLT_OK: results are in the request's output buffers and the id is retired.
+ * FGLT_ERR_PENDING (timeout 0) / FGLT_ERR_TIMEOUT: not finished yet.
+ * latency_us (nullable) receives submit-to-results-on-host time. */
+fglt_status fglt_stream_poll(fglt_t handle, uint64_t request_id, int timeout_ms, double* latency_us);
+
+/* Cancels a request that has not been admitted yet (FGLT_ERR_BUSY if it is
+ * already on the device, in which case poll it as usual). */
+fglt_status fglt_stream_cancel(fglt_t handle, uint64_t request_id);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGLT_H */
