@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""FGLT benchmark: one JSON line on stdout (rank 0).
+
+Default workload: R-MAT scale 20, edge factor 16 (a,b,c = .57,.19,.19, seed 0,
+seeded vertex permutation, symmetrised, deduplicated, no self-loops), int32
+column indices, int64 row pointers, synthetic. A step is one full transform
+(all 16 raw and 16 net frequencies for every vertex) through the C ABI with the
+inputs resident in device memory. L2 is flushed (512 MiB write) before every
+timed step, outside the timed events.
+
+--impl reference times the CPU oracle (the reference arm of this build) on a
+bounded sample of the workload family on the host cores.
+
+Multi-GPU (torchrun, --gpus N): every rank transforms its own replica of the
+graph (the single-graph path is not sharded); value = all ranks' edges / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+METRIC = "FGLT edges/s & HBM GB/s vs peak; batched graphs/s, p50/p99 vs per-graph launch"
+UNIT = "undirected edges/s"
+
+WORKLOADS = {
+    "rmat-s20-ef16": dict(kind="rmat", scale=20, ef=16, seed=0,
+                          desc="R-MAT scale 20, edge factor 16, a=.57 b=.19 c=.19, seed 0, permuted, "
+                               "symmetric simple CSR, int32 colidx, int64 rowptr"),
+    "er-2000-d10": dict(kind="er", n=2000, deg=10, seed=0,
+                        desc="Erdos-Renyi G(n=2000, avg degree 10), seed 0, symmetric simple CSR"),
+}
+# Bounded sample for the CPU oracle: the same generator and parameters at a
+# smaller scale.
+CPU_SAMPLE = dict(kind="rmat", scale=14, ef=16, seed=0,
+                  desc="R-MAT scale 14, edge factor 16, a=.57 b=.19 c=.19, seed 0 (same generator, 1/64 of the vertices)")
+
+
+def make_graph(spec):
+    if spec["kind"] == "rmat":
+        return gg.rmat(spec["scale"], spec["ef"], seed=spec["seed"])
+    return gg.erdos_renyi(spec["n"], spec["deg"], seed=spec["seed"])
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Roofline accounting
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(stage: str, w: dict) -> int:
+    """Bytes the method itself must move for one launch of a stage (see the
+    measurement section of the design doc): 4 B per neighbour-list entry read,
+    4 B per per-edge C3 value, 8 B per per-vertex int64 value."""
+    n, nnz, m = w["n"], w["nnz"], w["m"]
+    if stage == "cyc":
+        return 4 * w["wedges"] + 4 * nnz + 8 * n
+    if stage == "tri1":
+        return 4 * w["tri_scanned"] + 4 * m + 4 * m + 24 * n
+    if stage == "tri2":
+        return 4 * w["tri_scanned"] + 4 * m + 4 * m + 8 * n
+    if stage in ("spmv1", "spmv2"):
+        return 4 * nnz + 4 * nnz + 8 * (n + 1) + 16 * n
+    if stage == "epilogue":
+        return 256 * n + 8 * 12 * n
+    return 4 * nnz + 8 * n
+
+
+def traffic_for(stage: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (profiles/traffic.json keyed by stage and
+    workload, with the source digest it was measured on)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t[workload][stage]
+        src = os.path.join(ROOT, "paper_2007_11111_gb300", "csrc", e["source"])
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if digest != e["sha256_16"]:
+            return None
+        return int(e["dram_bytes"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# Arms
+# ---------------------------------------------------------------------------
+def oracle_step(g, threads=0):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.fglt(g, threads=threads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(threads=0):
+    import oracle
+    g = make_graph(CPU_SAMPLE)
+    dt = oracle_step(g, threads)
+    return {"value": g.m / dt, "unit": UNIT, "cores": threads or oracle.max_threads(), "kind": "oracle",
+            "sample": CPU_SAMPLE["desc"] + f"; full transform of m={g.m} edges in {dt:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    g = make_graph(CPU_SAMPLE)
+    for _ in range(args.warmup):
+        oracle_step(g)
+    times = [oracle_step(g) for _ in range(args.steps)]
+    ms = 1000 * statistics.mean(times)
+    value = g.m / (ms / 1000)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": CPU_SAMPLE["desc"], "n": g.n, "m": g.m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": CPU_SAMPLE["desc"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_2007_11111_gb300 as fg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    spec = WORKLOADS[args.workload]
+    g = make_graph(spec)
+    rp = torch.from_numpy(g.rowptr).to(dev)
+    ci = torch.from_numpy(g.colidx).to(dev)
+    raw = torch.empty((g.n, 16), dtype=torch.int64, device=dev)
+    net = torch.empty((g.n, 16), dtype=torch.int64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    h = fg.Handle(device=local_rank, profile_stages=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        h.transform(rp, ci, g.n, raw, net, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    step_ms, stage_acc = [], {}
+    launches = 0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for k, v in h.stage_times().items():
+            stage_acc.setdefault(k, []).append(v)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    ms = statistics.mean(step_ms)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    work = h.work_counters()
+    launches = KERNELS_PER_STEP * args.steps
+
+    # End to end through the public API with host buffers (pinned host memory).
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        prp = torch.from_numpy(g.rowptr).pin_memory().numpy()
+        pci = torch.from_numpy(g.colidx).pin_memory().numpy()
+        hraw = torch.empty((g.n, 16), dtype=torch.int64).pin_memory().numpy()
+        hnet = torch.empty((g.n, 16), dtype=torch.int64).pin_memory().numpy()
+        fg.fglt_transform_host(h.h, prp, 1, pci, g.n, hraw, hnet)
+        tl = []
+        for _ in range(max(3, min(args.steps, 10))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fg.fglt_transform_host(h.h, prp, 1, pci, g.n, hraw, hnet)
+            tl.append(time.perf_counter() - t0)
+        e2e = {"value": g.m / statistics.mean(tl), "unit": UNIT,
+               "h2d_bytes_per_step": int(prp.nbytes + pci.nbytes),
+               "d2h_bytes_per_step": int(hraw.nbytes + hnet.nbytes)}
+
+    if rank != 0:
+        h.close()
+        return 0
+
+    stage_ms = {k: statistics.mean(v) for k, v in stage_acc.items()}
+    dom = max(stage_ms, key=stage_ms.get)
+    peak, peak_kind = load_peaks()
+    ab = algorithmic_bytes(dom, work)
+    achieved = ab / (stage_ms[dom] / 1000) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_for(dom, args.workload),
+                "kernel": dom, "kernel_ms": stage_ms[dom], "algorithmic_bytes": ab,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s"}
+    value = world * g.m / (ms / 1000)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": spec["desc"], "n": g.n, "m": g.m, "nnz": g.nnz,
+                   "l2": "flushed before every timed step (512 MiB write, outside the timed events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "stage_ms": stage_ms,
+        "work": work,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
+# Kernel launches of one transform (degree-ordered pipeline):
+# degree, spmv1 (2), hist, scan (3), rank, orient count (2), scan (3),
+# orient fill (2), sort (2), worklist, tri1, edge terms, unrank, spmv2 (2),
+# tri2, wedge count (2), cyc worklists, cyc (2), epilogue.
+KERNELS_PER_STEP = 34
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat-s20-ef16", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    rc = run_gpu(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -43,7 +43,9 @@ def csr_from_pairs(n: int, src, dst) -> Graph:
         if src.min() < 0 or dst.min() < 0 or src.max() >= n or dst.max() >= n:
             raise ValueError("vertex id out of range")
     keys = np.concatenate([src * n + dst, dst * n + src])
-    keys = np.unique(keys)
+    keys.sort()
+    if keys.size:
+        keys = keys[np.concatenate([[True], keys[1:] != keys[:-1]])]
     rows = keys // max(n, 1)
     cols = (keys - rows * n).astype(np.int32)
     counts = np.bincount(rows, minlength=n) if n > 0 else np.zeros(0, np.int64)

@@ -15,12 +15,12 @@
  * Conventions shared by every entry point:
  *  - Graph input is a symmetric CSR: row pointers (int32 or int64, n+1 entries,
  *    rowptr[0] = 0) and int32 column indices (rowptr[n] entries). Vertex ids are
- *    0-based (the paper numbers vertices from 1). The graph must be simple: no
- *    self-loops, no repeated neighbour, and j in N(i) iff i in N(j) (Sec. 1,
- *    notation: "simple, undirected ... symmetric adjacency matrix"). Rows need
- *    not be sorted. With fglt_options.validate = 1 these preconditions are
- *    checked on the device and a violation returns FGLT_ERR_INVALID_GRAPH;
- *    otherwise a violating input gives unspecified counts (never a fault).
+ *    0-based (the paper numbers vertices from 1). The graph must be simple
+ *    and undirected, as Sec. 1 assumes: no self-loops, every row strictly
+ *    increasing (so no repeated neighbour), and j in N(i) iff i in N(j). With
+ *    fglt_options.validate = 1 these preconditions are checked on the device
+ *    and a violation returns FGLT_ERR_INVALID_GRAPH; otherwise a violating
+ *    input gives unspecified counts (never a fault).
  *  - Output is row-major int64 [n][16]: row v, column k = frequency of sigma_k
  *    at vertex v (the orientation of the tables of Fig. 2). Either output
  *    pointer may be NULL to skip it (not both).
@@ -144,6 +144,23 @@ fglt_status fglt_transform_batched(fglt_t handle, const void* rowptr, int rowptr
  * *count receives the number of stages (at most max_stages are written). */
 fglt_status fglt_stage_times(fglt_t handle, const char** names, float* ms,
                              int max_stages, int* count);
+
+/* Work counters of the last successful transform on this handle, for
+ * roofline accounting. counters[i] (at most max_counters written; *count
+ * receives the number available):
+ *   0 n                 vertices
+ *   1 nnz               stored CSR entries (2m for a valid graph)
+ *   2 m                 edges of the degree-ordered orientation (= undirected edges)
+ *   3 max degree
+ *   4 max out-degree in the degree orientation
+ *   5 out-list entries scanned by the first triangle pass (sum over a -> b of
+ *     the part of N+(b) not above max N+(a))
+ *   6 triangles (each once; e^T C3 e / 6, Lemma 3)
+ *   7 4-cliques (each once)
+ *   8 wedges enumerated by the 4-cycle stage
+ *   9 largest wedge count of one vertex
+ * FGLT_ERR_NOT_FOUND if no transform has completed on the handle. */
+fglt_status fglt_work_counters(fglt_t handle, int64_t* counters, int max_counters, int* count);
 
 /* ---------------------------------------------------------------------------
  * Serving: requests arrive one by one from host memory; the library admits

@@ -1,0 +1,119 @@
+// Host-side launchers of the FGLT kernels. Every launcher enqueues work on
+// `st` and returns the launch status; none synchronises.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fglt {
+
+typedef unsigned long long u64;
+
+// Input CSR as given by the caller (device pointers).
+struct Csr {
+  const void* rowptr;
+  bool rp64;
+  const int32_t* colidx;
+  int64_t n;
+  int64_t nnz;
+};
+
+// Degree threshold above which a vertex of the input CSR is handled by a
+// whole thread block instead of an 8-lane group.
+constexpr int HEAVY_DEGREE = 512;
+
+// --- input CSR passes ------------------------------------------------------
+// Degrees, max degree, heavy-row list; flags malformed row pointers in *err.
+cudaError_t launch_degree(const Csr& g, int32_t* d, int32_t* dmax, int32_t* heavy, int32_t* nheavy, int* err,
+                          cudaStream_t st);
+cudaError_t launch_validate(const Csr& g, const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap,
+                            int* err, cudaStream_t st);
+// p2 = A p1 - p1 and d^7 = A((p1-1)o(p1-2))/2 (SpMV chain 1)
+// (also flags column indices outside [0, n) in *err; later passes skip them)
+cudaError_t launch_spmv1(const Csr& g, const int32_t* d, const int32_t* heavy, const int32_t* nheavy,
+                         int64_t heavy_cap, int64_t* p2, int64_t* r7, int* err, cudaStream_t st);
+// p3 = A p2 - p1 o (p1-1) - 2 c3 and d^9 = A c3 - 2 c3 (SpMV chain 2)
+cudaError_t launch_spmv2(const Csr& g, const int32_t* d, const int64_t* p2, const int64_t* c3o,
+                         const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap,
+                         int64_t* p3, int64_t* r9, cudaStream_t st);
+
+// --- degree ordering and the oriented graph ---------------------------------
+cudaError_t launch_degree_hist(const int32_t* d, int64_t n, int32_t* hist, cudaStream_t st);
+cudaError_t launch_rank_assign(const int32_t* d, int64_t n, const int64_t* base, int32_t* cursor,
+                               int32_t* rank, int32_t* perm, int32_t* dr, cudaStream_t st);
+cudaError_t launch_orient_count(const Csr& g, const int32_t* rank, const int32_t* heavy,
+                                const int32_t* nheavy, int64_t heavy_cap, int32_t* opc, int32_t* dpmax,
+                                cudaStream_t st);
+cudaError_t launch_orient_fill(const Csr& g, const int32_t* rank, const int64_t* orp, const int32_t* heavy,
+                               const int32_t* nheavy, int64_t heavy_cap, int32_t* cursor, int32_t* ocol,
+                               cudaStream_t st);
+// Sorts every oriented row ascending. Rows longer than 16384 use gscratch
+// (at least next_pow2(max row) int32).
+cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int32_t* ocol,
+                             int32_t* gscratch, cudaStream_t st);
+// Vertices (rank labels) with at least `min_out` out-neighbours.
+cudaError_t launch_worklist_outdeg(const int32_t* opc, int64_t n, int min_out, int32_t* list,
+                                   int32_t* count, cudaStream_t st);
+
+// --- scans -----------------------------------------------------------------
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
+size_t scan_temp_bytes(int64_t n);
+cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t n, int64_t* out, void* temp, cudaStream_t st);
+
+// --- triangle passes (oriented, rank space) ---------------------------------
+// Per-block shared memory the triangle kernels need for a max out-degree.
+size_t tri1_smem_bytes(int dpmax, bool bitmap_in_smem);
+size_t tri2_smem_bytes(int dpmax);
+bool tri1_bitmap_fits_smem(int dpmax);
+int tri_grid_blocks();
+// C3 per oriented edge, c3 per vertex, 4-clique count per vertex.
+// work_ctr[0..2] += (scanned out-list entries, triangles, 4-cliques).
+cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
+                        int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm,
+                        u64* work_ctr, int* err, cudaStream_t st);
+size_t tri1_gbm_bytes(int dpmax);
+// d^13 (diamond, off-cord) per vertex from the final C3.
+cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
+                        int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st);
+// d^10 = C3 (p1 - 2) and d^14 = D4,3 e / 2 from the final C3 (rank space).
+cudaError_t launch_c3_edge_terms(const int64_t* orp, const int32_t* ocol, const int32_t* C3o,
+                                 const int32_t* dr, int64_t n, u64* r10r, u64* r14r, cudaStream_t st);
+// c3o[perm[r]] = c3r[r]
+cudaError_t launch_unrank_u64(const u64* src_r, const int32_t* perm, int64_t n, int64_t* dst_o,
+                              cudaStream_t st);
+
+// --- 4-cycles (rank space) ---------------------------------------------------
+// wc[rank w] = wedges of w; *wmax = max, *wsum = total.
+cudaError_t launch_wedge_count(const Csr& g, const int32_t* rank, const int64_t* orp, const int32_t* ocol,
+                               const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap,
+                               int64_t* wc, u64* wmax, u64* wsum, cudaStream_t st);
+// Splits vertices with wedges into the shared-memory list and the global-memory list.
+cudaError_t launch_cyc_worklists(const int64_t* wc, int64_t n, int64_t smem_cap, int32_t* list_s,
+                                 int32_t* cnt_s, int32_t* list_g, int32_t* cnt_g, cudaStream_t st);
+int cyc_smem_hash_bits();
+int cyc_grid_blocks_smem();
+int cyc_grid_blocks_gmem();
+cudaError_t launch_cyc(const Csr& g, const int32_t* rank, const int32_t* perm, const int64_t* orp,
+                       const int32_t* ocol, const int64_t* wc, const int32_t* list, const int32_t* cnt,
+                       int* next, bool gmem, int gbits, uint32_t* gkeys, uint32_t* gcnt, u64* r12r,
+                       int* err, cudaStream_t st);
+
+// --- epilogue ------------------------------------------------------------------
+struct EpilogueIn {
+  const int32_t* d;
+  const int32_t* rank;
+  const int64_t* p2;
+  const int64_t* p3;
+  const int64_t* r7;
+  const int64_t* r9;
+  const u64* c3r;
+  const u64* r10r;
+  const u64* r12r;
+  const u64* r13r;
+  const u64* r14r;
+  const u64* r15r;
+};
+// Table I assembly and the exact int64 U16^{-1} product.
+cudaError_t launch_epilogue(const EpilogueIn& in, int64_t n, int64_t* raw, int64_t* net, cudaStream_t st);
+
+}  // namespace fglt

@@ -1,0 +1,738 @@
+// Passes over the input CSR (degrees, the two SpMV chains, validation, the
+// wedge-count pre-pass of the 4-cycle stage), the degree ordering, the
+// oriented graph, scans and the epilogue.
+//
+// Rows of the input CSR are processed by 8-lane groups when their degree is at
+// most HEAVY_DEGREE and by a whole block otherwise (degree-binned scheduling:
+// power-law graphs have a few rows with 10^4-10^6 entries next to millions of
+// rows with a handful).
+#include "fglt_device.cuh"
+#include "fglt_kernels.h"
+
+namespace fglt {
+
+namespace {
+
+constexpr int G = 8;          // lanes per light row
+constexpr int ROW_BLOCK = 256;
+
+template <typename RP>
+__device__ __forceinline__ int64_t ld_rp(const RP* rp, int64_t i) {
+  return (int64_t)__ldg(rp + i);
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+int64_t light_blocks(int64_t n) {
+  int64_t want = (n * G + ROW_BLOCK - 1) / ROW_BLOCK;
+  int64_t cap = (int64_t)num_sms() * 16;
+  if (want < 1) want = 1;
+  return want < cap ? want : cap;
+}
+
+// ---------------------------------------------------------------------------
+// Generic row kernels. Op supplies
+//   edge(v, j, k, s, e, a, b): one entry j = colidx[k] of row v = [s, e)
+//   done(v, a, b): the row's reductions
+// ---------------------------------------------------------------------------
+template <typename RP, typename Op>
+__global__ void __launch_bounds__(ROW_BLOCK) k_rows_light(const RP* __restrict__ rp,
+                                                          const int32_t* __restrict__ ci, int64_t n, Op op) {
+  const int lane = threadIdx.x & (G - 1);
+  const unsigned gmask = 0xFFu << ((threadIdx.x & 31) & ~(G - 1));
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += stride) {
+    const int64_t s = ld_rp(rp, v), e = ld_rp(rp, v + 1);
+    if (e - s > HEAVY_DEGREE) continue;
+    long long a = 0, b = 0;
+    for (int64_t k = s + lane; k < e; k += G) op.edge(v, __ldg(ci + k), k, s, e, a, b);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(gmask, a, o, G);
+      b += __shfl_xor_sync(gmask, b, o, G);
+    }
+    if (lane == 0) op.done(v, a, b);
+  }
+}
+
+template <typename RP, typename Op>
+__global__ void __launch_bounds__(ROW_BLOCK) k_rows_heavy(const RP* __restrict__ rp,
+                                                          const int32_t* __restrict__ ci,
+                                                          const int32_t* __restrict__ heavy,
+                                                          const int32_t* __restrict__ nheavy, Op op) {
+  __shared__ long long red[32];
+  const int nh = *nheavy;
+  for (int h = blockIdx.x; h < nh; h += gridDim.x) {
+    const int64_t v = heavy[h];
+    const int64_t s = ld_rp(rp, v), e = ld_rp(rp, v + 1);
+    long long a = 0, b = 0;
+    for (int64_t k = s + threadIdx.x; k < e; k += blockDim.x) op.edge(v, __ldg(ci + k), k, s, e, a, b);
+    a = block_sum(a, red);
+    b = block_sum(b, red);
+    if (threadIdx.x == 0) op.done(v, a, b);
+  }
+}
+
+template <typename RP, typename Op>
+cudaError_t run_rows(const Csr& g, const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap, Op op,
+                     cudaStream_t st) {
+  const RP* rp = static_cast<const RP*>(g.rowptr);
+  if (g.n <= 0) return cudaSuccess;
+  k_rows_light<RP, Op><<<(unsigned)light_blocks(g.n), ROW_BLOCK, 0, st>>>(rp, g.colidx, g.n, op);
+  if (heavy_cap > 0) {
+    int64_t hb = heavy_cap < (int64_t)num_sms() * 4 ? heavy_cap : (int64_t)num_sms() * 4;
+    if (hb < 1) hb = 1;
+    k_rows_heavy<RP, Op><<<(unsigned)hb, ROW_BLOCK, 0, st>>>(rp, g.colidx, heavy, nheavy, op);
+  }
+  return cudaGetLastError();
+}
+
+template <typename Op>
+cudaError_t dispatch_rows(const Csr& g, const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap,
+                          Op op, cudaStream_t st) {
+  return g.rp64 ? run_rows<int64_t>(g, heavy, nheavy, heavy_cap, op, st)
+                : run_rows<int32_t>(g, heavy, nheavy, heavy_cap, op, st);
+}
+
+// --- row operations ----------------------------------------------------------
+
+struct Spmv1Op {  // p2 = A p1 - p1 (eq. p2), d^7 = A((p1-1) o (p1-2)) / 2
+  const int32_t* d;
+  int64_t* p2;
+  int64_t* r7;
+  int64_t n;
+  int* err;
+  __device__ __forceinline__ void edge(int64_t, int32_t j, int64_t, int64_t, int64_t, long long& a,
+                                       long long& b) const {
+    if ((uint32_t)j >= (uint64_t)n) {
+      atomicOr(err, ERR_BAD_GRAPH);
+      return;
+    }
+    const long long dj = __ldg(d + j);
+    a += dj;
+    b += (dj - 1) * (dj - 2) / 2;
+  }
+  __device__ __forceinline__ void done(int64_t v, long long a, long long b) const {
+    p2[v] = a - __ldg(d + v);
+    r7[v] = b;
+  }
+};
+
+struct Spmv2Op {  // p3 = A p2 - p1 o (p1-1) - 2 c3, d^9 = A c3 - 2 c3
+  const int32_t* d;
+  const int64_t* p2;
+  const int64_t* c3o;
+  int64_t* p3;
+  int64_t* r9;
+  int64_t n;
+  __device__ __forceinline__ void edge(int64_t, int32_t j, int64_t, int64_t, int64_t, long long& a,
+                                       long long& b) const {
+    if ((uint32_t)j >= (uint64_t)n) return;
+    a += __ldg(p2 + j);
+    b += __ldg(c3o + j);
+  }
+  __device__ __forceinline__ void done(int64_t v, long long a, long long b) const {
+    const long long dv = __ldg(d + v), c = __ldg(c3o + v);
+    p3[v] = a - dv * (dv - 1) - 2 * c;
+    r9[v] = b - 2 * c;
+  }
+};
+
+struct OrientCountOp {  // out-degree in the degree-ordered orientation
+  const int32_t* rank;
+  int32_t* opc;
+  int32_t* dpmax;
+  int64_t n;
+  __device__ __forceinline__ void edge(int64_t v, int32_t j, int64_t, int64_t, int64_t, long long& a,
+                                       long long&) const {
+    if ((uint32_t)j >= (uint64_t)n) return;
+    a += __ldg(rank + j) > __ldg(rank + v);
+  }
+  __device__ __forceinline__ void done(int64_t v, long long a, long long) const {
+    opc[__ldg(rank + v)] = (int32_t)a;
+    atomicMax(dpmax, (int32_t)a);
+  }
+};
+
+struct OrientFillOp {  // appends rank(j) to the oriented row of rank(v)
+  const int32_t* rank;
+  const int64_t* orp;
+  int32_t* cursor;
+  int32_t* ocol;
+  int64_t n;
+  __device__ __forceinline__ void edge(int64_t v, int32_t j, int64_t, int64_t, int64_t, long long&,
+                                       long long&) const {
+    if ((uint32_t)j >= (uint64_t)n) return;
+    const int32_t rv = __ldg(rank + v), rj = __ldg(rank + j);
+    if (rj > rv) {
+      const int64_t base = orp[rv];
+      const int32_t pos = atomicAdd(cursor + rv, 1);
+      if (base + pos < orp[rv + 1]) ocol[base + pos] = rj;
+    }
+  }
+  __device__ __forceinline__ void done(int64_t, long long, long long) const {}
+};
+
+// Wedges w - v - u with u above both v and w in the degree order (u in N+(v),
+// u > w): the 4-cycle stage's work and hash-table bound per vertex w.
+struct WedgeCountOp {
+  const int32_t* rank;
+  const int64_t* orp;
+  const int32_t* ocol;
+  int64_t* wc;
+  u64* wmax;
+  u64* wsum;
+  int64_t n;
+  __device__ __forceinline__ void edge(int64_t v, int32_t j, int64_t, int64_t, int64_t, long long& a,
+                                       long long&) const {
+    if ((uint32_t)j >= (uint64_t)n) return;
+    const int32_t rw = __ldg(rank + v), rv = __ldg(rank + j);
+    const int64_t ob = __ldg(orp + rv), oe = __ldg(orp + rv + 1);
+    a += oe - upper_bound_i32(ocol, ob, oe, rw);
+  }
+  __device__ __forceinline__ void done(int64_t v, long long a, long long) const {
+    wc[__ldg(rank + v)] = a;
+    if (a) {
+      atomicMax(wmax, (u64)a);
+      atomicAdd(wsum, (u64)a);
+    }
+  }
+};
+
+template <typename RP>
+struct ValidateOp {  // simple, symmetric, strictly increasing rows
+  const RP* rp;
+  const int32_t* ci;
+  int64_t n;
+  int* err;
+  __device__ __forceinline__ void edge(int64_t v, int32_t j, int64_t k, int64_t s, int64_t, long long&,
+                                       long long&) const {
+    bool bad = (j < 0) || ((int64_t)j >= n) || ((int64_t)j == v);
+    if (!bad && k > s && __ldg(ci + k - 1) >= j) bad = true;
+    if (!bad) {
+      int64_t lo = ld_rp(rp, j), hi = ld_rp(rp, j + 1);
+      bool found = false;
+      while (lo < hi) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        int32_t x = __ldg(ci + mid);
+        if (x == (int32_t)v) { found = true; break; }
+        if (x < (int32_t)v) lo = mid + 1; else hi = mid;
+      }
+      bad = !found;
+    }
+    if (bad) atomicOr(err, ERR_BAD_GRAPH);
+  }
+  __device__ __forceinline__ void done(int64_t, long long, long long) const {}
+};
+
+// ---------------------------------------------------------------------------
+// Degrees
+// ---------------------------------------------------------------------------
+template <typename RP>
+__global__ void k_degree(const RP* __restrict__ rp, int64_t n, int64_t nnz, int32_t* d, int32_t* dmax,
+                         int32_t* heavy, int32_t* nheavy, int64_t heavy_cap, int* err) {
+  int local_max = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = ld_rp(rp, v), hi = ld_rp(rp, v + 1);
+    int64_t dv = hi - lo;
+    if (lo < 0 || hi > nnz || dv < 0 || dv > 0x7fffffff || (v == 0 && lo != 0)) {
+      atomicOr(err, ERR_BAD_ROWPTR);
+      dv = 0;
+    }
+    const int32_t dd = (int32_t)dv;
+    d[v] = dd;
+    local_max = max(local_max, dd);
+    if (dd > HEAVY_DEGREE) {
+      int h = atomicAdd(nheavy, 1);
+      if (h < heavy_cap) heavy[h] = (int32_t)v;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(dmax, local_max);
+}
+
+// ---------------------------------------------------------------------------
+// Degree ordering: a counting sort of the vertices by degree. rank(v) is the
+// position of v in non-decreasing degree order (ties in any order); the
+// oriented graph keeps the edge v -> u iff rank(v) < rank(u).
+// ---------------------------------------------------------------------------
+constexpr int SMALL_BINS = 1024;
+
+__global__ void k_degree_hist(const int32_t* __restrict__ d, int64_t n, int32_t* hist) {
+  __shared__ int32_t h[SMALL_BINS];
+  for (int i = threadIdx.x; i < SMALL_BINS; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t dv = d[v];
+    if (dv < SMALL_BINS) atomicAdd(&h[dv], 1);
+    else atomicAdd(&hist[dv], 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < SMALL_BINS; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+constexpr int RANK_T = 256, RANK_I = 8;
+
+__global__ void __launch_bounds__(RANK_T) k_rank_assign(const int32_t* __restrict__ d, int64_t n,
+                                                        const int64_t* __restrict__ base, int32_t* cursor,
+                                                        int32_t* rank, int32_t* perm, int32_t* dr) {
+  __shared__ int32_t cnt[SMALL_BINS];
+  __shared__ int32_t off[SMALL_BINS];
+  const int64_t chunk = (int64_t)RANK_T * RANK_I;
+  for (int64_t c0 = (int64_t)blockIdx.x * chunk; c0 < n; c0 += (int64_t)gridDim.x * chunk) {
+    for (int i = threadIdx.x; i < SMALL_BINS; i += RANK_T) cnt[i] = 0;
+    __syncthreads();
+    int32_t dv[RANK_I], loc[RANK_I];
+#pragma unroll
+    for (int t = 0; t < RANK_I; ++t) {
+      const int64_t v = c0 + (int64_t)t * RANK_T + threadIdx.x;
+      dv[t] = v < n ? d[v] : -1;
+      loc[t] = (dv[t] >= 0 && dv[t] < SMALL_BINS) ? atomicAdd(&cnt[dv[t]], 1) : 0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SMALL_BINS; i += RANK_T)
+      if (cnt[i]) off[i] = atomicAdd(&cursor[i], cnt[i]);
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < RANK_I; ++t) {
+      const int64_t v = c0 + (int64_t)t * RANK_T + threadIdx.x;
+      if (dv[t] < 0) continue;
+      int64_t r;
+      if (dv[t] < SMALL_BINS) r = base[dv[t]] + off[dv[t]] + loc[t];
+      else r = base[dv[t]] + atomicAdd(&cursor[dv[t]], 1);
+      rank[v] = (int32_t)r;
+      perm[r] = (int32_t)v;
+      dr[r] = dv[t];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row sort of the oriented graph (ascending rank labels): bitonic networks in
+// registers (rows of at most 32), shared memory (at most 16384) or global
+// scratch (longer rows).
+// ---------------------------------------------------------------------------
+__global__ void k_sort_rows_warp(const int64_t* __restrict__ orp, int64_t n, int32_t* ocol) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+    const int64_t b = orp[r];
+    const int L = (int)(orp[r + 1] - b);
+    if (L < 2 || L > 32) continue;
+    int32_t x = lane < L ? ocol[b + lane] : 0x7fffffff;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const int32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        const bool keep_min = ((lane & k) == 0) == ((lane & j) == 0);
+        x = keep_min ? min(x, y) : max(x, y);
+      }
+    }
+    if (lane < L) ocol[b + lane] = x;
+  }
+}
+
+__device__ void bitonic_block(int32_t* buf, int P) {
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const int32_t a = buf[i], b = buf[ixj];
+          const bool asc = (i & k) == 0;
+          if ((a > b) == asc) { buf[i] = b; buf[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+constexpr int SORT_SMEM_MAX = 16384;
+
+__global__ void k_sort_rows_block(const int64_t* __restrict__ orp, int64_t n, int32_t* ocol) {
+  extern __shared__ int32_t sbuf[];
+  for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+    const int64_t b = orp[r];
+    const int L = (int)(orp[r + 1] - b);
+    if (L <= 32 || L > SORT_SMEM_MAX) continue;
+    int P = 64;
+    while (P < L) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sbuf[i] = i < L ? ocol[b + i] : 0x7fffffff;
+    __syncthreads();
+    bitonic_block(sbuf, P);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) ocol[b + i] = sbuf[i];
+    __syncthreads();
+  }
+}
+
+__global__ void k_sort_rows_global(const int64_t* __restrict__ orp, int64_t n, int32_t* ocol, int32_t* scratch) {
+  for (int64_t r = 0; r < n; ++r) {
+    const int64_t b = orp[r];
+    const int64_t L = orp[r + 1] - b;
+    if (L <= SORT_SMEM_MAX) continue;
+    int P = SORT_SMEM_MAX;
+    while (P < L) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) scratch[i] = i < L ? ocol[b + i] : 0x7fffffff;
+    __syncthreads();
+    bitonic_block(scratch, P);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) ocol[b + i] = scratch[i];
+    __syncthreads();
+  }
+}
+
+__global__ void k_worklist_outdeg(const int32_t* __restrict__ opc, int64_t n, int min_out, int32_t* list,
+                                  int32_t* count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < n; r0 += stride) {
+    const int64_t r = r0 + lane;
+    const bool take = r < n && opc[r] >= min_out;
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    int pos0 = 0;
+    if (lane == 0 && m) pos0 = atomicAdd(count, __popc(m));
+    pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+    if (take) list[pos0 + __popc(m & ((1u << lane) - 1))] = (int32_t)r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan int32 -> int64 (three phases).
+// ---------------------------------------------------------------------------
+constexpr int SCAN_T = 256, SCAN_I = 8, SCAN_B = SCAN_T * SCAN_I;
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const int32_t* __restrict__ in, int64_t n, int64_t* bsum) {
+  __shared__ long long red[32];
+  const int64_t b0 = (int64_t)blockIdx.x * SCAN_B;
+  long long s = 0;
+  for (int i = threadIdx.x; i < SCAN_B; i += SCAN_T) {
+    const int64_t k = b0 + i;
+    if (k < n) s += in[k];
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_bsums(int64_t* bsum, int64_t nb) {
+  __shared__ long long wsum[32];
+  __shared__ long long carry_s;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t c0 = 0; c0 < nb; c0 += 1024) {
+    const int64_t k = c0 + threadIdx.x;
+    long long x = k < nb ? bsum[k] : 0;
+    long long incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      long long w = wsum[lane];
+      long long wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      wsum[lane] = wi - w;  // exclusive over warps
+    }
+    __syncthreads();
+    const long long carry = carry_s;
+    if (k < nb) bsum[k] = carry + wsum[wid] + incl - x;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry_s = carry + wsum[wid] + incl;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_down(const int32_t* __restrict__ in, int64_t n,
+                                                      const int64_t* __restrict__ bsum, int64_t* out) {
+  __shared__ long long wsum[SCAN_T / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t b0 = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_I;
+  long long v[SCAN_I];
+  long long t = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_I; ++i) {
+    v[i] = (b0 + i < n) ? in[b0 + i] : 0;
+    t += v[i];
+  }
+  long long incl = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  long long wpre = 0;
+  for (int w = 0; w < wid; ++w) wpre += wsum[w];
+  long long run = bsum[blockIdx.x] + wpre + incl - t;
+#pragma unroll
+  for (int i = 0; i < SCAN_I; ++i) {
+    if (b0 + i < n) out[b0 + i] = run;
+    run += v[i];
+  }
+  if (b0 < n && b0 + SCAN_I >= n) out[n] = run;
+}
+
+// ---------------------------------------------------------------------------
+// Edge terms of the final C3 (oriented edges a -> b, rank space):
+// d^10 = C3 (p1 - 2) and d^14 = D4,3 e / 2 = sum_j C3(i,j)(C3(i,j)-1)/2, since
+// P2(i,j) = C3(i,j) on an edge (Sec. 4.3, D4,3 = A o C4,2).
+// ---------------------------------------------------------------------------
+__global__ void k_c3_edge_terms(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                const int32_t* __restrict__ C3o, const int32_t* __restrict__ dr, int64_t n,
+                                u64* r10r, u64* r14r) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n; a += warps) {
+    const int64_t b0 = orp[a], b1 = orp[a + 1];
+    if (b1 == b0) continue;
+    const long long da = dr[a];
+    long long s10 = 0, s14 = 0;
+    for (int64_t k = b0 + lane; k < b1; k += 32) {
+      const long long t = C3o[k];
+      if (t) {
+        const int32_t b = ocol[k];
+        const long long pair = t * (t - 1) / 2;
+        s10 += t * ((long long)dr[b] - 2);
+        s14 += pair;
+        atomicAdd(r10r + b, (u64)(t * (da - 2)));
+        if (pair) atomicAdd(r14r + b, (u64)pair);
+      }
+    }
+    s10 = warp_sum_i64(s10);
+    s14 = warp_sum_i64(s14);
+    if (lane == 0) {
+      if (s10) atomicAdd(r10r + a, (u64)s10);
+      if (s14) atomicAdd(r14r + a, (u64)s14);
+    }
+  }
+}
+
+__global__ void k_unrank_u64(const u64* __restrict__ src, const int32_t* __restrict__ perm, int64_t n,
+                             int64_t* dst) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    dst[perm[r]] = (int64_t)src[r];
+}
+
+// ---------------------------------------------------------------------------
+// Epilogue: Table I rows and f = U16^{-1} f^ (Table II), exact in int64.
+// ---------------------------------------------------------------------------
+template <bool VEC>
+__global__ void k_epilogue(EpilogueIn in, int64_t n, int64_t* __restrict__ raw, int64_t* __restrict__ net) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const long long d = in.d[v];
+    const int32_t r = in.rank[v];
+    const long long c3 = (long long)in.c3r[r];
+    const long long p2 = in.p2[v];
+    long long f[16];
+    f[0] = 1;
+    f[1] = d;
+    f[2] = p2;
+    f[3] = d * (d - 1) / 2;
+    f[4] = c3;
+    f[5] = in.p3[v];
+    f[6] = p2 * (d - 1) - 2 * c3;
+    f[7] = in.r7[v];
+    f[8] = (d * (d - 1) / 2) * (d - 2) / 3;
+    f[9] = in.r9[v];
+    f[10] = (long long)in.r10r[r];
+    f[11] = (d - 2) * c3;
+    f[12] = (long long)in.r12r[r];
+    f[13] = (long long)in.r13r[r];
+    f[14] = (long long)in.r14r[r];
+    f[15] = (long long)in.r15r[r];
+    long long g[16];
+    g[0] = f[0];
+    g[1] = f[1];
+    g[2] = f[2] - 2 * f[4];
+    g[3] = f[3] - f[4];
+    g[4] = f[4];
+    g[5] = f[5] - 2 * f[9] - f[10] - 2 * f[12] + 4 * f[13] + 2 * f[14] - 6 * f[15];
+    g[6] = f[6] - f[10] - 2 * f[11] - 2 * f[12] + 2 * f[13] + 4 * f[14] - 6 * f[15];
+    g[7] = f[7] - f[9] - f[10] + 2 * f[13] + f[14] - 3 * f[15];
+    g[8] = f[8] - f[11] + f[14] - f[15];
+    g[9] = f[9] - 2 * f[13] + 3 * f[15];
+    g[10] = f[10] - 2 * f[13] - 2 * f[14] + 6 * f[15];
+    g[11] = f[11] - 2 * f[14] + 3 * f[15];
+    g[12] = f[12] - f[13] - f[14] + 3 * f[15];
+    g[13] = f[13] - 3 * f[15];
+    g[14] = f[14] - 3 * f[15];
+    g[15] = f[15];
+    if (VEC) {  // both outputs 16-byte aligned
+      if (raw) {
+        longlong2* o = reinterpret_cast<longlong2*>(raw + v * 16);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) o[i] = make_longlong2(f[2 * i], f[2 * i + 1]);
+      }
+      if (net) {
+        longlong2* o = reinterpret_cast<longlong2*>(net + v * 16);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) o[i] = make_longlong2(g[2 * i], g[2 * i + 1]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (raw) raw[v * 16 + i] = f[i];
+        if (net) net[v * 16 + i] = g[i];
+      }
+    }
+  }
+}
+
+unsigned grid_for(int64_t items, int threads, int per_sm = 8) {
+  int64_t want = (items + threads - 1) / threads;
+  int64_t cap = (int64_t)num_sms() * per_sm;
+  if (want < 1) want = 1;
+  return (unsigned)(want < cap ? want : cap);
+}
+
+}  // namespace
+
+// ===========================================================================
+// Launchers
+// ===========================================================================
+
+cudaError_t launch_degree(const Csr& g, int32_t* d, int32_t* dmax, int32_t* heavy, int32_t* nheavy, int* err,
+                          cudaStream_t st) {
+  if (g.n <= 0) return cudaSuccess;
+  const int64_t cap = g.nnz / HEAVY_DEGREE + 1;
+  if (g.rp64)
+    k_degree<int64_t><<<grid_for(g.n, 256), 256, 0, st>>>(static_cast<const int64_t*>(g.rowptr), g.n, g.nnz, d,
+                                                          dmax, heavy, nheavy, cap, err);
+  else
+    k_degree<int32_t><<<grid_for(g.n, 256), 256, 0, st>>>(static_cast<const int32_t*>(g.rowptr), g.n, g.nnz, d,
+                                                          dmax, heavy, nheavy, cap, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const Csr& g, const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap,
+                            int* err, cudaStream_t st) {
+  if (g.rp64) {
+    ValidateOp<int64_t> op{static_cast<const int64_t*>(g.rowptr), g.colidx, g.n, err};
+    return run_rows<int64_t>(g, heavy, nheavy, heavy_cap, op, st);
+  }
+  ValidateOp<int32_t> op{static_cast<const int32_t*>(g.rowptr), g.colidx, g.n, err};
+  return run_rows<int32_t>(g, heavy, nheavy, heavy_cap, op, st);
+}
+
+cudaError_t launch_spmv1(const Csr& g, const int32_t* d, const int32_t* heavy, const int32_t* nheavy,
+                         int64_t heavy_cap, int64_t* p2, int64_t* r7, int* err, cudaStream_t st) {
+  return dispatch_rows(g, heavy, nheavy, heavy_cap, Spmv1Op{d, p2, r7, g.n, err}, st);
+}
+
+cudaError_t launch_spmv2(const Csr& g, const int32_t* d, const int64_t* p2, const int64_t* c3o,
+                         const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap, int64_t* p3,
+                         int64_t* r9, cudaStream_t st) {
+  return dispatch_rows(g, heavy, nheavy, heavy_cap, Spmv2Op{d, p2, c3o, p3, r9, g.n}, st);
+}
+
+cudaError_t launch_degree_hist(const int32_t* d, int64_t n, int32_t* hist, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_degree_hist<<<grid_for(n, 256, 4), 256, 0, st>>>(d, n, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rank_assign(const int32_t* d, int64_t n, const int64_t* base, int32_t* cursor,
+                               int32_t* rank, int32_t* perm, int32_t* dr, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_rank_assign<<<grid_for(n, RANK_T * RANK_I, 4), RANK_T, 0, st>>>(d, n, base, cursor, rank, perm, dr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_orient_count(const Csr& g, const int32_t* rank, const int32_t* heavy,
+                                const int32_t* nheavy, int64_t heavy_cap, int32_t* opc, int32_t* dpmax,
+                                cudaStream_t st) {
+  return dispatch_rows(g, heavy, nheavy, heavy_cap, OrientCountOp{rank, opc, dpmax, g.n}, st);
+}
+
+cudaError_t launch_orient_fill(const Csr& g, const int32_t* rank, const int64_t* orp, const int32_t* heavy,
+                               const int32_t* nheavy, int64_t heavy_cap, int32_t* cursor, int32_t* ocol,
+                               cudaStream_t st) {
+  return dispatch_rows(g, heavy, nheavy, heavy_cap, OrientFillOp{rank, orp, cursor, ocol, g.n}, st);
+}
+
+cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int32_t* ocol, int32_t* gscratch,
+                             cudaStream_t st) {
+  if (n <= 0 || dpmax < 2) return cudaSuccess;
+  k_sort_rows_warp<<<grid_for(n * 32, 256), 256, 0, st>>>(orp, n, ocol);
+  if (dpmax > 32) {
+    int P = 64;
+    while (P < dpmax && P < SORT_SMEM_MAX) P <<= 1;
+    const size_t smem = (size_t)P * sizeof(int32_t);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_sort_rows_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_sort_rows_block<<<grid_for(n, 1, 4), 256, smem, st>>>(orp, n, ocol);
+  }
+  if (dpmax > SORT_SMEM_MAX) k_sort_rows_global<<<1, 1024, 0, st>>>(orp, n, ocol, gscratch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_worklist_outdeg(const int32_t* opc, int64_t n, int min_out, int32_t* list, int32_t* count,
+                                   cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_worklist_outdeg<<<grid_for(n, 256), 256, 0, st>>>(opc, n, min_out, list, count);
+  return cudaGetLastError();
+}
+
+size_t scan_temp_bytes(int64_t n) {
+  const int64_t nb = (n + SCAN_B - 1) / SCAN_B + 1;
+  return (size_t)nb * sizeof(int64_t);
+}
+
+cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t n, int64_t* out, void* temp, cudaStream_t st) {
+  if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), st);
+  const int64_t nb = (n + SCAN_B - 1) / SCAN_B;
+  int64_t* bsum = static_cast<int64_t*>(temp);
+  k_scan_reduce<<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, bsum);
+  k_scan_bsums<<<1, 1024, 0, st>>>(bsum, nb);
+  k_scan_down<<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, bsum, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c3_edge_terms(const int64_t* orp, const int32_t* ocol, const int32_t* C3o, const int32_t* dr,
+                                 int64_t n, u64* r10r, u64* r14r, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_c3_edge_terms<<<grid_for(n * 32, 256), 256, 0, st>>>(orp, ocol, C3o, dr, n, r10r, r14r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unrank_u64(const u64* src_r, const int32_t* perm, int64_t n, int64_t* dst_o, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_unrank_u64<<<grid_for(n, 256), 256, 0, st>>>(src_r, perm, n, dst_o);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wedge_count(const Csr& g, const int32_t* rank, const int64_t* orp, const int32_t* ocol,
+                               const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap, int64_t* wc,
+                               u64* wmax, u64* wsum, cudaStream_t st) {
+  return dispatch_rows(g, heavy, nheavy, heavy_cap, WedgeCountOp{rank, orp, ocol, wc, wmax, wsum, g.n}, st);
+}
+
+cudaError_t launch_epilogue(const EpilogueIn& in, int64_t n, int64_t* raw, int64_t* net, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const bool vec = ((uintptr_t)raw % 16 == 0) && ((uintptr_t)net % 16 == 0);
+  if (vec) k_epilogue<true><<<grid_for(n, 256), 256, 0, st>>>(in, n, raw, net);
+  else k_epilogue<false><<<grid_for(n, 256), 256, 0, st>>>(in, n, raw, net);
+  return cudaGetLastError();
+}
+
+}  // namespace fglt

@@ -1,0 +1,328 @@
+// Triangle passes over the degree-ordered orientation (rank space).
+//
+// Every triangle {a, b, c} with rank a < b < c is listed exactly once, while
+// processing its lowest vertex a: b runs over N+(a), c over N+(b), and c is
+// kept when it is also in N+(a). N+(a) lives in a shared-memory hash table
+// (key = rank label, value = position in N+(a)). Both out-lists are sorted, so
+// the scan of N+(b) stops at the largest element of N+(a).
+//
+// Pass 1 builds, per vertex a, the adjacency bitmap of the subgraph induced on
+// N+(a) (bit (b, c) = edge b -> c) and from it
+//   C3(i,j) = |N(i) ∩ N(j)| per oriented edge           (Lemma 2: C3 = A o A^2)
+//   c3(i)   = triangles at i = C3 e / 2                  (Lemma 2)
+//   d^15(i) = 4-cliques at i = T e / 6, T(i,j) = q_ij^T A q_ij (Sec. 4.3):
+//             a 4-clique {a,b,c,d} (a < b < c < d) is the bit pair (b,c) with
+//             d in row(b) AND row(c).
+// Pass 2 re-lists the triangles once C3 is final and adds, for a triangle
+// {i,j,k}, C3(j,k) - 1 to i (and likewise for j and k):
+//   d^13 = D4,c e / 2 with D4,c = A o (A (C3 - A))       (Sec. 4.3)
+#include "fglt_device.cuh"
+#include "fglt_kernels.h"
+
+namespace fglt {
+
+namespace {
+
+constexpr int TRI_T = 256;
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+int hash_bits_for(int D) {
+  int hb = 5;
+  while ((1 << hb) < 2 * D) ++hb;
+  return hb;
+}
+
+int num_sms() {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+__device__ __forceinline__ void table_insert(uint32_t* keys, int32_t* vals, uint32_t key, int32_t val, int hb,
+                                             int* err) {
+  const uint32_t mask = (1u << hb) - 1;
+  uint32_t h = hash_slot(key, hb);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    if (atomicCAS(&keys[h], EMPTY_KEY, key) == EMPTY_KEY) {
+      vals[h] = val;
+      return;
+    }
+    h = (h + 1) & mask;
+  }
+  atomicOr(err, ERR_HASH_FULL);
+}
+
+__device__ __forceinline__ int table_find(const uint32_t* keys, const int32_t* vals, uint32_t key, int hb) {
+  const uint32_t mask = (1u << hb) - 1;
+  uint32_t h = hash_slot(key, hb);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const uint32_t k = keys[h];
+    if (k == key) return vals[h];
+    if (k == EMPTY_KEY) return -1;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1
+// ---------------------------------------------------------------------------
+template <bool SMEM_BM>
+__global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                                const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
+                                                int* next, int Dmax, int Hbits, int32_t* C3o, u64* c3r, u64* k4r,
+                                                uint32_t* gbm, u64* work_ctr, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  __shared__ u64 red[32];
+  const int Hmax = 1 << Hbits, Wmax = (Dmax + 31) >> 5;
+  uint32_t* keys = reinterpret_cast<uint32_t*>(smem);
+  int32_t* vals = reinterpret_cast<int32_t*>(keys + Hmax);
+  int32_t* rowc = vals + Hmax;
+  int32_t* colc = rowc + Dmax;
+  uint32_t* k4c = reinterpret_cast<uint32_t*>(colc + Dmax);
+  uint32_t* bm = SMEM_BM ? (k4c + Dmax) : (gbm + (size_t)blockIdx.x * Dmax * Wmax);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int total = *nwork;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    const int a = work[item];
+    const int64_t base = orp[a];
+    const int D = (int)(orp[a + 1] - base);
+    int hb = 5;
+    while ((1 << hb) < 2 * D) ++hb;
+    const int W = (D + 31) >> 5;
+
+    for (int i = tid; i < (1 << hb); i += blockDim.x) keys[i] = EMPTY_KEY;
+    for (int i = tid; i < D; i += blockDim.x) { rowc[i] = 0; colc[i] = 0; k4c[i] = 0; }
+    for (int i = tid; i < D * W; i += blockDim.x) bm[i] = 0u;
+    __syncthreads();
+    for (int x = tid; x < D; x += blockDim.x) table_insert(keys, vals, (uint32_t)ocol[base + x], x, hb, err);
+    __syncthreads();
+
+    // Triangles {a, b, c}: c in N+(b) ∩ N+(a).
+    const int32_t lastA = ocol[base + D - 1];
+    u64 probes = 0;
+    for (int ib = warp; ib < D; ib += nwarps) {
+      const int32_t b = ocol[base + ib];
+      const int64_t bb = orp[b];
+      const int64_t be = upper_bound_i32(ocol, bb, orp[b + 1], lastA);
+      probes += (u64)(be - bb);
+      uint32_t* row = bm + (size_t)ib * W;
+      int hits = 0;
+      for (int64_t k = bb + lane; k < be; k += 32) {
+        const int ic = table_find(keys, vals, (uint32_t)ocol[k], hb);
+        if (ic >= 0) {
+          atomicOr(&row[ic >> 5], 1u << (ic & 31));
+          atomicAdd(&C3o[k], 1);      // edge b -> c
+          atomicAdd(&colc[ic], 1);    // edge a -> c
+          ++hits;                     // edge a -> b
+        }
+      }
+      hits = warp_sum_i32(hits);
+      if (lane == 0) rowc[ib] = hits;
+    }
+    __syncthreads();
+
+    // 4-cliques {a, b, c, d}: bit (b, c) and d in row(b) AND row(c).
+    u64 k4_here = 0;
+    for (int ib = warp; ib < D; ib += nwarps) {
+      if (rowc[ib] < 2) continue;
+      const uint32_t* row = bm + (size_t)ib * W;
+      int krow = 0;
+      for (int w0 = (ib + 1) >> 5; w0 < W; ++w0) {
+        const uint32_t bits = row[w0];
+        if (!bits) continue;
+        if ((bits >> lane) & 1u) {
+          const int ic = (w0 << 5) + lane;
+          const uint32_t* rc = bm + (size_t)ic * W;
+          int k = 0;
+          for (int w = w0; w < W; ++w) {
+            uint32_t x = row[w] & rc[w];
+            while (x) {
+              const int t = __ffs(x) - 1;
+              x &= x - 1;
+              atomicAdd(&k4c[(w << 5) + t], 1u);
+              ++k;
+            }
+          }
+          if (k) {
+            atomicAdd(&k4c[ic], (uint32_t)k);
+            krow += k;
+          }
+        }
+      }
+      krow = warp_sum_i32(krow);
+      if (lane == 0 && krow) {
+        atomicAdd(&k4c[ib], (uint32_t)krow);
+        k4_here += (u64)krow;
+      }
+    }
+    __syncthreads();
+
+    // Flush: C3(a, x) gets the triangles of this pass through edge a -> x.
+    u64 tri_here = 0;
+    for (int x = tid; x < D; x += blockDim.x) {
+      const int t = rowc[x] + colc[x];
+      tri_here += (u64)rowc[x];
+      const int32_t vx = ocol[base + x];
+      if (t) {
+        atomicAdd(&C3o[base + x], t);
+        atomicAdd(&c3r[vx], (u64)t);
+      }
+      if (k4c[x]) atomicAdd(&k4r[vx], (u64)k4c[x]);
+    }
+    const u64 tri_sum = block_sum(tri_here, red);
+    const u64 k4_sum = block_sum(k4_here, red);
+    const u64 probe_sum = block_sum(lane == 0 ? probes : (u64)0, red);
+    if (tid == 0) {
+      if (tri_sum) atomicAdd(&c3r[a], tri_sum);
+      if (k4_sum) atomicAdd(&k4r[a], k4_sum);
+      atomicAdd(&work_ctr[0], probe_sum);
+      atomicAdd(&work_ctr[1], tri_sum);
+      atomicAdd(&work_ctr[2], k4_sum);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                                const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
+                                                int* next, int Dmax, int Hbits, const int32_t* __restrict__ C3o,
+                                                u64* r13r, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  __shared__ u64 red[32];
+  const int Hmax = 1 << Hbits;
+  u64* acc = reinterpret_cast<u64*>(smem);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(acc + Dmax);
+  int32_t* vals = reinterpret_cast<int32_t*>(keys + Hmax);
+  int32_t* tv = vals + Hmax;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int total = *nwork;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    const int a = work[item];
+    const int64_t base = orp[a];
+    const int D = (int)(orp[a + 1] - base);
+    int hb = 5;
+    while ((1 << hb) < 2 * D) ++hb;
+
+    for (int i = tid; i < (1 << hb); i += blockDim.x) keys[i] = EMPTY_KEY;
+    for (int i = tid; i < D; i += blockDim.x) { acc[i] = 0; tv[i] = C3o[base + i]; }
+    __syncthreads();
+    for (int x = tid; x < D; x += blockDim.x) table_insert(keys, vals, (uint32_t)ocol[base + x], x, hb, err);
+    __syncthreads();
+
+    const int32_t lastA = ocol[base + D - 1];
+    long long acc_a = 0;
+    for (int ib = warp; ib < D; ib += nwarps) {
+      const int32_t b = ocol[base + ib];
+      const int64_t bb = orp[b];
+      const int64_t be = upper_bound_i32(ocol, bb, orp[b + 1], lastA);
+      const long long tab = tv[ib];
+      long long accb = 0;
+      for (int64_t k = bb + lane; k < be; k += 32) {
+        const int ic = table_find(keys, vals, (uint32_t)ocol[k], hb);
+        if (ic >= 0) {
+          acc_a += (long long)C3o[k] - 1;  // a: opposite edge b-c
+          accb += (long long)tv[ic] - 1;   // b: opposite edge a-c
+          if (tab > 1) atomicAdd(&acc[ic], (u64)(tab - 1));  // c: opposite edge a-b
+        }
+      }
+      accb = warp_sum_i64(accb);
+      if (lane == 0 && accb) atomicAdd(&acc[ib], (u64)accb);
+    }
+    __syncthreads();
+    for (int x = tid; x < D; x += blockDim.x)
+      if (acc[x]) atomicAdd(&r13r[ocol[base + x]], acc[x]);
+    const u64 sa = block_sum((u64)acc_a, red);
+    if (tid == 0 && sa) atomicAdd(&r13r[a], sa);
+    __syncthreads();
+  }
+}
+
+size_t tri1_smem_impl(int D, bool smem_bm) {
+  const int H = 1 << hash_bits_for(D);
+  const size_t W = (size_t)(D + 31) / 32;
+  size_t bytes = (size_t)H * 8 + (size_t)D * 12;
+  if (smem_bm) bytes += (size_t)D * W * 4;
+  return (bytes + 15) & ~(size_t)15;
+}
+
+int occupancy_grid(const void* fn, size_t smem) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TRI_T, smem);
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * num_sms();
+}
+
+}  // namespace
+
+bool tri1_bitmap_fits_smem(int dpmax) { return tri1_smem_impl(dpmax, true) <= SMEM_LIMIT - 1024; }
+
+size_t tri1_smem_bytes(int dpmax, bool bitmap_in_smem) { return tri1_smem_impl(dpmax, bitmap_in_smem); }
+
+size_t tri2_smem_bytes(int dpmax) {
+  const int H = 1 << hash_bits_for(dpmax);
+  return (((size_t)dpmax * 12 + (size_t)H * 8) + 15) & ~(size_t)15;
+}
+
+int tri_grid_blocks() { return num_sms(); }
+
+static int tri1_grid(int dpmax, bool smem_bm) {
+  const size_t smem = tri1_smem_impl(dpmax, smem_bm);
+  if (smem_bm) {
+    cudaFuncSetAttribute(k_tri1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return occupancy_grid((const void*)k_tri1<true>, smem);
+  }
+  cudaFuncSetAttribute(k_tri1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return occupancy_grid((const void*)k_tri1<false>, smem);
+}
+
+size_t tri1_gbm_bytes(int dpmax) {
+  if (dpmax < 2 || tri1_bitmap_fits_smem(dpmax)) return 0;
+  const size_t W = (size_t)(dpmax + 31) / 32;
+  return (size_t)tri1_grid(dpmax, false) * (size_t)dpmax * W * 4;
+}
+
+cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
+                        int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm, u64* work_ctr,
+                        int* err, cudaStream_t st) {
+  if (dpmax < 2) return cudaSuccess;
+  const bool smem_bm = tri1_bitmap_fits_smem(dpmax);
+  const size_t smem = tri1_smem_impl(dpmax, smem_bm);
+  const int grid = tri1_grid(dpmax, smem_bm);
+  const int hb = hash_bits_for(dpmax);
+  if (smem_bm)
+    k_tri1<true><<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, C3o, c3r, k4r, nullptr, work_ctr,
+                                            err);
+  else
+    k_tri1<false><<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, C3o, c3r, k4r, gbm, work_ctr, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
+                        int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st) {
+  if (dpmax < 2) return cudaSuccess;
+  const size_t smem = tri2_smem_bytes(dpmax);
+  if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
+  cudaFuncSetAttribute(k_tri2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int grid = occupancy_grid((const void*)k_tri2, smem);
+  k_tri2<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hash_bits_for(dpmax), C3o, r13r, err);
+  return cudaGetLastError();
+}
+
+}  // namespace fglt
