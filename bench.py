@@ -41,6 +41,9 @@ WORKLOADS = {
     "rmat-s20-ef16": dict(kind="rmat", scale=20, ef=16, seed=0,
                           desc="R-MAT scale 20, edge factor 16, a=.57 b=.19 c=.19, seed 0, permuted, "
                                "symmetric simple CSR, int32 colidx, int64 rowptr"),
+    "rmat-s18-ef16": dict(kind="rmat", scale=18, ef=16, seed=0,
+                          desc="R-MAT scale 18, edge factor 16, a=.57 b=.19 c=.19, seed 0, permuted, "
+                               "symmetric simple CSR (profiling size)"),
     "er-2000-d10": dict(kind="er", n=2000, deg=10, seed=0,
                         desc="Erdos-Renyi G(n=2000, avg degree 10), seed 0, symmetric simple CSR"),
 }

@@ -77,6 +77,11 @@ typedef struct {
     /* 1: record CUDA events around every stage of each transform so that
      * fglt_stage_times can report per-stage device time. */
     int profile_stages;
+    /* Tuning: number of top-ranked (highest-degree) vertices that get dense
+     * shared-memory counters in the 4-cycle stage. 0 selects the largest span
+     * that fits (32768, or 16384 when some degree is >= 65536); smaller values
+     * move work to the hash-table paths. Results do not depend on it. */
+    int cyc_hub_span;
 } fglt_options;
 
 /* Fills *opt with the defaults (all fields 0 = automatic). */

@@ -48,6 +48,7 @@ class fglt_options(ctypes.Structure):
         ("serve_max_batch", ctypes.c_int),
         ("serve_max_queue", ctypes.c_int),
         ("profile_stages", ctypes.c_int),
+        ("cyc_hub_span", ctypes.c_int),
     ]
 
 
@@ -254,8 +255,10 @@ class Handle:
     """Owns one fglt_t."""
 
     def __init__(self, device: int = 0, validate: bool = False, profile_stages: bool = False,
-                 serve_memory_budget: int = 0, serve_max_batch: int = 0, serve_max_queue: int = 0):
+                 serve_memory_budget: int = 0, serve_max_batch: int = 0, serve_max_queue: int = 0,
+                 cyc_hub_span: int = 0):
         opt = fglt_options_default()
+        opt.cyc_hub_span = int(cyc_hub_span)
         opt.validate = int(validate)
         opt.profile_stages = int(profile_stages)
         opt.serve_memory_budget = int(serve_memory_budget)

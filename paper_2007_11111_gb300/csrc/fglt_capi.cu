@@ -27,18 +27,19 @@ struct Buf {
 enum BufId {
   B_D, B_HEAVY, B_CNT, B_HIST, B_BASE, B_CURSOR, B_RANK, B_PERM, B_DR, B_OPC, B_ORP, B_SCAN, B_OCOL, B_OCUR,
   B_SORT, B_TWORK, B_C3O, B_C3R, B_K4R, B_R10R, B_R14R, B_R13R, B_R12R, B_C3OO, B_P2, B_P3, B_R7, B_R9, B_WC,
-  B_LS, B_LG, B_GBM, B_GKEYS, B_GCNT,
+  B_LS, B_WCN, B_GBM, B_GKEYS, B_GCNT,
   B_H_ROWPTR, B_H_COLIDX, B_H_RAW, B_H_NET, B_BATCH_OFF, B_CTR64,
   B_COUNT
 };
 
 // Small device counters, one int slot each.
 enum CounterId {
-  C_DMAX, C_NHEAVY, C_DPMAX, C_NTRI, C_NEXT1, C_NEXT2, C_NCYC_S, C_NCYC_G, C_NEXT3, C_NEXT4, C_ERR, C_NUM
+  C_DMAX, C_NHEAVY, C_DPMAX, C_NTRI, C_NEXT1, C_NEXT2, C_NCYC0, C_NCYC1, C_NCYC2, C_NEXTC0, C_NEXTC1,
+  C_NEXTC2, C_ERR, C_NUM
 };
 // 64-bit work counters: triangle-pass scanned entries, triangles, 4-cliques,
 // max and total wedges of the 4-cycle stage.
-enum Counter64Id { W_PROBES, W_TRIANGLES, W_K4, W_WMAX, W_WSUM, W_NUM };
+enum Counter64Id { W_PROBES, W_TRIANGLES, W_K4, W_WMAX, W_WSUM, W_GCAP, W_NUM };
 
 // Host copy of the last transform's work counters (fglt_work_counters order).
 enum WorkOut { O_N, O_NNZ, O_M, O_DMAX, O_DPMAX, O_PROBES, O_TRIANGLES, O_K4, O_WEDGES, O_WMAX, O_NUM };
@@ -298,37 +299,51 @@ fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out
 
   // 4-cycles.
   mark(9);
-  int64_t* wc;
+  int64_t *wc, *wcn;
   NEED(B_WC, n, wc);
-  u64* wmax_dev = ctr + W_WMAX;
-  CK(launch_wedge_count(g, rank, orp, ocol, heavy, cnt + C_NHEAVY, heavy_cap, wc, wmax_dev, ctr + W_WSUM, st));
-  u64 wmax = 0;
+  NEED(B_WCN, n, wcn);
+  const bool c16 = dmax < 65536;
+  int64_t span = cyc_dense_span(c16);
+  if (h->opt.cyc_hub_span > 0) span = std::min<int64_t>(span, h->opt.cyc_hub_span);
+  const int32_t hub_lo = (int32_t)std::max<int64_t>(0, n - span);
+  CK(launch_wedge_count(g, rank, orp, ocol, heavy, cnt + C_NHEAVY, heavy_cap, hub_lo, wc, wcn, ctr + W_WMAX,
+                        ctr + W_WSUM, st));
+  int32_t* lists;
+  NEED(B_LS, 3 * n, lists);
+  CK(launch_cyc_worklists(wc, wcn, n, lists, n, cnt + C_NCYC0, ctr + W_GCAP, st));
+  int32_t n_gmem = 0;
+  u64 gcap = 0;
   {
-    fglt_status s = read_scalar(h, st, wmax_dev, &wmax);
+    fglt_status s = read_scalar(h, st, cnt + C_NCYC2, &n_gmem);
+    if (s == FGLT_OK) s = read_scalar(h, st, ctr + W_GCAP, &gcap);
     if (s != FGLT_OK) return s;
   }
   mark(10);
   u64* r12r;
   NEED(B_R12R, n, r12r);
   CK(cudaMemsetAsync(r12r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
-  if (wmax >= 2) {
-    int32_t *ls, *lg;
-    NEED(B_LS, n, ls);
-    NEED(B_LG, n, lg);
-    const int64_t smem_cap = 1LL << (cyc_smem_hash_bits() - 1);
-    CK(launch_cyc_worklists(wc, n, smem_cap, ls, cnt + C_NCYC_S, lg, cnt + C_NCYC_G, st));
-    CK(launch_cyc(g, rank, perm, orp, ocol, wc, ls, cnt + C_NCYC_S, cnt + C_NEXT3, false, 0, nullptr, nullptr,
-                  r12r, err, st));
-    const int64_t gcap = std::min<int64_t>((int64_t)wmax, n);
-    if (gcap > smem_cap) {
-      const int gbits = bits_for(gcap);
-      const size_t slots = (size_t)cyc_grid_blocks_gmem() << gbits;
-      uint32_t *gkeys, *gcnt;
-      NEED(B_GKEYS, (int64_t)slots, gkeys);
-      NEED(B_GCNT, (int64_t)slots, gcnt);
-      CK(launch_cyc(g, rank, perm, orp, ocol, wc, lg, cnt + C_NCYC_G, cnt + C_NEXT4, true, gbits, gkeys, gcnt,
-                    r12r, err, st));
+  {
+    CycArgs ca{};
+    ca.rank = rank;
+    ca.perm = perm;
+    ca.orp = orp;
+    ca.ocol = ocol;
+    ca.wc = wc;
+    ca.lists = lists;
+    ca.list_stride = n;
+    ca.counts = cnt + C_NCYC0;
+    ca.next = cnt + C_NEXTC0;
+    ca.c16 = c16;
+    ca.hub_lo = hub_lo;
+    ca.r12r = r12r;
+    ca.err = err;
+    if (n_gmem > 0) {
+      ca.gbits = bits_for((int64_t)gcap);
+      const size_t slots = (size_t)cyc_gmem_blocks() << ca.gbits;
+      NEED(B_GKEYS, (int64_t)slots, ca.gkeys);
+      NEED(B_GCNT, (int64_t)slots, ca.gcnt);
     }
+    CK(launch_cyc(g, ca, st));
   }
 
   // Table I + U16^{-1}.

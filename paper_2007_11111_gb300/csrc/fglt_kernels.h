@@ -83,20 +83,38 @@ cudaError_t launch_unrank_u64(const u64* src_r, const int32_t* perm, int64_t n, 
                               cudaStream_t st);
 
 // --- 4-cycles (rank space) ---------------------------------------------------
-// wc[rank w] = wedges of w; *wmax = max, *wsum = total.
+// wc[rank w] = wedges w - v - u (u in N+(v), u > w); wcn[rank w] = those with
+// u < hub_lo; *wmax = max wc, *wsum = total wedges.
 cudaError_t launch_wedge_count(const Csr& g, const int32_t* rank, const int64_t* orp, const int32_t* ocol,
-                               const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap,
-                               int64_t* wc, u64* wmax, u64* wsum, cudaStream_t st);
-// Splits vertices with wedges into the shared-memory list and the global-memory list.
-cudaError_t launch_cyc_worklists(const int64_t* wc, int64_t n, int64_t smem_cap, int32_t* list_s,
-                                 int32_t* cnt_s, int32_t* list_g, int32_t* cnt_g, cudaStream_t st);
-int cyc_smem_hash_bits();
-int cyc_grid_blocks_smem();
-int cyc_grid_blocks_gmem();
-cudaError_t launch_cyc(const Csr& g, const int32_t* rank, const int32_t* perm, const int64_t* orp,
-                       const int32_t* ocol, const int64_t* wc, const int32_t* list, const int32_t* cnt,
-                       int* next, bool gmem, int gbits, uint32_t* gkeys, uint32_t* gcnt, u64* r12r,
-                       int* err, cudaStream_t st);
+                               const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap, int32_t hub_lo,
+                               int64_t* wc, int64_t* wcn, u64* wmax, u64* wsum, cudaStream_t st);
+// Dense counter span of the heavy-vertex kernel (16-bit counters when every
+// degree is below 65536, else 32-bit).
+int cyc_dense_span(bool c16);
+int cyc_gmem_blocks();
+// Splits the vertices with at least two wedges into three classes (lists at
+// lists + c * list_stride, counts[c]); *gcap_max = largest table need of class 2.
+cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, int64_t n, int32_t* lists,
+                                 int64_t list_stride, int32_t* counts, u64* gcap_max, cudaStream_t st);
+struct CycArgs {
+  const int32_t* rank;
+  const int32_t* perm;
+  const int64_t* orp;
+  const int32_t* ocol;
+  const int64_t* wc;
+  const int32_t* lists;
+  int64_t list_stride;
+  const int32_t* counts;  // 3 class sizes
+  int* next;              // 3 scheduling counters (zeroed)
+  bool c16;
+  int32_t hub_lo;
+  int gbits;              // class-2 tables: cyc_gmem_blocks() << gbits slots each array
+  uint32_t* gkeys;        // NULL when class 2 is empty
+  uint32_t* gcnt;
+  u64* r12r;
+  int* err;
+};
+cudaError_t launch_cyc(const Csr& g, const CycArgs& a, cudaStream_t st);
 
 // --- epilogue ------------------------------------------------------------------
 struct EpilogueIn {

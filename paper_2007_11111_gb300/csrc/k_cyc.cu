@@ -3,17 +3,25 @@
 // The paper's formula is c4 = C4,2 e / 2 with C4,2 = P2 o (P2 - 1) (Lemma on
 // c4): for every vertex i, c4(i) = sum over l != i of binom(P2(i,l), 2), i.e.
 // every 4-cycle through i is counted once via its vertex l opposite to i.
-// Forming the P2 rows costs sum_k d_k^2 (Lemma 1). This kernel reaches the
-// same integers by enumerating each 4-cycle once from its bottom-opposite pair:
-// every 4-cycle has a unique top vertex u (highest rank) and u's opposite w;
-// the two other vertices v, v' are common neighbours of u and w below u.
-// For a vertex w, the wedges w - v - u with u in N+(v) and u above w are
-// counted per u in a hash table (cnt[u] = number of such v). Then, for the
-// pair (u, w), binom(cnt[u], 2) cycles have top u and bottom w; each of u and w
-// gains that many cycles, and each middle v gains cnt[u] - 1 (one per other
-// middle). Summed over all w this is exactly C4,2 e / 2 per vertex; the work
-// is sum_v d_v * d+_v instead of sum_k d_k^2 (degree orientation, as in the
-// cost analysis of Appendix A).
+// Forming the P2 rows costs sum_k d_k^2 (Lemma 1). These kernels reach the
+// same integers by enumerating each 4-cycle once: every 4-cycle has a unique
+// top vertex u (highest rank) and u's opposite w; the two other vertices v, v'
+// are common neighbours of u and w below u. For a vertex w, the wedges
+// w - v - u with u in N+(v) and u above w are counted per u (cnt[u] = number
+// of such v). Then binom(cnt[u], 2) cycles have top u and bottom w; each of u
+// and w gains that many, and each middle v gains cnt[u] - 1 (one per other
+// middle). Summed over all w this is C4,2 e / 2 per vertex; the work is the
+// number of such wedges, at most sum_v d_v d+_v (degree orientation, the cost
+// model of Appendix A), instead of sum_k d_k^2.
+//
+// Counters per w live in
+//  - a per-warp shared-memory hash table (vertices with few wedges),
+//  - a dense shared-memory array over the top-ranked ("hub") vertices plus a
+//    small shared-memory hash table for the other tops (most wedges of a
+//    power-law graph end at a hub),
+//  - or a global-memory hash table (fallback).
+// Wedges are walked warp-cooperatively: 32 middles v at a time, their
+// segments of N+(v) concatenated and split evenly over the lanes.
 #include "fglt_device.cuh"
 #include "fglt_kernels.h"
 
@@ -21,8 +29,13 @@ namespace fglt {
 
 namespace {
 
-constexpr int CYC_T = 256;
-constexpr int SMEM_BITS = 13;  // 8192 slots x (key, count) = 64 KB
+constexpr int WARP_HASH = 1024;   // slots per warp table
+constexpr int WARP_CAP = 512;     // most wedges handled by one warp table
+constexpr int WARP_T = 256;
+constexpr int DENSE_T = 512;
+constexpr int DENSE_WORDS = 16384;  // 64 KB of counters
+constexpr int DHASH_BITS = 12;      // 4096-slot table for the non-hub tops
+constexpr int GMEM_T = 512;
 
 int num_sms() {
   int dev = 0, sms = 1;
@@ -82,27 +95,242 @@ struct Table {
   }
 };
 
-template <typename RP, bool GMEM>
-__global__ void __launch_bounds__(CYC_T) k_cyc(const RP* __restrict__ rp, const int32_t* __restrict__ ci,
-                                               const int32_t* __restrict__ rank, const int32_t* __restrict__ perm,
-                                               const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
-                                               const int64_t* __restrict__ wc, const int32_t* __restrict__ list,
-                                               const int32_t* __restrict__ cnt, int* next, int gbits,
-                                               uint32_t* gkeys, uint32_t* gcnt, u64* r12r, int64_t n, int* err) {
+// One group of up to 32 middles v = colidx[k0 .. k0+32) of w: each lane owns
+// one v and its segment of N+(v) above w; the concatenated segments are split
+// over the lanes. f(u, owner_lane) is called for every wedge.
+struct Group {
+  int32_t rv;     // rank of this lane's v (-1 if none)
+  int64_t st;     // segment start in ocol
+  int64_t excl;   // exclusive prefix of segment lengths
+  int64_t total;  // wedges in the group
+};
+
+__device__ __forceinline__ Group make_group(const int32_t* __restrict__ ci, const int32_t* __restrict__ rank,
+                                            const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                            int64_t k, int64_t e, int32_t w, int64_t n, int lane) {
+  Group g;
+  g.rv = -1;
+  g.st = 0;
+  int64_t len = 0;
+  if (k < e) {
+    const int32_t v = __ldg(ci + k);
+    if ((uint32_t)v < (uint64_t)n) {
+      g.rv = __ldg(rank + v);
+      const int64_t ob = __ldg(orp + g.rv), oe = __ldg(orp + g.rv + 1);
+      g.st = upper_bound_i32(ocol, ob, oe, w);
+      len = oe - g.st;
+    }
+  }
+  int64_t incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  g.excl = incl - len;
+  g.total = __shfl_sync(0xffffffffu, incl, 31);
+  return g;
+}
+
+template <typename F>
+__device__ __forceinline__ void walk_group(const Group& g, const int32_t* __restrict__ ocol, int lane, F f) {
+  for (int64_t t0 = 0; t0 < g.total; t0 += 32) {
+    const int64_t t = t0 + lane;
+    // owner = last lane whose exclusive prefix is <= t (prefixes are non-decreasing)
+    int j = 0;
+#pragma unroll
+    for (int b = 16; b >= 1; b >>= 1) {
+      const int64_t p = __shfl_sync(0xffffffffu, g.excl, j + b);
+      if (p <= t) j += b;
+    }
+    const int64_t ost = __shfl_sync(0xffffffffu, g.st, j);
+    const int64_t oex = __shfl_sync(0xffffffffu, g.excl, j);
+    if (t < g.total) f((uint32_t)__ldg(ocol + ost + (t - oex)), j);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small vertices: one warp per w, a 1024-slot hash table per warp.
+// ---------------------------------------------------------------------------
+template <typename RP>
+__global__ void __launch_bounds__(WARP_T) k_cyc_warp(const RP* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                     const int32_t* __restrict__ rank, const int32_t* __restrict__ perm,
+                                                     const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                                     const int64_t* __restrict__ wc, const int32_t* __restrict__ list,
+                                                     const int32_t* __restrict__ cnt, int* next, u64* r12r, int64_t n,
+                                                     int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u64* acc = reinterpret_cast<u64*>(smem) + warp * 32;
+  uint32_t* tables = reinterpret_cast<uint32_t*>(reinterpret_cast<u64*>(smem) + (WARP_T / 32) * 32);
+  Table<false> T{tables + (size_t)warp * 2 * WARP_HASH, tables + (size_t)warp * 2 * WARP_HASH + WARP_HASH};
+  const int total = *cnt;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(next, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    const int32_t w = list[item];
+    int64_t cap = wc[w];
+    if (cap > n - 1 - w) cap = n - 1 - w;
+    int hb = 5;
+    while ((1LL << hb) < 2 * cap) ++hb;
+    const uint32_t H = 1u << hb;
+    for (uint32_t i = lane; i < H; i += 32) T.clear(i);
+    acc[lane] = 0;
+    __syncwarp();
+    const int64_t wo = perm[w];
+    const int64_t s = (int64_t)rp[wo], e = (int64_t)rp[wo + 1];
+    for (int64_t k0 = s; k0 < e; k0 += 32) {
+      const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
+      walk_group(g, ocol, lane, [&](uint32_t u, int) { T.increment(u, hb, err); });
+    }
+    __syncwarp();
+    for (int64_t k0 = s; k0 < e; k0 += 32) {
+      const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
+      walk_group(g, ocol, lane, [&](uint32_t u, int j) {
+        const uint32_t c = T.count_of(u, hb);
+        if (c > 1) atomicAdd(&acc[j], (u64)(c - 1));
+      });
+      __syncwarp();
+      if (acc[lane]) {
+        atomicAdd(&r12r[g.rv], acc[lane]);
+        acc[lane] = 0;
+      }
+      __syncwarp();
+    }
+    u64 accw = 0;
+    for (uint32_t i = lane; i < H; i += 32) {
+      const uint32_t key = T.load_key(i);
+      if (key != EMPTY_KEY) {
+        const u64 c = T.load_cnt(i);
+        if (c >= 2) {
+          const u64 v = c * (c - 1) / 2;
+          atomicAdd(&r12r[key], v);
+          accw += v;
+        }
+      }
+    }
+    accw = warp_sum_u64(accw);
+    if (lane == 0 && accw) atomicAdd(&r12r[w], accw);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Heavy vertices: one block per w. Tops u >= hub_lo count in a dense array
+// (16-bit or 32-bit counters), the others in a 4096-slot hash table.
+// ---------------------------------------------------------------------------
+template <typename RP, bool C16>
+__global__ void __launch_bounds__(DENSE_T) k_cyc_dense(const RP* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                       const int32_t* __restrict__ rank,
+                                                       const int32_t* __restrict__ perm,
+                                                       const int64_t* __restrict__ orp,
+                                                       const int32_t* __restrict__ ocol,
+                                                       const int32_t* __restrict__ list,
+                                                       const int32_t* __restrict__ cnt, int* next, u64* r12r,
+                                                       int64_t n, int32_t hub_lo, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* dense = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* hkeys = dense + DENSE_WORDS;
+  uint32_t* hcnts = hkeys + (1 << DHASH_BITS);
+  u64* sacc = reinterpret_cast<u64*>(hcnts + (1 << DHASH_BITS));
   __shared__ int s_item;
   __shared__ u64 red[32];
-  Table<GMEM> T;
-  if (GMEM) {
-    T.keys = gkeys + ((size_t)blockIdx.x << gbits);
-    T.cnts = gcnt + ((size_t)blockIdx.x << gbits);
-  } else {
-    T.keys = reinterpret_cast<uint32_t*>(smem);
-    T.cnts = T.keys + (1 << SMEM_BITS);
-  }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  Table<false> T{hkeys, hcnts};
+  u64* acc = sacc + warp * 32;
   const int total = *cnt;
+  const int hub_n = (int)(n - hub_lo);  // number of dense counters in use
 
+  auto add = [&](uint32_t u) {
+    const uint32_t i = u - (uint32_t)hub_lo;
+    if (C16) atomicAdd(&dense[i >> 1], 1u << ((i & 1u) << 4));
+    else atomicAdd(&dense[i], 1u);
+  };
+  auto get = [&](uint32_t u) -> uint32_t {
+    const uint32_t i = u - (uint32_t)hub_lo;
+    if (C16) return (dense[i >> 1] >> ((i & 1u) << 4)) & 0xFFFFu;
+    return dense[i];
+  };
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    const int32_t w = list[item];
+    const int words = C16 ? (hub_n + 1) >> 1 : hub_n;
+    for (int i = tid; i < words; i += blockDim.x) dense[i] = 0u;
+    for (int i = tid; i < (1 << DHASH_BITS); i += blockDim.x) T.clear(i);
+    if (tid < nwarps * 32) sacc[tid] = 0;
+    __syncthreads();
+    const int64_t wo = perm[w];
+    const int64_t s = (int64_t)rp[wo], e = (int64_t)rp[wo + 1];
+    for (int64_t k0 = s + warp * 32; k0 < e; k0 += nwarps * 32) {
+      const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
+      walk_group(g, ocol, lane, [&](uint32_t u, int) {
+        if ((int32_t)u >= hub_lo) add(u);
+        else T.increment(u, DHASH_BITS, err);
+      });
+    }
+    __syncthreads();
+    for (int64_t k0 = s + warp * 32; k0 < e; k0 += nwarps * 32) {
+      const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
+      walk_group(g, ocol, lane, [&](uint32_t u, int j) {
+        const uint32_t c = (int32_t)u >= hub_lo ? get(u) : T.count_of(u, DHASH_BITS);
+        if (c > 1) atomicAdd(&acc[j], (u64)(c - 1));
+      });
+      __syncwarp();
+      if (acc[lane]) {
+        atomicAdd(&r12r[g.rv], acc[lane]);
+        acc[lane] = 0;
+      }
+      __syncwarp();
+    }
+    u64 accw = 0;
+    for (int i = tid; i < hub_n; i += blockDim.x) {
+      const u64 c = get((uint32_t)(hub_lo + i));
+      if (c >= 2) {
+        const u64 v = c * (c - 1) / 2;
+        atomicAdd(&r12r[hub_lo + i], v);
+        accw += v;
+      }
+    }
+    for (int i = tid; i < (1 << DHASH_BITS); i += blockDim.x) {
+      const uint32_t key = T.load_key(i);
+      if (key != EMPTY_KEY) {
+        const u64 c = T.load_cnt(i);
+        if (c >= 2) {
+          const u64 v = c * (c - 1) / 2;
+          atomicAdd(&r12r[key], v);
+          accw += v;
+        }
+      }
+    }
+    accw = block_sum(accw, red);
+    if (tid == 0 && accw) atomicAdd(&r12r[w], accw);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fallback: one block per w, hash table in global memory.
+// ---------------------------------------------------------------------------
+template <typename RP>
+__global__ void __launch_bounds__(GMEM_T) k_cyc_gmem(const RP* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                     const int32_t* __restrict__ rank, const int32_t* __restrict__ perm,
+                                                     const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                                     const int64_t* __restrict__ wc, const int32_t* __restrict__ list,
+                                                     const int32_t* __restrict__ cnt, int* next, int gbits,
+                                                     uint32_t* gkeys, uint32_t* gcnt, u64* r12r, int64_t n, int* err) {
+  __shared__ int s_item;
+  __shared__ u64 red[32];
+  __shared__ u64 sacc[GMEM_T];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  Table<true> T{gkeys + ((size_t)blockIdx.x << gbits), gcnt + ((size_t)blockIdx.x << gbits)};
+  u64* acc = sacc + warp * 32;
+  const int total = *cnt;
   for (;;) {
     if (tid == 0) s_item = atomicAdd(next, 1);
     __syncthreads();
@@ -115,33 +343,28 @@ __global__ void __launch_bounds__(CYC_T) k_cyc(const RP* __restrict__ rp, const 
     while ((1LL << hb) < 2 * cap) ++hb;
     const uint32_t H = 1u << hb;
     for (uint32_t i = tid; i < H; i += blockDim.x) T.clear(i);
+    sacc[tid] = 0;
     __syncthreads();
-
     const int64_t wo = perm[w];
     const int64_t s = (int64_t)rp[wo], e = (int64_t)rp[wo + 1];
-    // Pass A: count wedges w - v - u per top vertex u.
-    for (int64_t k = s + warp; k < e; k += nwarps) {
-      const int32_t v = ci[k];
-      if ((uint32_t)v >= (uint64_t)n) continue;
-      const int32_t rv = rank[v];
-      const int64_t ob = orp[rv], oe = orp[rv + 1];
-      const int64_t st = upper_bound_i32(ocol, ob, oe, w);
-      for (int64_t q = st + lane; q < oe; q += 32) T.increment((uint32_t)ocol[q], hb, err);
+    for (int64_t k0 = s + warp * 32; k0 < e; k0 += nwarps * 32) {
+      const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
+      walk_group(g, ocol, lane, [&](uint32_t u, int) { T.increment(u, hb, err); });
     }
     __syncthreads();
-    // Pass B: every middle v of a wedge gains cnt[u] - 1.
-    for (int64_t k = s + warp; k < e; k += nwarps) {
-      const int32_t v = ci[k];
-      if ((uint32_t)v >= (uint64_t)n) continue;
-      const int32_t rv = rank[v];
-      const int64_t ob = orp[rv], oe = orp[rv + 1];
-      const int64_t st = upper_bound_i32(ocol, ob, oe, w);
-      long long sum = 0;
-      for (int64_t q = st + lane; q < oe; q += 32) sum += (long long)T.count_of((uint32_t)ocol[q], hb) - 1;
-      sum = warp_sum_i64(sum);
-      if (lane == 0 && sum) atomicAdd(&r12r[rv], (u64)sum);
+    for (int64_t k0 = s + warp * 32; k0 < e; k0 += nwarps * 32) {
+      const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
+      walk_group(g, ocol, lane, [&](uint32_t u, int j) {
+        const uint32_t c = T.count_of(u, hb);
+        if (c > 1) atomicAdd(&acc[j], (u64)(c - 1));
+      });
+      __syncwarp();
+      if (acc[lane]) {
+        atomicAdd(&r12r[g.rv], acc[lane]);
+        acc[lane] = 0;
+      }
+      __syncwarp();
     }
-    // Pass C: top u and bottom w gain binom(cnt[u], 2) each.
     u64 accw = 0;
     for (uint32_t i = tid; i < H; i += blockDim.x) {
       const uint32_t key = T.load_key(i);
@@ -160,76 +383,91 @@ __global__ void __launch_bounds__(CYC_T) k_cyc(const RP* __restrict__ rp, const 
   }
 }
 
-__global__ void k_cyc_worklists(const int64_t* __restrict__ wc, int64_t n, int64_t smem_cap, int32_t* list_s,
-                                int32_t* cnt_s, int32_t* list_g, int32_t* cnt_g) {
+// Vertex classes: 0 = warp table, 1 = dense + shared hash, 2 = global hash.
+__global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* __restrict__ wcn, int64_t n,
+                                int32_t* lists, int64_t list_stride, int32_t* counts, u64* gcap_max) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < n; r0 += stride) {
     const int64_t r = r0 + lane;
+    int cls = -1;
     int64_t cap = 0;
-    if (r < n) {
+    if (r < n && wc[r] >= 2) {
       cap = wc[r];
       if (cap > n - 1 - r) cap = n - 1 - r;
+      if (wc[r] <= WARP_CAP) cls = 0;
+      else if (wcn[r] <= (1 << (DHASH_BITS - 1))) cls = 1;
+      else cls = 2;
     }
-    const bool take = r < n && wc[r] >= 2;
-    const bool small = cap <= smem_cap;
-    const unsigned ms = __ballot_sync(0xffffffffu, take && small);
-    const unsigned mg = __ballot_sync(0xffffffffu, take && !small);
-    int ps = 0, pg = 0;
-    if (lane == 0) {
-      if (ms) ps = atomicAdd(cnt_s, __popc(ms));
-      if (mg) pg = atomicAdd(cnt_g, __popc(mg));
+    if (cls == 2) atomicMax(gcap_max, (u64)cap);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const unsigned m = __ballot_sync(0xffffffffu, cls == c);
+      int pos = 0;
+      if (lane == 0 && m) pos = atomicAdd(&counts[c], __popc(m));
+      pos = __shfl_sync(0xffffffffu, pos, 0);
+      if (cls == c) lists[c * list_stride + pos + __popc(m & ((1u << lane) - 1))] = (int32_t)r;
     }
-    ps = __shfl_sync(0xffffffffu, ps, 0);
-    pg = __shfl_sync(0xffffffffu, pg, 0);
-    const unsigned below = (1u << lane) - 1;
-    if (take && small) list_s[ps + __popc(ms & below)] = (int32_t)r;
-    if (take && !small) list_g[pg + __popc(mg & below)] = (int32_t)r;
   }
 }
 
+int occupancy(const void* fn, int threads, size_t smem) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  return per_sm < 1 ? 1 : per_sm;
+}
+
+size_t dense_smem() {
+  return (size_t)DENSE_WORDS * 4 + (size_t)(1 << DHASH_BITS) * 8 + (size_t)(DENSE_T / 32) * 32 * 8;
+}
+
 template <typename RP>
-cudaError_t launch_cyc_rp(const Csr& g, const int32_t* rank, const int32_t* perm, const int64_t* orp,
-                          const int32_t* ocol, const int64_t* wc, const int32_t* list, const int32_t* cnt, int* next,
-                          bool gmem, int gbits, uint32_t* gkeys, uint32_t* gcnt, u64* r12r, int* err,
-                          cudaStream_t st) {
+cudaError_t launch_rp(const Csr& g, const CycArgs& a, cudaStream_t st) {
   const RP* rp = static_cast<const RP*>(g.rowptr);
-  if (gmem) {
-    k_cyc<RP, true><<<cyc_grid_blocks_gmem(), CYC_T, 0, st>>>(rp, g.colidx, rank, perm, orp, ocol, wc, list, cnt,
-                                                               next, gbits, gkeys, gcnt, r12r, g.n, err);
+  const int sms = num_sms();
+  const size_t wsmem = (size_t)(WARP_T / 32) * (32 * 8 + 2 * WARP_HASH * 4);
+  cudaFuncSetAttribute(k_cyc_warp<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
+  k_cyc_warp<RP><<<sms * occupancy((const void*)k_cyc_warp<RP>, WARP_T, wsmem), WARP_T, wsmem, st>>>(
+      rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc, a.lists, a.counts, a.next + 0, a.r12r, g.n, a.err);
+  const size_t smem = dense_smem();
+  if (a.c16) {
+    cudaFuncSetAttribute(k_cyc_dense<RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = sms * occupancy((const void*)k_cyc_dense<RP, true>, DENSE_T, smem);
+    k_cyc_dense<RP, true><<<grid, DENSE_T, smem, st>>>(rp, g.colidx, a.rank, a.perm, a.orp, a.ocol,
+                                                       a.lists + a.list_stride, a.counts + 1, a.next + 1, a.r12r,
+                                                       g.n, a.hub_lo, a.err);
   } else {
-    const size_t smem = (size_t)8 << SMEM_BITS;
-    cudaFuncSetAttribute(k_cyc<RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cyc<RP, false><<<cyc_grid_blocks_smem(), CYC_T, smem, st>>>(rp, g.colidx, rank, perm, orp, ocol, wc, list,
-                                                                   cnt, next, 0, nullptr, nullptr, r12r, g.n, err);
+    cudaFuncSetAttribute(k_cyc_dense<RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = sms * occupancy((const void*)k_cyc_dense<RP, false>, DENSE_T, smem);
+    k_cyc_dense<RP, false><<<grid, DENSE_T, smem, st>>>(rp, g.colidx, a.rank, a.perm, a.orp, a.ocol,
+                                                        a.lists + a.list_stride, a.counts + 1, a.next + 1, a.r12r,
+                                                        g.n, a.hub_lo, a.err);
+  }
+  if (a.gkeys) {
+    k_cyc_gmem<RP><<<cyc_gmem_blocks(), GMEM_T, 0, st>>>(rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc,
+                                                         a.lists + 2 * a.list_stride, a.counts + 2, a.next + 2,
+                                                         a.gbits, a.gkeys, a.gcnt, a.r12r, g.n, a.err);
   }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int cyc_smem_hash_bits() { return SMEM_BITS; }
-int cyc_grid_blocks_smem() { return num_sms() * 3; }
-int cyc_grid_blocks_gmem() { return num_sms(); }
+int cyc_dense_span(bool c16) { return c16 ? 2 * DENSE_WORDS : DENSE_WORDS; }
+int cyc_gmem_blocks() { return num_sms(); }
 
-cudaError_t launch_cyc_worklists(const int64_t* wc, int64_t n, int64_t smem_cap, int32_t* list_s, int32_t* cnt_s,
-                                 int32_t* list_g, int32_t* cnt_g, cudaStream_t st) {
+cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, int64_t n, int32_t* lists,
+                                 int64_t list_stride, int32_t* counts, u64* gcap_max, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int64_t blocks = (n + 255) / 256;
   if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
-  k_cyc_worklists<<<(unsigned)blocks, 256, 0, st>>>(wc, n, smem_cap, list_s, cnt_s, list_g, cnt_g);
+  k_cyc_worklists<<<(unsigned)blocks, 256, 0, st>>>(wc, wcn, n, lists, list_stride, counts, gcap_max);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cyc(const Csr& g, const int32_t* rank, const int32_t* perm, const int64_t* orp,
-                       const int32_t* ocol, const int64_t* wc, const int32_t* list, const int32_t* cnt, int* next,
-                       bool gmem, int gbits, uint32_t* gkeys, uint32_t* gcnt, u64* r12r, int* err,
-                       cudaStream_t st) {
+cudaError_t launch_cyc(const Csr& g, const CycArgs& a, cudaStream_t st) {
   if (g.n <= 0) return cudaSuccess;
-  return g.rp64 ? launch_cyc_rp<int64_t>(g, rank, perm, orp, ocol, wc, list, cnt, next, gmem, gbits, gkeys, gcnt,
-                                         r12r, err, st)
-                : launch_cyc_rp<int32_t>(g, rank, perm, orp, ocol, wc, list, cnt, next, gmem, gbits, gkeys, gcnt,
-                                         r12r, err, st);
+  return g.rp64 ? launch_rp<int64_t>(g, a, st) : launch_rp<int32_t>(g, a, st);
 }
 
 }  // namespace fglt

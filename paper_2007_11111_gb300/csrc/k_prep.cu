@@ -189,18 +189,23 @@ struct WedgeCountOp {
   const int64_t* orp;
   const int32_t* ocol;
   int64_t* wc;
+  int64_t* wcn;
   u64* wmax;
   u64* wsum;
   int64_t n;
+  int32_t hub_lo;
   __device__ __forceinline__ void edge(int64_t v, int32_t j, int64_t, int64_t, int64_t, long long& a,
-                                       long long&) const {
+                                       long long& b) const {
     if ((uint32_t)j >= (uint64_t)n) return;
     const int32_t rw = __ldg(rank + v), rv = __ldg(rank + j);
     const int64_t ob = __ldg(orp + rv), oe = __ldg(orp + rv + 1);
-    a += oe - upper_bound_i32(ocol, ob, oe, rw);
+    const int64_t st = upper_bound_i32(ocol, ob, oe, rw);
+    a += oe - st;
+    if (rw + 1 < hub_lo) b += upper_bound_i32(ocol, st, oe, hub_lo - 1) - st;
   }
-  __device__ __forceinline__ void done(int64_t v, long long a, long long) const {
+  __device__ __forceinline__ void done(int64_t v, long long a, long long b) const {
     wc[__ldg(rank + v)] = a;
+    wcn[__ldg(rank + v)] = b;
     if (a) {
       atomicMax(wmax, (u64)a);
       atomicAdd(wsum, (u64)a);
@@ -722,9 +727,10 @@ cudaError_t launch_unrank_u64(const u64* src_r, const int32_t* perm, int64_t n, 
 }
 
 cudaError_t launch_wedge_count(const Csr& g, const int32_t* rank, const int64_t* orp, const int32_t* ocol,
-                               const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap, int64_t* wc,
-                               u64* wmax, u64* wsum, cudaStream_t st) {
-  return dispatch_rows(g, heavy, nheavy, heavy_cap, WedgeCountOp{rank, orp, ocol, wc, wmax, wsum, g.n}, st);
+                               const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap, int32_t hub_lo,
+                               int64_t* wc, int64_t* wcn, u64* wmax, u64* wsum, cudaStream_t st) {
+  return dispatch_rows(g, heavy, nheavy, heavy_cap,
+                       WedgeCountOp{rank, orp, ocol, wc, wcn, wmax, wsum, g.n, hub_lo}, st);
 }
 
 cudaError_t launch_epilogue(const EpilogueIn& in, int64_t n, int64_t* raw, int64_t* net, cudaStream_t st) {

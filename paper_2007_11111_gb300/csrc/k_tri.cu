@@ -6,13 +6,13 @@
 // (key = rank label, value = position in N+(a)). Both out-lists are sorted, so
 // the scan of N+(b) stops at the largest element of N+(a).
 //
-// Pass 1 builds, per vertex a, the adjacency bitmap of the subgraph induced on
-// N+(a) (bit (b, c) = edge b -> c) and from it
+// Pass 1 builds, per vertex a, the symmetric adjacency bitmap of the subgraph
+// G_a induced on N+(a) and from it
 //   C3(i,j) = |N(i) ∩ N(j)| per oriented edge           (Lemma 2: C3 = A o A^2)
 //   c3(i)   = triangles at i = C3 e / 2                  (Lemma 2)
 //   d^15(i) = 4-cliques at i = T e / 6, T(i,j) = q_ij^T A q_ij (Sec. 4.3):
-//             a 4-clique {a,b,c,d} (a < b < c < d) is the bit pair (b,c) with
-//             d in row(b) AND row(c).
+//             the 4-cliques {a, x, y, z} with a lowest are the triangles
+//             {x, y, z} of G_a, counted per vertex by popcounts of row ANDs.
 // Pass 2 re-lists the triangles once C3 is final and adds, for a triangle
 // {i,j,k}, C3(j,k) - 1 to i (and likewise for j and k):
 //   d^13 = D4,c e / 2 with D4,c = A o (A (C3 - A))       (Sec. 4.3)
@@ -67,6 +67,13 @@ __device__ __forceinline__ int table_find(const uint32_t* keys, const int32_t* v
 
 // ---------------------------------------------------------------------------
 // Pass 1
+//
+// S is the symmetric adjacency bitmap of the subgraph G_a induced on N+(a)
+// (row x = local neighbours of x inside N+(a)). From it, per local vertex x:
+//   popc(S_x)                      triangles {a, x, .}  -> C3(a,x), c3(x)
+//   sum_{y in S_x} popc(S_x & S_y) twice the triangles of G_a through x,
+//                                  i.e. twice the 4-cliques {a, x, ., .}
+// and a's own counts are the sums over x divided by 2 and 6.
 // ---------------------------------------------------------------------------
 template <bool SMEM_BM>
 __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
@@ -79,10 +86,7 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
   const int Hmax = 1 << Hbits, Wmax = (Dmax + 31) >> 5;
   uint32_t* keys = reinterpret_cast<uint32_t*>(smem);
   int32_t* vals = reinterpret_cast<int32_t*>(keys + Hmax);
-  int32_t* rowc = vals + Hmax;
-  int32_t* colc = rowc + Dmax;
-  uint32_t* k4c = reinterpret_cast<uint32_t*>(colc + Dmax);
-  uint32_t* bm = SMEM_BM ? (k4c + Dmax) : (gbm + (size_t)blockIdx.x * Dmax * Wmax);
+  uint32_t* bm = SMEM_BM ? reinterpret_cast<uint32_t*>(vals + Hmax) : (gbm + (size_t)blockIdx.x * Dmax * Wmax);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int total = *nwork;
 
@@ -99,7 +103,6 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
     const int W = (D + 31) >> 5;
 
     for (int i = tid; i < (1 << hb); i += blockDim.x) keys[i] = EMPTY_KEY;
-    for (int i = tid; i < D; i += blockDim.x) { rowc[i] = 0; colc[i] = 0; k4c[i] = 0; }
     for (int i = tid; i < D * W; i += blockDim.x) bm[i] = 0u;
     __syncthreads();
     for (int x = tid; x < D; x += blockDim.x) table_insert(keys, vals, (uint32_t)ocol[base + x], x, hb, err);
@@ -114,71 +117,49 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
       const int64_t be = upper_bound_i32(ocol, bb, orp[b + 1], lastA);
       probes += (u64)(be - bb);
       uint32_t* row = bm + (size_t)ib * W;
-      int hits = 0;
       for (int64_t k = bb + lane; k < be; k += 32) {
         const int ic = table_find(keys, vals, (uint32_t)ocol[k], hb);
         if (ic >= 0) {
           atomicOr(&row[ic >> 5], 1u << (ic & 31));
-          atomicAdd(&C3o[k], 1);      // edge b -> c
-          atomicAdd(&colc[ic], 1);    // edge a -> c
-          ++hits;                     // edge a -> b
+          atomicOr(&bm[(size_t)ic * W + (ib >> 5)], 1u << (ib & 31));
+          atomicAdd(&C3o[k], 1);  // edge b -> c
         }
       }
-      hits = warp_sum_i32(hits);
-      if (lane == 0) rowc[ib] = hits;
     }
     __syncthreads();
 
-    // 4-cliques {a, b, c, d}: bit (b, c) and d in row(b) AND row(c).
-    u64 k4_here = 0;
-    for (int ib = warp; ib < D; ib += nwarps) {
-      if (rowc[ib] < 2) continue;
-      const uint32_t* row = bm + (size_t)ib * W;
-      int krow = 0;
-      for (int w0 = (ib + 1) >> 5; w0 < W; ++w0) {
-        const uint32_t bits = row[w0];
+    // Per local vertex x: triangles through edge a-x and 4-cliques through a-x.
+    u64 tri2x = 0, k4_6x = 0;
+    for (int x = warp; x < D; x += nwarps) {
+      const uint32_t* Sx = bm + (size_t)x * W;
+      int deg = 0;
+      for (int w = lane; w < W; w += 32) deg += __popc(Sx[w]);
+      deg = warp_sum_i32(deg);
+      long long k2 = 0;  // sum over y in S_x of |S_x ∩ S_y|
+      for (int w0 = 0; w0 < W; ++w0) {
+        const uint32_t bits = Sx[w0];
         if (!bits) continue;
         if ((bits >> lane) & 1u) {
-          const int ic = (w0 << 5) + lane;
-          const uint32_t* rc = bm + (size_t)ic * W;
+          const uint32_t* Sy = bm + (size_t)((w0 << 5) + lane) * W;
           int k = 0;
-          for (int w = w0; w < W; ++w) {
-            uint32_t x = row[w] & rc[w];
-            while (x) {
-              const int t = __ffs(x) - 1;
-              x &= x - 1;
-              atomicAdd(&k4c[(w << 5) + t], 1u);
-              ++k;
-            }
-          }
-          if (k) {
-            atomicAdd(&k4c[ic], (uint32_t)k);
-            krow += k;
-          }
+          for (int w = 0; w < W; ++w) k += __popc(Sx[w] & Sy[w]);
+          k2 += k;
         }
       }
-      krow = warp_sum_i32(krow);
-      if (lane == 0 && krow) {
-        atomicAdd(&k4c[ib], (uint32_t)krow);
-        k4_here += (u64)krow;
+      k2 = warp_sum_i64(k2);
+      if (lane == 0) {
+        const int32_t vx = ocol[base + x];
+        if (deg) {
+          atomicAdd(&C3o[base + x], deg);
+          atomicAdd(&c3r[vx], (u64)deg);
+        }
+        if (k2) atomicAdd(&k4r[vx], (u64)(k2 / 2));
+        tri2x += (u64)deg;
+        k4_6x += (u64)k2;
       }
     }
-    __syncthreads();
-
-    // Flush: C3(a, x) gets the triangles of this pass through edge a -> x.
-    u64 tri_here = 0;
-    for (int x = tid; x < D; x += blockDim.x) {
-      const int t = rowc[x] + colc[x];
-      tri_here += (u64)rowc[x];
-      const int32_t vx = ocol[base + x];
-      if (t) {
-        atomicAdd(&C3o[base + x], t);
-        atomicAdd(&c3r[vx], (u64)t);
-      }
-      if (k4c[x]) atomicAdd(&k4r[vx], (u64)k4c[x]);
-    }
-    const u64 tri_sum = block_sum(tri_here, red);
-    const u64 k4_sum = block_sum(k4_here, red);
+    const u64 tri_sum = block_sum(tri2x, red) / 2;
+    const u64 k4_sum = block_sum(k4_6x, red) / 6;
     const u64 probe_sum = block_sum(lane == 0 ? probes : (u64)0, red);
     if (tid == 0) {
       if (tri_sum) atomicAdd(&c3r[a], tri_sum);
@@ -257,7 +238,7 @@ __global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp,
 size_t tri1_smem_impl(int D, bool smem_bm) {
   const int H = 1 << hash_bits_for(D);
   const size_t W = (size_t)(D + 31) / 32;
-  size_t bytes = (size_t)H * 8 + (size_t)D * 12;
+  size_t bytes = (size_t)H * 8;
   if (smem_bm) bytes += (size_t)D * W * 4;
   return (bytes + 15) & ~(size_t)15;
 }

@@ -217,3 +217,42 @@ def test_batched_equals_per_graph(handle):
     oraw, onet = oracle.fglt(batch.graph)
     assert_same(raw, oraw, "batched raw")
     assert_same(net, onet, "batched net")
+
+
+@pytest.mark.parametrize("span", [1, 64, 1024])
+def test_cycle_paths_with_small_hub_span(span):
+    """Shrinking the dense hub range routes 4-cycle work through the shared and
+    global hash tables; the counts must not change."""
+    import paper_2007_11111_gb300 as fg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    with fg.Handle(device=0, cyc_hub_span=span) as h:
+        for g in (gg.rmat(12, 16, seed=21), gg.barabasi_albert(2000, 6, seed=3), complete_bipartite(60, 90)):
+            check_vs_oracle(h, g, f"span {span} n={g.n}")
+
+
+def test_rmat_s20_full_size_sampled(handle):
+    """R-MAT scale 20, edge factor 16, seed 0 (the benchmark workload), in the
+    benchmark's launch configuration: every row checked against the invariants
+    that hold at any size, and a vertex sample (top-degree hubs, low-degree and
+    isolated vertices, uniform picks) element by element against the oracle."""
+    g = gg.rmat(20, 16, seed=0)
+    raw, net = gpu(handle, g)
+    deg = np.diff(g.rowptr)
+    # invariants on every row
+    np.testing.assert_array_equal(raw[:, 0], 1)
+    np.testing.assert_array_equal(raw[:, 1], deg)
+    assert (net >= 0).all()
+    assert_same(raw, net @ oracle.u16().T, "raw = U16 net")
+    s = net.sum(axis=0)
+    assert s[1] == 2 * g.m and s[2] == 2 * s[3] and s[5] == s[6] and s[7] == 3 * s[8]
+    assert s[10] == 2 * s[9] and s[9] == s[11] and s[13] == s[14]
+    assert s[4] % 3 == 0 and s[12] % 4 == 0 and s[15] % 4 == 0
+    # sampled rows vs the oracle
+    rng = np.random.default_rng(2024)
+    order = np.argsort(deg)
+    verts = np.unique(np.concatenate([order[-8:], order[:4], order[len(order) // 2: len(order) // 2 + 4],
+                                      rng.integers(0, g.n, 40)]))
+    oraw, onet = oracle.fglt(g, vertices=verts)
+    assert_same(raw[verts], oraw, "sampled raw")
+    assert_same(net[verts], onet, "sampled net")
