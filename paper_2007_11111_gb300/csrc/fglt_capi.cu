@@ -34,8 +34,8 @@ enum BufId {
 
 // Small device counters, one int slot each.
 enum CounterId {
-  C_DMAX, C_NHEAVY, C_DPMAX, C_NTRI, C_NEXT1, C_NEXT2, C_NCYC0, C_NCYC1, C_NCYC2, C_NEXTC0, C_NEXTC1,
-  C_NEXTC2, C_ERR, C_NUM
+  C_DMAX, C_NHEAVY, C_DPMAX, C_NTRI, C_NEXT1, C_NEXT2, C_NCYC0, C_NCYC1, C_NCYC2, C_NCYC3, C_NEXTC0,
+  C_NEXTC1, C_NEXTC2, C_NEXTC3, C_ERR, C_NUM
 };
 // 64-bit work counters: triangle-pass scanned entries, triangles, 4-cliques,
 // max and total wedges of the 4-cycle stage.
@@ -309,12 +309,12 @@ fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out
   CK(launch_wedge_count(g, rank, orp, ocol, heavy, cnt + C_NHEAVY, heavy_cap, hub_lo, wc, wcn, ctr + W_WMAX,
                         ctr + W_WSUM, st));
   int32_t* lists;
-  NEED(B_LS, 3 * n, lists);
-  CK(launch_cyc_worklists(wc, wcn, n, lists, n, cnt + C_NCYC0, ctr + W_GCAP, st));
+  NEED(B_LS, 4 * n, lists);
+  CK(launch_cyc_worklists(wc, wcn, n, lists, n, cnt + C_NCYC0, ctr + W_GCAP, hub_lo < n, st));
   int32_t n_gmem = 0;
   u64 gcap = 0;
   {
-    fglt_status s = read_scalar(h, st, cnt + C_NCYC2, &n_gmem);
+    fglt_status s = read_scalar(h, st, cnt + C_NCYC3, &n_gmem);
     if (s == FGLT_OK) s = read_scalar(h, st, ctr + W_GCAP, &gcap);
     if (s != FGLT_OK) return s;
   }
@@ -434,7 +434,7 @@ fglt_status fglt_create(fglt_t* out, const fglt_options* opt, int device) {
   if (opt) h->opt = *opt;
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMallocHost(&h->pinned, 64);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->pinned, 256);
   for (int i = 0; e == cudaSuccess && i <= NUM_STAGES; ++i) e = cudaEventCreate(&h->ev[i]);
   if (e != cudaSuccess) {
     fglt_status s = cuda_fail(h, e);

@@ -92,10 +92,13 @@ cudaError_t launch_wedge_count(const Csr& g, const int32_t* rank, const int64_t*
 // degree is below 65536, else 32-bit).
 int cyc_dense_span(bool c16);
 int cyc_gmem_blocks();
-// Splits the vertices with at least two wedges into three classes (lists at
-// lists + c * list_stride, counts[c]); *gcap_max = largest table need of class 2.
+// Splits the vertices with at least two wedges into four classes (lists at
+// lists + c * list_stride, counts[c]): warp table, block hash table, dense hub
+// counters (only if dense_ok), global hash table; *gcap_max = largest table
+// need of the last class.
 cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, int64_t n, int32_t* lists,
-                                 int64_t list_stride, int32_t* counts, u64* gcap_max, cudaStream_t st);
+                                 int64_t list_stride, int32_t* counts, u64* gcap_max, bool dense_ok,
+                                 cudaStream_t st);
 struct CycArgs {
   const int32_t* rank;
   const int32_t* perm;
@@ -104,12 +107,12 @@ struct CycArgs {
   const int64_t* wc;
   const int32_t* lists;
   int64_t list_stride;
-  const int32_t* counts;  // 3 class sizes
-  int* next;              // 3 scheduling counters (zeroed)
+  const int32_t* counts;  // 4 class sizes
+  int* next;              // 4 scheduling counters (zeroed)
   bool c16;
   int32_t hub_lo;
-  int gbits;              // class-2 tables: cyc_gmem_blocks() << gbits slots each array
-  uint32_t* gkeys;        // NULL when class 2 is empty
+  int gbits;              // class-3 tables: cyc_gmem_blocks() << gbits slots each array
+  uint32_t* gkeys;        // NULL when class 3 is empty
   uint32_t* gcnt;
   u64* r12r;
   int* err;

@@ -16,12 +16,13 @@
 //
 // Counters per w live in
 //  - a per-warp shared-memory hash table (vertices with few wedges),
+//  - a per-block shared-memory hash table (medium vertices),
 //  - a dense shared-memory array over the top-ranked ("hub") vertices plus a
-//    small shared-memory hash table for the other tops (most wedges of a
-//    power-law graph end at a hub),
+//    small shared-memory hash table for the other tops (heavy vertices: most
+//    wedges of a power-law graph end at a hub),
 //  - or a global-memory hash table (fallback).
-// Wedges are walked warp-cooperatively: 32 middles v at a time, their
-// segments of N+(v) concatenated and split evenly over the lanes.
+// Wedges are walked cooperatively: the segments of N+(v) of many middles v are
+// concatenated and split evenly over the lanes of a warp or a block.
 #include "fglt_device.cuh"
 #include "fglt_kernels.h"
 
@@ -32,10 +33,11 @@ namespace {
 constexpr int WARP_HASH = 1024;   // slots per warp table
 constexpr int WARP_CAP = 512;     // most wedges handled by one warp table
 constexpr int WARP_T = 256;
-constexpr int DENSE_T = 512;
+constexpr int BLOCK_T = 512;
 constexpr int DENSE_WORDS = 16384;  // 64 KB of counters
 constexpr int DHASH_BITS = 12;      // 4096-slot table for the non-hub tops
-constexpr int GMEM_T = 512;
+constexpr int BHASH_BITS = 13;      // largest per-w table of the hash-only block class
+constexpr int BLOCK_CAP = 1 << (BHASH_BITS - 1);
 
 int num_sms() {
   int dev = 0, sms = 1;
@@ -218,37 +220,167 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const RP* __restrict__ rp, 
 }
 
 // ---------------------------------------------------------------------------
-// Heavy vertices: one block per w. Tops u >= hub_lo count in a dense array
-// (16-bit or 32-bit counters), the others in a 4096-slot hash table.
+// Larger vertices: one block per w. N(w) is taken CHUNK middles at a time;
+// the non-empty segments of the chunk are compacted into shared memory with
+// their exclusive wedge prefix, and the chunk's wedges are split evenly over
+// the block's warps, 32 consecutive wedges per warp step (the owner of each
+// lane follows from the segment starts that fall inside the step).
+//
+// MODE 0: hash table in shared memory sized per w (at most 2^13 slots)
+// MODE 1: dense 16-bit counters for tops >= hub_lo + 2^12-slot shared hash
+// MODE 2: dense 32-bit counters for tops >= hub_lo + 2^12-slot shared hash
+// MODE 3: hash table in global memory sized per w (fallback)
 // ---------------------------------------------------------------------------
-template <typename RP, bool C16>
-__global__ void __launch_bounds__(DENSE_T) k_cyc_dense(const RP* __restrict__ rp, const int32_t* __restrict__ ci,
+constexpr int CHUNK = BLOCK_T;
+
+struct Segs {
+  int64_t* st;      // [CHUNK] segment start in ocol
+  int64_t* pre;     // [CHUNK + 1] exclusive wedge prefix
+  u64* acc;         // [CHUNK] middle credits
+  long long* scan;  // [64] block-scan scratch
+  int32_t* rv;      // [CHUNK] rank of the middle
+  int* misc;        // [0] = segment count
+};
+
+// Block-wide exclusive scan (blockDim.x == BLOCK_T); *total = sum.
+__device__ __forceinline__ long long block_excl_scan(long long x, long long* scratch, long long* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const long long wv = lane < (BLOCK_T / 32) ? scratch[lane] : 0;
+    long long wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    scratch[32 + lane] = wi - wv;
+    if (lane == 31) scratch[63] = wi;
+  }
+  __syncthreads();
+  *total = scratch[63];
+  const long long r = scratch[32 + warp] + incl - x;
+  __syncthreads();
+  return r;
+}
+
+// Compacted segments of the middles colidx[c0 .. c0 + CHUNK).
+__device__ __forceinline__ void build_chunk(const Segs& S, const int32_t* __restrict__ ci,
+                                            const int32_t* __restrict__ rank, const int64_t* __restrict__ orp,
+                                            const int32_t* __restrict__ ocol, int64_t c0, int64_t e, int32_t w,
+                                            int64_t n) {
+  const int64_t k = c0 + threadIdx.x;
+  int32_t rv = -1;
+  int64_t st = 0, len = 0;
+  if (k < e) {
+    const int32_t v = __ldg(ci + k);
+    if ((uint32_t)v < (uint64_t)n) {
+      rv = __ldg(rank + v);
+      const int64_t ob = __ldg(orp + rv), oe = __ldg(orp + rv + 1);
+      st = upper_bound_i32(ocol, ob, oe, w);
+      len = oe - st;
+    }
+  }
+  long long nseg, total;
+  const long long pos = block_excl_scan(len > 0 ? 1 : 0, S.scan, &nseg);
+  const long long off = block_excl_scan(len, S.scan, &total);
+  if (len > 0) {
+    S.st[pos] = st;
+    S.pre[pos] = off;
+    S.rv[pos] = rv;
+    S.acc[pos] = 0;
+  }
+  if (threadIdx.x == 0) {
+    S.misc[0] = (int)nseg;
+    S.pre[nseg] = total;
+  }
+  __syncthreads();
+}
+
+// f(u, segment) for every wedge of the current chunk.
+template <typename F>
+__device__ __forceinline__ void walk_chunk(const Segs& S, const int32_t* __restrict__ ocol, F f) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int ns = S.misc[0];
+  const int64_t total = S.pre[ns];
+  for (int64_t t0 = (int64_t)warp * 32; t0 < total; t0 += (int64_t)nwarps * 32) {
+    int lo = 0, hi = ns - 1;  // last segment whose start is <= t0
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (S.pre[mid] <= t0) lo = mid; else hi = mid - 1;
+    }
+    const int jb = lo + 1 + lane;
+    uint32_t bit = 0;
+    if (jb < ns) {
+      const int64_t r = S.pre[jb] - t0;
+      if (r < 32) bit = 1u << r;
+    }
+    const uint32_t M = __reduce_or_sync(0xffffffffu, bit);
+    const uint32_t upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const int j = lo + __popc(M & upto);
+    const int64_t t = t0 + lane;
+    if (t < total) f((uint32_t)__ldg(ocol + S.st[j] + (t - S.pre[j])), j);
+  }
+}
+
+size_t seg_bytes() {
+  return (size_t)CHUNK * 8 + (size_t)(CHUNK + 1) * 8 + (size_t)CHUNK * 8 + 64 * 8 + (size_t)CHUNK * 4 + 16;
+}
+
+template <typename RP, int MODE>
+__global__ void __launch_bounds__(BLOCK_T) k_cyc_block(const RP* __restrict__ rp, const int32_t* __restrict__ ci,
                                                        const int32_t* __restrict__ rank,
                                                        const int32_t* __restrict__ perm,
                                                        const int64_t* __restrict__ orp,
                                                        const int32_t* __restrict__ ocol,
+                                                       const int64_t* __restrict__ wc,
                                                        const int32_t* __restrict__ list,
                                                        const int32_t* __restrict__ cnt, int* next, u64* r12r,
-                                                       int64_t n, int32_t hub_lo, int* err) {
+                                                       int64_t n, int32_t hub_lo, int gbits, uint32_t* gkeys,
+                                                       uint32_t* gcnt, int* err) {
+  constexpr bool DENSE = MODE == 1 || MODE == 2;
+  constexpr bool C16 = MODE == 1;
+  constexpr bool GMEM = MODE == 3;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* dense = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* hkeys = dense + DENSE_WORDS;
-  uint32_t* hcnts = hkeys + (1 << DHASH_BITS);
-  u64* sacc = reinterpret_cast<u64*>(hcnts + (1 << DHASH_BITS));
   __shared__ int s_item;
   __shared__ u64 red[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  Table<false> T{hkeys, hcnts};
-  u64* acc = sacc + warp * 32;
+  // dynamic layout: [segments][dense counters][hash keys][hash counts]
+  Segs S;
+  S.st = reinterpret_cast<int64_t*>(smem);
+  S.pre = S.st + CHUNK;
+  S.acc = reinterpret_cast<u64*>(S.pre + CHUNK + 1);
+  S.scan = reinterpret_cast<long long*>(S.acc + CHUNK);
+  S.rv = reinterpret_cast<int32_t*>(S.scan + 64);
+  S.misc = S.rv + CHUNK;
+  uint32_t* after = reinterpret_cast<uint32_t*>(S.misc + 4);
+  uint32_t* dense = after;
+  uint32_t* hbase = DENSE ? after + DENSE_WORDS : after;
+  const int tbits = GMEM ? gbits : (DENSE ? DHASH_BITS : BHASH_BITS);
+  Table<GMEM> T;
+  if (GMEM) {
+    T.keys = gkeys + ((size_t)blockIdx.x << gbits);
+    T.cnts = gcnt + ((size_t)blockIdx.x << gbits);
+  } else {
+    T.keys = hbase;
+    T.cnts = hbase + (1 << tbits);
+  }
+  const int tid = threadIdx.x;
   const int total = *cnt;
-  const int hub_n = (int)(n - hub_lo);  // number of dense counters in use
+  const int hub_n = DENSE ? (int)(n - hub_lo) : 0;
 
-  auto add = [&](uint32_t u) {
+  auto dense_add = [&](uint32_t u) {
     const uint32_t i = u - (uint32_t)hub_lo;
     if (C16) atomicAdd(&dense[i >> 1], 1u << ((i & 1u) << 4));
     else atomicAdd(&dense[i], 1u);
   };
-  auto get = [&](uint32_t u) -> uint32_t {
+  auto dense_get = [&](uint32_t u) -> uint32_t {
     const uint32_t i = u - (uint32_t)hub_lo;
     if (C16) return (dense[i >> 1] >> ((i & 1u) << 4)) & 0xFFFFu;
     return dense[i];
@@ -260,112 +392,58 @@ __global__ void __launch_bounds__(DENSE_T) k_cyc_dense(const RP* __restrict__ rp
     const int item = s_item;
     if (item >= total) break;
     const int32_t w = list[item];
-    const int words = C16 ? (hub_n + 1) >> 1 : hub_n;
-    for (int i = tid; i < words; i += blockDim.x) dense[i] = 0u;
-    for (int i = tid; i < (1 << DHASH_BITS); i += blockDim.x) T.clear(i);
-    if (tid < nwarps * 32) sacc[tid] = 0;
+    int hb = tbits;
+    if (!DENSE) {
+      int64_t cap = wc[w];
+      if (cap > n - 1 - w) cap = n - 1 - w;
+      hb = 5;
+      while ((1LL << hb) < 2 * cap) ++hb;
+    }
+    const uint32_t H = 1u << hb;
+    if (DENSE) {
+      const int words = C16 ? (hub_n + 1) >> 1 : hub_n;
+      for (int i = tid; i < words; i += blockDim.x) dense[i] = 0u;
+    }
+    for (uint32_t i = tid; i < H; i += blockDim.x) T.clear(i);
     __syncthreads();
+
     const int64_t wo = perm[w];
     const int64_t s = (int64_t)rp[wo], e = (int64_t)rp[wo + 1];
-    for (int64_t k0 = s + warp * 32; k0 < e; k0 += nwarps * 32) {
-      const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
-      walk_group(g, ocol, lane, [&](uint32_t u, int) {
-        if ((int32_t)u >= hub_lo) add(u);
-        else T.increment(u, DHASH_BITS, err);
+    const bool single = e - s <= CHUNK;
+    // Pass A: count the wedges per top u.
+    for (int64_t c0 = s; c0 < e; c0 += CHUNK) {
+      build_chunk(S, ci, rank, orp, ocol, c0, e, w, n);
+      walk_chunk(S, ocol, [&](uint32_t u, int) {
+        if (DENSE && (int32_t)u >= hub_lo) dense_add(u);
+        else T.increment(u, hb, err);
       });
+      __syncthreads();
     }
-    __syncthreads();
-    for (int64_t k0 = s + warp * 32; k0 < e; k0 += nwarps * 32) {
-      const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
-      walk_group(g, ocol, lane, [&](uint32_t u, int j) {
-        const uint32_t c = (int32_t)u >= hub_lo ? get(u) : T.count_of(u, DHASH_BITS);
-        if (c > 1) atomicAdd(&acc[j], (u64)(c - 1));
+    // Pass B: each middle gains cnt[u] - 1 per wedge.
+    for (int64_t c0 = s; c0 < e; c0 += CHUNK) {
+      if (!single) build_chunk(S, ci, rank, orp, ocol, c0, e, w, n);
+      walk_chunk(S, ocol, [&](uint32_t u, int j) {
+        const uint32_t c = (DENSE && (int32_t)u >= hub_lo) ? dense_get(u) : T.count_of(u, hb);
+        if (c > 1) atomicAdd(&S.acc[j], (u64)(c - 1));
       });
-      __syncwarp();
-      if (acc[lane]) {
-        atomicAdd(&r12r[g.rv], acc[lane]);
-        acc[lane] = 0;
-      }
-      __syncwarp();
+      __syncthreads();
+      const int ns = S.misc[0];
+      for (int j = tid; j < ns; j += blockDim.x)
+        if (S.acc[j]) atomicAdd(&r12r[S.rv[j]], S.acc[j]);
+      __syncthreads();
     }
+    // Pass C: top u and bottom w gain binom(cnt[u], 2).
     u64 accw = 0;
-    for (int i = tid; i < hub_n; i += blockDim.x) {
-      const u64 c = get((uint32_t)(hub_lo + i));
-      if (c >= 2) {
-        const u64 v = c * (c - 1) / 2;
-        atomicAdd(&r12r[hub_lo + i], v);
-        accw += v;
-      }
-    }
-    for (int i = tid; i < (1 << DHASH_BITS); i += blockDim.x) {
-      const uint32_t key = T.load_key(i);
-      if (key != EMPTY_KEY) {
-        const u64 c = T.load_cnt(i);
+    if (DENSE) {
+      for (int i = tid; i < hub_n; i += blockDim.x) {
+        const u64 c = dense_get((uint32_t)(hub_lo + i));
         if (c >= 2) {
           const u64 v = c * (c - 1) / 2;
-          atomicAdd(&r12r[key], v);
+          atomicAdd(&r12r[hub_lo + i], v);
           accw += v;
         }
       }
     }
-    accw = block_sum(accw, red);
-    if (tid == 0 && accw) atomicAdd(&r12r[w], accw);
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Fallback: one block per w, hash table in global memory.
-// ---------------------------------------------------------------------------
-template <typename RP>
-__global__ void __launch_bounds__(GMEM_T) k_cyc_gmem(const RP* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                     const int32_t* __restrict__ rank, const int32_t* __restrict__ perm,
-                                                     const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
-                                                     const int64_t* __restrict__ wc, const int32_t* __restrict__ list,
-                                                     const int32_t* __restrict__ cnt, int* next, int gbits,
-                                                     uint32_t* gkeys, uint32_t* gcnt, u64* r12r, int64_t n, int* err) {
-  __shared__ int s_item;
-  __shared__ u64 red[32];
-  __shared__ u64 sacc[GMEM_T];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  Table<true> T{gkeys + ((size_t)blockIdx.x << gbits), gcnt + ((size_t)blockIdx.x << gbits)};
-  u64* acc = sacc + warp * 32;
-  const int total = *cnt;
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(next, 1);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= total) break;
-    const int32_t w = list[item];
-    int64_t cap = wc[w];
-    if (cap > n - 1 - w) cap = n - 1 - w;
-    int hb = 5;
-    while ((1LL << hb) < 2 * cap) ++hb;
-    const uint32_t H = 1u << hb;
-    for (uint32_t i = tid; i < H; i += blockDim.x) T.clear(i);
-    sacc[tid] = 0;
-    __syncthreads();
-    const int64_t wo = perm[w];
-    const int64_t s = (int64_t)rp[wo], e = (int64_t)rp[wo + 1];
-    for (int64_t k0 = s + warp * 32; k0 < e; k0 += nwarps * 32) {
-      const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
-      walk_group(g, ocol, lane, [&](uint32_t u, int) { T.increment(u, hb, err); });
-    }
-    __syncthreads();
-    for (int64_t k0 = s + warp * 32; k0 < e; k0 += nwarps * 32) {
-      const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
-      walk_group(g, ocol, lane, [&](uint32_t u, int j) {
-        const uint32_t c = T.count_of(u, hb);
-        if (c > 1) atomicAdd(&acc[j], (u64)(c - 1));
-      });
-      __syncwarp();
-      if (acc[lane]) {
-        atomicAdd(&r12r[g.rv], acc[lane]);
-        acc[lane] = 0;
-      }
-      __syncwarp();
-    }
-    u64 accw = 0;
     for (uint32_t i = tid; i < H; i += blockDim.x) {
       const uint32_t key = T.load_key(i);
       if (key != EMPTY_KEY) {
@@ -383,9 +461,11 @@ __global__ void __launch_bounds__(GMEM_T) k_cyc_gmem(const RP* __restrict__ rp, 
   }
 }
 
-// Vertex classes: 0 = warp table, 1 = dense + shared hash, 2 = global hash.
+// Vertex classes: 0 = warp table, 1 = block + shared hash, 2 = block + dense
+// hub counters + shared hash, 3 = block + global hash.
 __global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* __restrict__ wcn, int64_t n,
-                                int32_t* lists, int64_t list_stride, int32_t* counts, u64* gcap_max) {
+                                int32_t* lists, int64_t list_stride, int32_t* counts, u64* gcap_max,
+                                int dense_ok) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < n; r0 += stride) {
@@ -396,12 +476,13 @@ __global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* _
       cap = wc[r];
       if (cap > n - 1 - r) cap = n - 1 - r;
       if (wc[r] <= WARP_CAP) cls = 0;
-      else if (wcn[r] <= (1 << (DHASH_BITS - 1))) cls = 1;
-      else cls = 2;
+      else if (cap <= BLOCK_CAP) cls = 1;
+      else if (dense_ok && wcn[r] <= (1 << (DHASH_BITS - 1))) cls = 2;
+      else cls = 3;
     }
-    if (cls == 2) atomicMax(gcap_max, (u64)cap);
+    if (cls == 3) atomicMax(gcap_max, (u64)cap);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 4; ++c) {
       const unsigned m = __ballot_sync(0xffffffffu, cls == c);
       int pos = 0;
       if (lane == 0 && m) pos = atomicAdd(&counts[c], __popc(m));
@@ -417,8 +498,24 @@ int occupancy(const void* fn, int threads, size_t smem) {
   return per_sm < 1 ? 1 : per_sm;
 }
 
-size_t dense_smem() {
-  return (size_t)DENSE_WORDS * 4 + (size_t)(1 << DHASH_BITS) * 8 + (size_t)(DENSE_T / 32) * 32 * 8;
+size_t block_smem(int mode) {
+  const size_t seg = seg_bytes();
+  if (mode == 0) return seg + ((size_t)8 << BHASH_BITS);
+  if (mode == 1 || mode == 2) return seg + (size_t)DENSE_WORDS * 4 + ((size_t)8 << DHASH_BITS);
+  return seg;
+}
+
+int gmem_blocks() { return num_sms(); }
+
+template <typename RP, int MODE>
+void launch_block(const RP* rp, const Csr& g, const CycArgs& a, int cls, cudaStream_t st) {
+  const size_t smem = block_smem(MODE);
+  cudaFuncSetAttribute(k_cyc_block<RP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int grid = MODE == 3 ? gmem_blocks()
+                             : num_sms() * occupancy((const void*)k_cyc_block<RP, MODE>, BLOCK_T, smem);
+  k_cyc_block<RP, MODE><<<grid, BLOCK_T, smem, st>>>(rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc,
+                                                     a.lists + cls * a.list_stride, a.counts + cls, a.next + cls,
+                                                     a.r12r, g.n, a.hub_lo, a.gbits, a.gkeys, a.gcnt, a.err);
 }
 
 template <typename RP>
@@ -429,39 +526,26 @@ cudaError_t launch_rp(const Csr& g, const CycArgs& a, cudaStream_t st) {
   cudaFuncSetAttribute(k_cyc_warp<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
   k_cyc_warp<RP><<<sms * occupancy((const void*)k_cyc_warp<RP>, WARP_T, wsmem), WARP_T, wsmem, st>>>(
       rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc, a.lists, a.counts, a.next + 0, a.r12r, g.n, a.err);
-  const size_t smem = dense_smem();
-  if (a.c16) {
-    cudaFuncSetAttribute(k_cyc_dense<RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int grid = sms * occupancy((const void*)k_cyc_dense<RP, true>, DENSE_T, smem);
-    k_cyc_dense<RP, true><<<grid, DENSE_T, smem, st>>>(rp, g.colidx, a.rank, a.perm, a.orp, a.ocol,
-                                                       a.lists + a.list_stride, a.counts + 1, a.next + 1, a.r12r,
-                                                       g.n, a.hub_lo, a.err);
-  } else {
-    cudaFuncSetAttribute(k_cyc_dense<RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int grid = sms * occupancy((const void*)k_cyc_dense<RP, false>, DENSE_T, smem);
-    k_cyc_dense<RP, false><<<grid, DENSE_T, smem, st>>>(rp, g.colidx, a.rank, a.perm, a.orp, a.ocol,
-                                                        a.lists + a.list_stride, a.counts + 1, a.next + 1, a.r12r,
-                                                        g.n, a.hub_lo, a.err);
-  }
-  if (a.gkeys) {
-    k_cyc_gmem<RP><<<cyc_gmem_blocks(), GMEM_T, 0, st>>>(rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc,
-                                                         a.lists + 2 * a.list_stride, a.counts + 2, a.next + 2,
-                                                         a.gbits, a.gkeys, a.gcnt, a.r12r, g.n, a.err);
-  }
+  launch_block<RP, 0>(rp, g, a, 1, st);
+  if (a.c16) launch_block<RP, 1>(rp, g, a, 2, st);
+  else launch_block<RP, 2>(rp, g, a, 2, st);
+  if (a.gkeys) launch_block<RP, 3>(rp, g, a, 3, st);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 int cyc_dense_span(bool c16) { return c16 ? 2 * DENSE_WORDS : DENSE_WORDS; }
-int cyc_gmem_blocks() { return num_sms(); }
+int cyc_gmem_blocks() { return gmem_blocks(); }
 
 cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, int64_t n, int32_t* lists,
-                                 int64_t list_stride, int32_t* counts, u64* gcap_max, cudaStream_t st) {
+                                 int64_t list_stride, int32_t* counts, u64* gcap_max, bool dense_ok,
+                                 cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int64_t blocks = (n + 255) / 256;
   if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
-  k_cyc_worklists<<<(unsigned)blocks, 256, 0, st>>>(wc, wcn, n, lists, list_stride, counts, gcap_max);
+  k_cyc_worklists<<<(unsigned)blocks, 256, 0, st>>>(wc, wcn, n, lists, list_stride, counts, gcap_max,
+                                                     dense_ok ? 1 : 0);
   return cudaGetLastError();
 }
 
