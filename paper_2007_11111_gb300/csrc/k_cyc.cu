@@ -147,8 +147,24 @@ __device__ __forceinline__ void walk_group(const Group& g, const int32_t* __rest
     }
     const int64_t ost = __shfl_sync(0xffffffffu, g.st, j);
     const int64_t oex = __shfl_sync(0xffffffffu, g.excl, j);
-    if (t < g.total) f((uint32_t)__ldg(ocol + ost + (t - oex)), j);
+    const bool valid = t < g.total;
+    f(valid ? (uint32_t)__ldg(ocol + ost + (t - oex)) : 0u, j, valid);
   }
+}
+
+// Sum of x over the lanes of each run of equal owners j (owners are
+// non-decreasing over the lanes); the first lane of a run gets the run total.
+__device__ __forceinline__ u64 run_sum(u64 x, int j, bool& head) {
+  const int lane = threadIdx.x & 31;
+  const int jp = __shfl_up_sync(0xffffffffu, j, 1);
+  head = lane == 0 || jp != j;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u64 y = __shfl_down_sync(0xffffffffu, x, o);
+    const int jy = __shfl_down_sync(0xffffffffu, j, o);
+    if (lane + o < 32 && jy == j) x += y;
+  }
+  return x;
 }
 
 // ---------------------------------------------------------------------------
@@ -185,14 +201,22 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const RP* __restrict__ rp, 
     const int64_t s = (int64_t)rp[wo], e = (int64_t)rp[wo + 1];
     for (int64_t k0 = s; k0 < e; k0 += 32) {
       const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
-      walk_group(g, ocol, lane, [&](uint32_t u, int) { T.increment(u, hb, err); });
+      walk_group(g, ocol, lane, [&](uint32_t u, int, bool valid) {
+        if (valid) T.increment(u, hb, err);
+      });
     }
     __syncwarp();
     for (int64_t k0 = s; k0 < e; k0 += 32) {
       const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
-      walk_group(g, ocol, lane, [&](uint32_t u, int j) {
-        const uint32_t c = T.count_of(u, hb);
-        if (c > 1) atomicAdd(&acc[j], (u64)(c - 1));
+      walk_group(g, ocol, lane, [&](uint32_t u, int j, bool valid) {
+        u64 c = 0;
+        if (valid) {
+          c = T.count_of(u, hb);
+          c = c > 1 ? c - 1 : 0;
+        }
+        bool head;
+        const u64 sum = run_sum(c, valid ? j : -1, head);
+        if (head && valid && sum) atomicAdd(&acc[j], sum);
       });
       __syncwarp();
       if (acc[lane]) {
@@ -235,7 +259,7 @@ constexpr int CHUNK = BLOCK_T;
 
 struct Segs {
   int64_t* st;      // [CHUNK] segment start in ocol
-  int64_t* pre;     // [CHUNK + 1] exclusive wedge prefix
+  int32_t* pre;     // [CHUNK + 1] exclusive wedge prefix (a chunk holds < 2^31 wedges)
   u64* acc;         // [CHUNK] middle credits
   long long* scan;  // [64] block-scan scratch
   int32_t* rv;      // [CHUNK] rank of the middle
@@ -293,45 +317,61 @@ __device__ __forceinline__ void build_chunk(const Segs& S, const int32_t* __rest
   const long long off = block_excl_scan(len, S.scan, &total);
   if (len > 0) {
     S.st[pos] = st;
-    S.pre[pos] = off;
+    S.pre[pos] = (int32_t)off;
     S.rv[pos] = rv;
     S.acc[pos] = 0;
   }
   if (threadIdx.x == 0) {
     S.misc[0] = (int)nseg;
-    S.pre[nseg] = total;
+    S.pre[nseg] = (int32_t)total;
   }
   __syncthreads();
 }
 
-// f(u, segment) for every wedge of the current chunk.
+// Walks the current chunk's wedges. Warp k takes the contiguous range
+// [k*per, (k+1)*per) of the chunk's wedge space, 32 wedges per step; the
+// owner segment of each lane follows from the segment starts inside the step
+// (segments are non-empty, so starts are distinct). f(u, j, valid) is called
+// by every lane (valid = false past the end) so that it may use warp
+// collectives.
 template <typename F>
 __device__ __forceinline__ void walk_chunk(const Segs& S, const int32_t* __restrict__ ocol, F f) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int ns = S.misc[0];
-  const int64_t total = S.pre[ns];
-  for (int64_t t0 = (int64_t)warp * 32; t0 < total; t0 += (int64_t)nwarps * 32) {
-    int lo = 0, hi = ns - 1;  // last segment whose start is <= t0
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (S.pre[mid] <= t0) lo = mid; else hi = mid - 1;
-    }
-    const int jb = lo + 1 + lane;
+  const int total = S.pre[ns];
+  const int per = ((total + nwarps - 1) / nwarps + 31) & ~31;
+  const int w0 = warp * per;
+  const int w1 = min(w0 + per, total);
+  if (w0 >= w1) return;
+  int lo = 0, hi = ns - 1;  // segment containing w0
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (S.pre[mid] <= w0) lo = mid; else hi = mid - 1;
+  }
+  int base = lo;
+  const uint32_t upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  for (int t0 = w0; t0 < w1; t0 += 32) {
+    const int jb = base + 1 + lane;
     uint32_t bit = 0;
     if (jb < ns) {
-      const int64_t r = S.pre[jb] - t0;
+      const int r = S.pre[jb] - t0;
       if (r < 32) bit = 1u << r;
     }
     const uint32_t M = __reduce_or_sync(0xffffffffu, bit);
-    const uint32_t upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-    const int j = lo + __popc(M & upto);
-    const int64_t t = t0 + lane;
-    if (t < total) f((uint32_t)__ldg(ocol + S.st[j] + (t - S.pre[j])), j);
+    const int j = base + __popc(M & upto);
+    const int t = t0 + lane;
+    const bool valid = t < w1;
+    uint32_t u = 0;
+    if (valid) u = (uint32_t)__ldg(ocol + S.st[j] + (t - S.pre[j]));
+    f(u, j, valid);
+    // owner of t0 + 32
+    base += __popc(M);
+    if (base + 1 < ns && S.pre[base + 1] == t0 + 32) ++base;
   }
 }
 
 size_t seg_bytes() {
-  return (size_t)CHUNK * 8 + (size_t)(CHUNK + 1) * 8 + (size_t)CHUNK * 8 + 64 * 8 + (size_t)CHUNK * 4 + 16;
+  return (size_t)CHUNK * 8 + (size_t)CHUNK * 8 + 64 * 8 + (size_t)(CHUNK + 1) * 4 + (size_t)CHUNK * 4 + 16;
 }
 
 template <typename RP, int MODE>
@@ -354,10 +394,10 @@ __global__ void __launch_bounds__(BLOCK_T) k_cyc_block(const RP* __restrict__ rp
   // dynamic layout: [segments][dense counters][hash keys][hash counts]
   Segs S;
   S.st = reinterpret_cast<int64_t*>(smem);
-  S.pre = S.st + CHUNK;
-  S.acc = reinterpret_cast<u64*>(S.pre + CHUNK + 1);
+  S.acc = reinterpret_cast<u64*>(S.st + CHUNK);
   S.scan = reinterpret_cast<long long*>(S.acc + CHUNK);
-  S.rv = reinterpret_cast<int32_t*>(S.scan + 64);
+  S.pre = reinterpret_cast<int32_t*>(S.scan + 64);
+  S.rv = S.pre + CHUNK + 1;
   S.misc = S.rv + CHUNK;
   uint32_t* after = reinterpret_cast<uint32_t*>(S.misc + 4);
   uint32_t* dense = after;
@@ -413,7 +453,8 @@ __global__ void __launch_bounds__(BLOCK_T) k_cyc_block(const RP* __restrict__ rp
     // Pass A: count the wedges per top u.
     for (int64_t c0 = s; c0 < e; c0 += CHUNK) {
       build_chunk(S, ci, rank, orp, ocol, c0, e, w, n);
-      walk_chunk(S, ocol, [&](uint32_t u, int) {
+      walk_chunk(S, ocol, [&](uint32_t u, int, bool valid) {
+        if (!valid) return;
         if (DENSE && (int32_t)u >= hub_lo) dense_add(u);
         else T.increment(u, hb, err);
       });
@@ -422,9 +463,15 @@ __global__ void __launch_bounds__(BLOCK_T) k_cyc_block(const RP* __restrict__ rp
     // Pass B: each middle gains cnt[u] - 1 per wedge.
     for (int64_t c0 = s; c0 < e; c0 += CHUNK) {
       if (!single) build_chunk(S, ci, rank, orp, ocol, c0, e, w, n);
-      walk_chunk(S, ocol, [&](uint32_t u, int j) {
-        const uint32_t c = (DENSE && (int32_t)u >= hub_lo) ? dense_get(u) : T.count_of(u, hb);
-        if (c > 1) atomicAdd(&S.acc[j], (u64)(c - 1));
+      walk_chunk(S, ocol, [&](uint32_t u, int j, bool valid) {
+        u64 c = 0;
+        if (valid) {
+          c = (DENSE && (int32_t)u >= hub_lo) ? dense_get(u) : T.count_of(u, hb);
+          c = c > 1 ? c - 1 : 0;
+        }
+        bool head;
+        const u64 sum = run_sum(c, valid ? j : -1, head);
+        if (head && valid && sum) atomicAdd(&S.acc[j], sum);
       });
       __syncthreads();
       const int ns = S.misc[0];

@@ -65,6 +65,27 @@ __device__ __forceinline__ int table_find(const uint32_t* keys, const int32_t* v
   return -1;
 }
 
+// Membership pre-filter: one bit per hashed key, about 16 bits per element
+// of N+(a); a clear bit proves the key absent, so most probes of keys not in
+// N+(a) cost one shared-memory load.
+__device__ __forceinline__ int filter_bits_for(int D) {
+  int fb = 5;
+  while ((1 << fb) < 16 * D) ++fb;
+  return fb;
+}
+
+__device__ __forceinline__ uint32_t filter_slot(uint32_t key, int fb) { return (key * 0x85EBCA6Bu) >> (32 - fb); }
+
+__device__ __forceinline__ void filter_set(uint32_t* filt, uint32_t key, int fb) {
+  const uint32_t b = filter_slot(key, fb);
+  atomicOr(&filt[b >> 5], 1u << (b & 31));
+}
+
+__device__ __forceinline__ bool filter_test(const uint32_t* filt, uint32_t key, int fb) {
+  const uint32_t b = filter_slot(key, fb);
+  return (filt[b >> 5] >> (b & 31)) & 1u;
+}
+
 // ---------------------------------------------------------------------------
 // Pass 1
 //
@@ -84,11 +105,18 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
   __shared__ int s_item;
   __shared__ u64 red[32];
   const int Hmax = 1 << Hbits, Wmax = (Dmax + 31) >> 5;
+  const int FWmax = (1 << filter_bits_for(Dmax)) >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   uint32_t* keys = reinterpret_cast<uint32_t*>(smem);
   int32_t* vals = reinterpret_cast<int32_t*>(keys + Hmax);
-  uint32_t* bm = SMEM_BM ? reinterpret_cast<uint32_t*>(vals + Hmax) : (gbm + (size_t)blockIdx.x * Dmax * Wmax);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  uint32_t* filt = reinterpret_cast<uint32_t*>(vals + Hmax);
+  int32_t* ylist = reinterpret_cast<int32_t*>(filt + FWmax) + warp * (Dmax + Wmax);
+  int32_t* wlist = ylist + Dmax;
+  uint32_t* bm = SMEM_BM ? reinterpret_cast<uint32_t*>(reinterpret_cast<int32_t*>(filt + FWmax) +
+                                                       nwarps * (Dmax + Wmax))
+                         : (gbm + (size_t)blockIdx.x * Dmax * Wmax);
   const int total = *nwork;
+  const unsigned below = (1u << lane) - 1u;
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(next, 1);
@@ -100,51 +128,84 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
     const int D = (int)(orp[a + 1] - base);
     int hb = 5;
     while ((1 << hb) < 2 * D) ++hb;
+    const int fb = filter_bits_for(D);
     const int W = (D + 31) >> 5;
 
     for (int i = tid; i < (1 << hb); i += blockDim.x) keys[i] = EMPTY_KEY;
+    for (int i = tid; i < (1 << (fb - 5)); i += blockDim.x) filt[i] = 0u;
     for (int i = tid; i < D * W; i += blockDim.x) bm[i] = 0u;
     __syncthreads();
-    for (int x = tid; x < D; x += blockDim.x) table_insert(keys, vals, (uint32_t)ocol[base + x], x, hb, err);
+    for (int x = tid; x < D; x += blockDim.x) {
+      const uint32_t key = (uint32_t)ocol[base + x];
+      table_insert(keys, vals, key, x, hb, err);
+      filter_set(filt, key, fb);
+    }
     __syncthreads();
 
-    // Triangles {a, b, c}: c in N+(b) ∩ N+(a).
+    // Triangles {a, b, c}: c in N+(b) ∩ N+(a); N+(b) is sorted, so the scan
+    // stops at the first step beyond the largest element of N+(a).
     const int32_t lastA = ocol[base + D - 1];
     u64 probes = 0;
     for (int ib = warp; ib < D; ib += nwarps) {
       const int32_t b = ocol[base + ib];
-      const int64_t bb = orp[b];
-      const int64_t be = upper_bound_i32(ocol, bb, orp[b + 1], lastA);
-      probes += (u64)(be - bb);
+      const int64_t bb = orp[b], be = orp[b + 1];
       uint32_t* row = bm + (size_t)ib * W;
-      for (int64_t k = bb + lane; k < be; k += 32) {
-        const int ic = table_find(keys, vals, (uint32_t)ocol[k], hb);
-        if (ic >= 0) {
-          atomicOr(&row[ic >> 5], 1u << (ic & 31));
-          atomicOr(&bm[(size_t)ic * W + (ib >> 5)], 1u << (ib & 31));
-          atomicAdd(&C3o[k], 1);  // edge b -> c
+      for (int64_t k0 = bb; k0 < be; k0 += 32) {
+        const int64_t k = k0 + lane;
+        const int32_t c = k < be ? ocol[k] : 0x7fffffff;
+        if (__shfl_sync(0xffffffffu, c, 0) > lastA) break;
+        if (c <= lastA) {
+          ++probes;
+          if (filter_test(filt, (uint32_t)c, fb)) {
+            const int ic = table_find(keys, vals, (uint32_t)c, hb);
+            if (ic >= 0) {
+              atomicOr(&row[ic >> 5], 1u << (ic & 31));
+              atomicOr(&bm[(size_t)ic * W + (ib >> 5)], 1u << (ib & 31));
+              atomicAdd(&C3o[k], 1);  // edge b -> c
+            }
+          }
         }
       }
     }
     __syncthreads();
 
-    // Per local vertex x: triangles through edge a-x and 4-cliques through a-x.
+    // Per local vertex x: triangles through edge a-x (popc S_x) and 4-cliques
+    // through a-x (half of sum over y in S_x of |S_x ∩ S_y|).
     u64 tri2x = 0, k4_6x = 0;
     for (int x = warp; x < D; x += nwarps) {
       const uint32_t* Sx = bm + (size_t)x * W;
-      int deg = 0;
-      for (int w = lane; w < W; w += 32) deg += __popc(Sx[w]);
-      deg = warp_sum_i32(deg);
-      long long k2 = 0;  // sum over y in S_x of |S_x ∩ S_y|
-      for (int w0 = 0; w0 < W; ++w0) {
-        const uint32_t bits = Sx[w0];
-        if (!bits) continue;
-        if ((bits >> lane) & 1u) {
-          const uint32_t* Sy = bm + (size_t)((w0 << 5) + lane) * W;
-          int k = 0;
-          for (int w = 0; w < W; ++w) k += __popc(Sx[w] & Sy[w]);
-          k2 += k;
+      int deg = 0, nzw = 0;
+      for (int w0 = 0; w0 < W; w0 += 32) {
+        const int w = w0 + lane;
+        uint32_t bits = w < W ? Sx[w] : 0u;
+        const unsigned mz = __ballot_sync(0xffffffffu, bits != 0u);
+        if (bits) wlist[nzw + __popc(mz & below)] = w;
+        nzw += __popc(mz);
+        const int c = __popc(bits);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
         }
+        int p = deg + incl - c;
+        while (bits) {
+          const int t = __ffs(bits) - 1;
+          bits &= bits - 1;
+          ylist[p++] = (w << 5) + t;
+        }
+        deg += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      __syncwarp();
+      long long k2 = 0;
+      for (int i = lane; i < deg; i += 32) {
+        const uint32_t* Sy = bm + (size_t)ylist[i] * W;
+        int k = 0;
+        for (int q = 0; q < nzw; ++q) {
+          const int w = wlist[q];
+          k += __popc(Sx[w] & Sy[w]);
+        }
+        k2 += k;
       }
       k2 = warp_sum_i64(k2);
       if (lane == 0) {
@@ -157,10 +218,11 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
         tri2x += (u64)deg;
         k4_6x += (u64)k2;
       }
+      __syncwarp();
     }
     const u64 tri_sum = block_sum(tri2x, red) / 2;
     const u64 k4_sum = block_sum(k4_6x, red) / 6;
-    const u64 probe_sum = block_sum(lane == 0 ? probes : (u64)0, red);
+    const u64 probe_sum = block_sum(probes, red);
     if (tid == 0) {
       if (tri_sum) atomicAdd(&c3r[a], tri_sum);
       if (k4_sum) atomicAdd(&k4r[a], k4_sum);
@@ -187,6 +249,7 @@ __global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp,
   uint32_t* keys = reinterpret_cast<uint32_t*>(acc + Dmax);
   int32_t* vals = reinterpret_cast<int32_t*>(keys + Hmax);
   int32_t* tv = vals + Hmax;
+  uint32_t* filt = reinterpret_cast<uint32_t*>(tv + Dmax);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int total = *nwork;
 
@@ -200,27 +263,37 @@ __global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp,
     const int D = (int)(orp[a + 1] - base);
     int hb = 5;
     while ((1 << hb) < 2 * D) ++hb;
+    const int fb = filter_bits_for(D);
 
     for (int i = tid; i < (1 << hb); i += blockDim.x) keys[i] = EMPTY_KEY;
+    for (int i = tid; i < (1 << (fb - 5)); i += blockDim.x) filt[i] = 0u;
     for (int i = tid; i < D; i += blockDim.x) { acc[i] = 0; tv[i] = C3o[base + i]; }
     __syncthreads();
-    for (int x = tid; x < D; x += blockDim.x) table_insert(keys, vals, (uint32_t)ocol[base + x], x, hb, err);
+    for (int x = tid; x < D; x += blockDim.x) {
+      const uint32_t key = (uint32_t)ocol[base + x];
+      table_insert(keys, vals, key, x, hb, err);
+      filter_set(filt, key, fb);
+    }
     __syncthreads();
 
     const int32_t lastA = ocol[base + D - 1];
     long long acc_a = 0;
     for (int ib = warp; ib < D; ib += nwarps) {
       const int32_t b = ocol[base + ib];
-      const int64_t bb = orp[b];
-      const int64_t be = upper_bound_i32(ocol, bb, orp[b + 1], lastA);
+      const int64_t bb = orp[b], be = orp[b + 1];
       const long long tab = tv[ib];
       long long accb = 0;
-      for (int64_t k = bb + lane; k < be; k += 32) {
-        const int ic = table_find(keys, vals, (uint32_t)ocol[k], hb);
-        if (ic >= 0) {
-          acc_a += (long long)C3o[k] - 1;  // a: opposite edge b-c
-          accb += (long long)tv[ic] - 1;   // b: opposite edge a-c
-          if (tab > 1) atomicAdd(&acc[ic], (u64)(tab - 1));  // c: opposite edge a-b
+      for (int64_t k0 = bb; k0 < be; k0 += 32) {
+        const int64_t k = k0 + lane;
+        const int32_t c = k < be ? ocol[k] : 0x7fffffff;
+        if (__shfl_sync(0xffffffffu, c, 0) > lastA) break;
+        if (c <= lastA && filter_test(filt, (uint32_t)c, fb)) {
+          const int ic = table_find(keys, vals, (uint32_t)c, hb);
+          if (ic >= 0) {
+            acc_a += (long long)C3o[k] - 1;  // a: opposite edge b-c
+            accb += (long long)tv[ic] - 1;   // b: opposite edge a-c
+            if (tab > 1) atomicAdd(&acc[ic], (u64)(tab - 1));  // c: opposite edge a-b
+          }
         }
       }
       accb = warp_sum_i64(accb);
@@ -235,10 +308,16 @@ __global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp,
   }
 }
 
+int host_filter_words(int D) {
+  int fb = 5;
+  while ((1 << fb) < 16 * D) ++fb;
+  return (1 << fb) >> 5;
+}
+
 size_t tri1_smem_impl(int D, bool smem_bm) {
   const int H = 1 << hash_bits_for(D);
   const size_t W = (size_t)(D + 31) / 32;
-  size_t bytes = (size_t)H * 8;
+  size_t bytes = (size_t)H * 8 + (size_t)host_filter_words(D) * 4 + (size_t)(TRI_T / 32) * (D + W) * 4;
   if (smem_bm) bytes += (size_t)D * W * 4;
   return (bytes + 15) & ~(size_t)15;
 }
@@ -258,7 +337,7 @@ size_t tri1_smem_bytes(int dpmax, bool bitmap_in_smem) { return tri1_smem_impl(d
 
 size_t tri2_smem_bytes(int dpmax) {
   const int H = 1 << hash_bits_for(dpmax);
-  return (((size_t)dpmax * 12 + (size_t)H * 8) + 15) & ~(size_t)15;
+  return (((size_t)dpmax * 12 + (size_t)H * 8 + (size_t)host_filter_words(dpmax) * 4) + 15) & ~(size_t)15;
 }
 
 int tri_grid_blocks() { return num_sms(); }
