@@ -16,7 +16,7 @@ from typing import Optional
 
 import numpy as np
 
-from . import build as _build
+from . import buildlib as _build
 
 NUM_GRAPHLETS = 16
 

@@ -33,7 +33,7 @@ namespace {
 constexpr int WARP_HASH = 1024;   // slots per warp table
 constexpr int WARP_CAP = 512;     // most wedges handled by one warp table
 constexpr int WARP_T = 256;
-constexpr int BLOCK_T = 512;
+constexpr int BLOCK_T = 1024;
 constexpr int DENSE_WORDS = 16384;  // 64 KB of counters
 constexpr int DHASH_BITS = 12;      // 4096-slot table for the non-hub tops
 constexpr int BHASH_BITS = 13;      // largest per-w table of the hash-only block class
@@ -255,15 +255,21 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const RP* __restrict__ rp, 
 // MODE 2: dense 32-bit counters for tops >= hub_lo + 2^12-slot shared hash
 // MODE 3: hash table in global memory sized per w (fallback)
 // ---------------------------------------------------------------------------
-constexpr int CHUNK = BLOCK_T;
+constexpr int CHUNK = 512;  // middles per chunk (at most BLOCK_T)
+static_assert(CHUNK <= BLOCK_T, "one middle per thread");
+
+constexpr int LONG_SEG = 32;  // segments at least this long are walked by one warp
 
 struct Segs {
-  int64_t* st;      // [CHUNK] segment start in ocol
-  int32_t* pre;     // [CHUNK + 1] exclusive wedge prefix (a chunk holds < 2^31 wedges)
-  u64* acc;         // [CHUNK] middle credits
+  int64_t* st;      // [CHUNK] short segments: start in ocol
+  int32_t* pre;     // [CHUNK + 1] short segments: exclusive wedge prefix
+  u64* acc;         // [CHUNK] short segments: middle credits
   long long* scan;  // [64] block-scan scratch
-  int32_t* rv;      // [CHUNK] rank of the middle
-  int* misc;        // [0] = segment count
+  int32_t* rv;      // [CHUNK] short segments: rank of the middle
+  int64_t* lst;     // [CHUNK] long segments: start in ocol
+  int32_t* llen;    // [CHUNK] long segments: length
+  int32_t* lrv;     // [CHUNK] long segments: rank of the middle
+  int* misc;        // [0] short count, [1] long count, [2] long cursor
 };
 
 // Block-wide exclusive scan (blockDim.x == BLOCK_T); *total = sum.
@@ -295,7 +301,9 @@ __device__ __forceinline__ long long block_excl_scan(long long x, long long* scr
   return r;
 }
 
-// Compacted segments of the middles colidx[c0 .. c0 + CHUNK).
+// Segments of the middles colidx[c0 .. c0 + CHUNK): long ones listed for
+// warp-per-segment walks, short non-empty ones compacted with their wedge
+// prefix for the flattened walk (one packed block scan).
 __device__ __forceinline__ void build_chunk(const Segs& S, const int32_t* __restrict__ ci,
                                             const int32_t* __restrict__ rank, const int64_t* __restrict__ orp,
                                             const int32_t* __restrict__ ocol, int64_t c0, int64_t e, int32_t w,
@@ -303,7 +311,7 @@ __device__ __forceinline__ void build_chunk(const Segs& S, const int32_t* __rest
   const int64_t k = c0 + threadIdx.x;
   int32_t rv = -1;
   int64_t st = 0, len = 0;
-  if (k < e) {
+  if (threadIdx.x < CHUNK && k < e) {
     const int32_t v = __ldg(ci + k);
     if ((uint32_t)v < (uint64_t)n) {
       rv = __ldg(rank + v);
@@ -312,20 +320,52 @@ __device__ __forceinline__ void build_chunk(const Segs& S, const int32_t* __rest
       len = oe - st;
     }
   }
-  long long nseg, total;
-  const long long pos = block_excl_scan(len > 0 ? 1 : 0, S.scan, &nseg);
-  const long long off = block_excl_scan(len, S.scan, &total);
-  if (len > 0) {
+  const bool is_long = len >= LONG_SEG;
+  const bool is_short = len > 0 && !is_long;
+  // packed: [short wedge sum : 32 | short count : 16 | long count : 16]
+  const long long packed = ((is_short ? len : 0LL) << 32) | ((long long)is_short << 16) | (long long)is_long;
+  long long tot;
+  const long long ex = block_excl_scan(packed, S.scan, &tot);
+  if (is_short) {
+    const int pos = (int)((ex >> 16) & 0xFFFF);
     S.st[pos] = st;
-    S.pre[pos] = (int32_t)off;
+    S.pre[pos] = (int32_t)(ex >> 32);
     S.rv[pos] = rv;
     S.acc[pos] = 0;
+  } else if (is_long) {
+    const int pos = (int)(ex & 0xFFFF);
+    S.lst[pos] = st;
+    S.llen[pos] = (int32_t)len;
+    S.lrv[pos] = rv;
   }
   if (threadIdx.x == 0) {
-    S.misc[0] = (int)nseg;
-    S.pre[nseg] = (int32_t)total;
+    const int ns = (int)((tot >> 16) & 0xFFFF);
+    S.misc[0] = ns;
+    S.misc[1] = (int)(tot & 0xFFFF);
+    S.misc[2] = 0;
+    S.pre[ns] = (int32_t)(tot >> 32);
   }
   __syncthreads();
+}
+
+// Long segments: warps take them one at a time; lanes stride over the
+// segment (coalesced, one owner). g(u) per wedge; done(rv, lane_sum) after
+// each segment with the warp's sum of g's return values.
+template <typename G, typename D>
+__device__ __forceinline__ void walk_long(const Segs& S, const int32_t* __restrict__ ocol, G g, D done) {
+  const int lane = threadIdx.x & 31;
+  const int nl = S.misc[1];
+  for (;;) {
+    int i = 0;
+    if (lane == 0) i = atomicAdd(&S.misc[2], 1);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= nl) break;
+    const int32_t* p = ocol + S.lst[i];
+    const int len = S.llen[i];
+    u64 sum = 0;
+    for (int q = lane; q < len; q += 32) sum += g((uint32_t)__ldg(p + q));
+    done(S.lrv[i], sum);
+  }
 }
 
 // Walks the current chunk's wedges. Warp k takes the contiguous range
@@ -371,7 +411,7 @@ __device__ __forceinline__ void walk_chunk(const Segs& S, const int32_t* __restr
 }
 
 size_t seg_bytes() {
-  return (size_t)CHUNK * 8 + (size_t)CHUNK * 8 + 64 * 8 + (size_t)(CHUNK + 1) * 4 + (size_t)CHUNK * 4 + 16;
+  return (size_t)CHUNK * 8 * 3 + 64 * 8 + (size_t)(CHUNK + 1) * 4 + (size_t)CHUNK * 4 * 3 + 16;
 }
 
 template <typename RP, int MODE>
@@ -395,10 +435,13 @@ __global__ void __launch_bounds__(BLOCK_T) k_cyc_block(const RP* __restrict__ rp
   Segs S;
   S.st = reinterpret_cast<int64_t*>(smem);
   S.acc = reinterpret_cast<u64*>(S.st + CHUNK);
-  S.scan = reinterpret_cast<long long*>(S.acc + CHUNK);
+  S.lst = reinterpret_cast<int64_t*>(S.acc + CHUNK);
+  S.scan = reinterpret_cast<long long*>(S.lst + CHUNK);
   S.pre = reinterpret_cast<int32_t*>(S.scan + 64);
   S.rv = S.pre + CHUNK + 1;
-  S.misc = S.rv + CHUNK;
+  S.llen = S.rv + CHUNK;
+  S.lrv = S.llen + CHUNK;
+  S.misc = S.lrv + CHUNK;
   uint32_t* after = reinterpret_cast<uint32_t*>(S.misc + 4);
   uint32_t* dense = after;
   uint32_t* hbase = DENSE ? after + DENSE_WORDS : after;
@@ -450,25 +493,37 @@ __global__ void __launch_bounds__(BLOCK_T) k_cyc_block(const RP* __restrict__ rp
     const int64_t wo = perm[w];
     const int64_t s = (int64_t)rp[wo], e = (int64_t)rp[wo + 1];
     const bool single = e - s <= CHUNK;
+    auto count = [&](uint32_t u) {
+      if (DENSE && (int32_t)u >= hub_lo) dense_add(u);
+      else T.increment(u, hb, err);
+    };
+    auto credit = [&](uint32_t u) -> u64 {
+      const uint32_t c = (DENSE && (int32_t)u >= hub_lo) ? dense_get(u) : T.count_of(u, hb);
+      return c > 1 ? (u64)(c - 1) : 0;
+    };
     // Pass A: count the wedges per top u.
     for (int64_t c0 = s; c0 < e; c0 += CHUNK) {
       build_chunk(S, ci, rank, orp, ocol, c0, e, w, n);
+      walk_long(S, ocol, [&](uint32_t u) -> u64 { count(u); return 0; }, [](int32_t, u64) {});
       walk_chunk(S, ocol, [&](uint32_t u, int, bool valid) {
-        if (!valid) return;
-        if (DENSE && (int32_t)u >= hub_lo) dense_add(u);
-        else T.increment(u, hb, err);
+        if (valid) count(u);
       });
       __syncthreads();
     }
     // Pass B: each middle gains cnt[u] - 1 per wedge.
     for (int64_t c0 = s; c0 < e; c0 += CHUNK) {
-      if (!single) build_chunk(S, ci, rank, orp, ocol, c0, e, w, n);
+      if (!single) {
+        build_chunk(S, ci, rank, orp, ocol, c0, e, w, n);
+      } else {
+        if (tid == 0) S.misc[2] = 0;
+        __syncthreads();
+      }
+      walk_long(S, ocol, credit, [&](int32_t rv, u64 sum) {
+        sum = warp_sum_u64(sum);
+        if ((tid & 31) == 0 && sum) atomicAdd(&r12r[rv], sum);
+      });
       walk_chunk(S, ocol, [&](uint32_t u, int j, bool valid) {
-        u64 c = 0;
-        if (valid) {
-          c = (DENSE && (int32_t)u >= hub_lo) ? dense_get(u) : T.count_of(u, hb);
-          c = c > 1 ? c - 1 : 0;
-        }
+        const u64 c = valid ? credit(u) : 0;
         bool head;
         const u64 sum = run_sum(c, valid ? j : -1, head);
         if (head && valid && sum) atomicAdd(&S.acc[j], sum);

@@ -150,10 +150,7 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
       const int32_t b = ocol[base + ib];
       const int64_t bb = orp[b], be = orp[b + 1];
       uint32_t* row = bm + (size_t)ib * W;
-      for (int64_t k0 = bb; k0 < be; k0 += 32) {
-        const int64_t k = k0 + lane;
-        const int32_t c = k < be ? ocol[k] : 0x7fffffff;
-        if (__shfl_sync(0xffffffffu, c, 0) > lastA) break;
+      auto probe = [&](int32_t c, int64_t k) {
         if (c <= lastA) {
           ++probes;
           if (filter_test(filt, (uint32_t)c, fb)) {
@@ -165,6 +162,15 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
             }
           }
         }
+      };
+      // two steps per iteration so that both loads are in flight together
+      for (int64_t k0 = bb; k0 < be; k0 += 64) {
+        const int64_t k1 = k0 + lane, k2 = k1 + 32;
+        const int32_t c1 = k1 < be ? ocol[k1] : 0x7fffffff;
+        const int32_t c2 = k2 < be ? ocol[k2] : 0x7fffffff;
+        probe(c1, k1);
+        probe(c2, k2);
+        if (__shfl_sync(0xffffffffu, c2, 31) > lastA) break;
       }
     }
     __syncthreads();
@@ -283,10 +289,7 @@ __global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp,
       const int64_t bb = orp[b], be = orp[b + 1];
       const long long tab = tv[ib];
       long long accb = 0;
-      for (int64_t k0 = bb; k0 < be; k0 += 32) {
-        const int64_t k = k0 + lane;
-        const int32_t c = k < be ? ocol[k] : 0x7fffffff;
-        if (__shfl_sync(0xffffffffu, c, 0) > lastA) break;
+      auto probe = [&](int32_t c, int64_t k) {
         if (c <= lastA && filter_test(filt, (uint32_t)c, fb)) {
           const int ic = table_find(keys, vals, (uint32_t)c, hb);
           if (ic >= 0) {
@@ -295,6 +298,14 @@ __global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp,
             if (tab > 1) atomicAdd(&acc[ic], (u64)(tab - 1));  // c: opposite edge a-b
           }
         }
+      };
+      for (int64_t k0 = bb; k0 < be; k0 += 64) {
+        const int64_t k1 = k0 + lane, k2 = k1 + 32;
+        const int32_t c1 = k1 < be ? ocol[k1] : 0x7fffffff;
+        const int32_t c2 = k2 < be ? ocol[k2] : 0x7fffffff;
+        probe(c1, k1);
+        probe(c2, k2);
+        if (__shfl_sync(0xffffffffu, c2, 31) > lastA) break;
       }
       accb = warp_sum_i64(accb);
       if (lane == 0 && accb) atomicAdd(&acc[ib], (u64)accb);
