@@ -34,8 +34,9 @@ enum BufId {
 
 // Small device counters, one int slot each.
 enum CounterId {
-  C_DMAX, C_NHEAVY, C_DPMAX, C_NTRI, C_NEXT1, C_NEXT2, C_NCYC0, C_NCYC1, C_NCYC2, C_NCYC3, C_NEXTC0,
-  C_NEXTC1, C_NEXTC2, C_NEXTC3, C_ERR, C_NUM
+  C_DMAX, C_NHEAVY, C_DPMAX, C_NTRI0, C_NTRI1, C_NTRI2, C_NEXT1_0, C_NEXT1_1, C_NEXT1_2, C_NEXT2_0,
+  C_NEXT2_1, C_NEXT2_2, C_NCYC0, C_NCYC1, C_NCYC2, C_NCYC3, C_NEXTC0, C_NEXTC1, C_NEXTC2, C_NEXTC3, C_ERR,
+  C_NUM
 };
 // 64-bit work counters: triangle-pass scanned entries, triangles, 4-cliques,
 // max and total wedges of the 4-cycle stage.
@@ -248,9 +249,14 @@ fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out
     NEED(B_SORT, P, sort_scratch);
   }
   CK(launch_sort_rows(orp, n, dpmax, ocol, sort_scratch, st));
+  // Triangle-pass work lists by out-degree; each class is launched with shared
+  // memory sized for its largest out-degree.
+  constexpr int TRI_T0 = 64, TRI_T1 = 256;
   int32_t* twork;
-  NEED(B_TWORK, n, twork);
-  CK(launch_worklist_outdeg(opc, n, 2, twork, cnt + C_NTRI, st));
+  NEED(B_TWORK, 3 * n, twork);
+  CK(launch_worklist_outdeg3(opc, n, 2, TRI_T0, TRI_T1, twork, n, cnt + C_NTRI0, st));
+  const int tri_cap[3] = {std::min(dpmax, TRI_T0), std::min(dpmax, TRI_T1), dpmax};
+  const bool tri_on[3] = {dpmax >= 2, dpmax > TRI_T0, dpmax > TRI_T1};
 
   // Triangle pass 1: C3, c3, 4-cliques.
   mark(5);
@@ -270,8 +276,10 @@ fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out
     gbm = static_cast<uint32_t*>(p);
   }
   if (dpmax >= 2 && tri2_smem_bytes(dpmax) > 227 * 1024) return FGLT_ERR_UNSUPPORTED;
-  CK(launch_tri1(orp, ocol, twork, cnt + C_NTRI, cnt + C_NEXT1, dpmax, C3o, c3r, k4r, gbm, ctr + W_PROBES, err,
-                 st));
+  for (int c = 0; c < 3; ++c)
+    if (tri_on[c])
+      CK(launch_tri1(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT1_0 + c, tri_cap[c], C3o, c3r, k4r,
+                     c == 2 ? gbm : nullptr, ctr + W_PROBES, err, st));
 
   // Edge terms of the final C3, then SpMV chain 2.
   mark(6);
@@ -295,7 +303,10 @@ fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out
   u64* r13r;
   NEED(B_R13R, n, r13r);
   CK(cudaMemsetAsync(r13r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
-  CK(launch_tri2(orp, ocol, twork, cnt + C_NTRI, cnt + C_NEXT2, dpmax, C3o, r13r, err, st));
+  for (int c = 0; c < 3; ++c)
+    if (tri_on[c])
+      CK(launch_tri2(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT2_0 + c, tri_cap[c], C3o, r13r, err,
+                     st));
 
   // 4-cycles.
   mark(9);

@@ -54,6 +54,10 @@ cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int32
 // Vertices (rank labels) with at least `min_out` out-neighbours.
 cudaError_t launch_worklist_outdeg(const int32_t* opc, int64_t n, int min_out, int32_t* list,
                                    int32_t* count, cudaStream_t st);
+// The same split into three lists by out-degree: [min_out, t0], (t0, t1],
+// (t1, ...) at lists + c * stride, sizes in counts[0..2].
+cudaError_t launch_worklist_outdeg3(const int32_t* opc, int64_t n, int min_out, int t0, int t1, int32_t* lists,
+                                    int64_t stride, int32_t* counts, cudaStream_t st);
 
 // --- scans -----------------------------------------------------------------
 // out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.

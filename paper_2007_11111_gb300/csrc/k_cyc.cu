@@ -33,9 +33,8 @@ namespace {
 constexpr int WARP_HASH = 1024;   // slots per warp table
 constexpr int WARP_CAP = 512;     // most wedges handled by one warp table
 constexpr int WARP_T = 256;
-constexpr int BLOCK_T = 1024;
 constexpr int DENSE_WORDS = 16384;  // 64 KB of counters
-constexpr int DHASH_BITS = 12;      // 4096-slot table for the non-hub tops
+constexpr int DHASH_BITS = 11;      // 2048-slot table for the non-hub tops
 constexpr int BHASH_BITS = 13;      // largest per-w table of the hash-only block class
 constexpr int BLOCK_CAP = 1 << (BHASH_BITS - 1);
 
@@ -244,7 +243,7 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const RP* __restrict__ rp, 
 }
 
 // ---------------------------------------------------------------------------
-// Larger vertices: one block per w. N(w) is taken CHUNK middles at a time;
+// Larger vertices: one block per w. N(w) is taken CH middles at a time;
 // the non-empty segments of the chunk are compacted into shared memory with
 // their exclusive wedge prefix, and the chunk's wedges are split evenly over
 // the block's warps, 32 consecutive wedges per warp step (the owner of each
@@ -255,24 +254,23 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const RP* __restrict__ rp, 
 // MODE 2: dense 32-bit counters for tops >= hub_lo + 2^12-slot shared hash
 // MODE 3: hash table in global memory sized per w (fallback)
 // ---------------------------------------------------------------------------
-constexpr int CHUNK = 512;  // middles per chunk (at most BLOCK_T)
-static_assert(CHUNK <= BLOCK_T, "one middle per thread");
+constexpr int CHUNK_MAX = 512;  // middles per chunk: min(block size, 512)
 
 constexpr int LONG_SEG = 32;  // segments at least this long are walked by one warp
 
 struct Segs {
-  int64_t* st;      // [CHUNK] short segments: start in ocol
-  int32_t* pre;     // [CHUNK + 1] short segments: exclusive wedge prefix
-  u64* acc;         // [CHUNK] short segments: middle credits
+  int64_t* st;      // [chunk] short segments: start in ocol
+  int32_t* pre;     // [chunk + 1] short segments: exclusive wedge prefix
+  u64* acc;         // [chunk] short segments: middle credits
   long long* scan;  // [64] block-scan scratch
-  int32_t* rv;      // [CHUNK] short segments: rank of the middle
-  int64_t* lst;     // [CHUNK] long segments: start in ocol
-  int32_t* llen;    // [CHUNK] long segments: length
-  int32_t* lrv;     // [CHUNK] long segments: rank of the middle
+  int32_t* rv;      // [chunk] short segments: rank of the middle
+  int64_t* lst;     // [chunk] long segments: start in ocol
+  int32_t* llen;    // [chunk] long segments: length
+  int32_t* lrv;     // [chunk] long segments: rank of the middle
   int* misc;        // [0] short count, [1] long count, [2] long cursor
 };
 
-// Block-wide exclusive scan (blockDim.x == BLOCK_T); *total = sum.
+// Block-wide exclusive scan; *total = sum.
 __device__ __forceinline__ long long block_excl_scan(long long x, long long* scratch, long long* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   long long incl = x;
@@ -284,7 +282,7 @@ __device__ __forceinline__ long long block_excl_scan(long long x, long long* scr
   if (lane == 31) scratch[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    const long long wv = lane < (BLOCK_T / 32) ? scratch[lane] : 0;
+    const long long wv = lane < (int)(blockDim.x >> 5) ? scratch[lane] : 0;
     long long wi = wv;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -301,17 +299,17 @@ __device__ __forceinline__ long long block_excl_scan(long long x, long long* scr
   return r;
 }
 
-// Segments of the middles colidx[c0 .. c0 + CHUNK): long ones listed for
+// Segments of the middles colidx[c0 .. c0 + chunk): long ones listed for
 // warp-per-segment walks, short non-empty ones compacted with their wedge
 // prefix for the flattened walk (one packed block scan).
 __device__ __forceinline__ void build_chunk(const Segs& S, const int32_t* __restrict__ ci,
                                             const int32_t* __restrict__ rank, const int64_t* __restrict__ orp,
                                             const int32_t* __restrict__ ocol, int64_t c0, int64_t e, int32_t w,
-                                            int64_t n) {
+                                            int64_t n, int chunk) {
   const int64_t k = c0 + threadIdx.x;
   int32_t rv = -1;
   int64_t st = 0, len = 0;
-  if (threadIdx.x < CHUNK && k < e) {
+  if ((int)threadIdx.x < chunk && k < e) {
     const int32_t v = __ldg(ci + k);
     if ((uint32_t)v < (uint64_t)n) {
       rv = __ldg(rank + v);
@@ -410,12 +408,12 @@ __device__ __forceinline__ void walk_chunk(const Segs& S, const int32_t* __restr
   }
 }
 
-size_t seg_bytes() {
-  return (size_t)CHUNK * 8 * 3 + 64 * 8 + (size_t)(CHUNK + 1) * 4 + (size_t)CHUNK * 4 * 3 + 16;
+size_t seg_bytes(int ch) {
+  return (size_t)ch * 8 * 3 + 64 * 8 + (size_t)(ch + 1) * 4 + (size_t)ch * 4 * 3 + 16;
 }
 
-template <typename RP, int MODE>
-__global__ void __launch_bounds__(BLOCK_T) k_cyc_block(const RP* __restrict__ rp, const int32_t* __restrict__ ci,
+template <typename RP, int MODE, int BT>
+__global__ void __launch_bounds__(BT) k_cyc_block(const RP* __restrict__ rp, const int32_t* __restrict__ ci,
                                                        const int32_t* __restrict__ rank,
                                                        const int32_t* __restrict__ perm,
                                                        const int64_t* __restrict__ orp,
@@ -428,20 +426,21 @@ __global__ void __launch_bounds__(BLOCK_T) k_cyc_block(const RP* __restrict__ rp
   constexpr bool DENSE = MODE == 1 || MODE == 2;
   constexpr bool C16 = MODE == 1;
   constexpr bool GMEM = MODE == 3;
+  constexpr int CH = BT < CHUNK_MAX ? BT : CHUNK_MAX;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ u64 red[32];
   // dynamic layout: [segments][dense counters][hash keys][hash counts]
   Segs S;
   S.st = reinterpret_cast<int64_t*>(smem);
-  S.acc = reinterpret_cast<u64*>(S.st + CHUNK);
-  S.lst = reinterpret_cast<int64_t*>(S.acc + CHUNK);
-  S.scan = reinterpret_cast<long long*>(S.lst + CHUNK);
+  S.acc = reinterpret_cast<u64*>(S.st + CH);
+  S.lst = reinterpret_cast<int64_t*>(S.acc + CH);
+  S.scan = reinterpret_cast<long long*>(S.lst + CH);
   S.pre = reinterpret_cast<int32_t*>(S.scan + 64);
-  S.rv = S.pre + CHUNK + 1;
-  S.llen = S.rv + CHUNK;
-  S.lrv = S.llen + CHUNK;
-  S.misc = S.lrv + CHUNK;
+  S.rv = S.pre + CH + 1;
+  S.llen = S.rv + CH;
+  S.lrv = S.llen + CH;
+  S.misc = S.lrv + CH;
   uint32_t* after = reinterpret_cast<uint32_t*>(S.misc + 4);
   uint32_t* dense = after;
   uint32_t* hbase = DENSE ? after + DENSE_WORDS : after;
@@ -492,7 +491,7 @@ __global__ void __launch_bounds__(BLOCK_T) k_cyc_block(const RP* __restrict__ rp
 
     const int64_t wo = perm[w];
     const int64_t s = (int64_t)rp[wo], e = (int64_t)rp[wo + 1];
-    const bool single = e - s <= CHUNK;
+    const bool single = e - s <= CH;
     auto count = [&](uint32_t u) {
       if (DENSE && (int32_t)u >= hub_lo) dense_add(u);
       else T.increment(u, hb, err);
@@ -502,8 +501,8 @@ __global__ void __launch_bounds__(BLOCK_T) k_cyc_block(const RP* __restrict__ rp
       return c > 1 ? (u64)(c - 1) : 0;
     };
     // Pass A: count the wedges per top u.
-    for (int64_t c0 = s; c0 < e; c0 += CHUNK) {
-      build_chunk(S, ci, rank, orp, ocol, c0, e, w, n);
+    for (int64_t c0 = s; c0 < e; c0 += CH) {
+      build_chunk(S, ci, rank, orp, ocol, c0, e, w, n, CH);
       walk_long(S, ocol, [&](uint32_t u) -> u64 { count(u); return 0; }, [](int32_t, u64) {});
       walk_chunk(S, ocol, [&](uint32_t u, int, bool valid) {
         if (valid) count(u);
@@ -511,9 +510,9 @@ __global__ void __launch_bounds__(BLOCK_T) k_cyc_block(const RP* __restrict__ rp
       __syncthreads();
     }
     // Pass B: each middle gains cnt[u] - 1 per wedge.
-    for (int64_t c0 = s; c0 < e; c0 += CHUNK) {
+    for (int64_t c0 = s; c0 < e; c0 += CH) {
       if (!single) {
-        build_chunk(S, ci, rank, orp, ocol, c0, e, w, n);
+        build_chunk(S, ci, rank, orp, ocol, c0, e, w, n, CH);
       } else {
         if (tid == 0) S.misc[2] = 0;
         __syncthreads();
@@ -600,8 +599,13 @@ int occupancy(const void* fn, int threads, size_t smem) {
   return per_sm < 1 ? 1 : per_sm;
 }
 
-size_t block_smem(int mode) {
-  const size_t seg = seg_bytes();
+// Block sizes: medium vertices (hash-only class) have a few thousand wedges,
+// so a 256-thread block keeps every warp busy between the per-vertex
+// barriers; heavy vertices use 1024 threads.
+constexpr int BT_HASH = 256, BT_HEAVY = 1024;
+
+size_t block_smem(int mode, int bt) {
+  const size_t seg = seg_bytes(bt < CHUNK_MAX ? bt : CHUNK_MAX);
   if (mode == 0) return seg + ((size_t)8 << BHASH_BITS);
   if (mode == 1 || mode == 2) return seg + (size_t)DENSE_WORDS * 4 + ((size_t)8 << DHASH_BITS);
   return seg;
@@ -609,15 +613,15 @@ size_t block_smem(int mode) {
 
 int gmem_blocks() { return num_sms(); }
 
-template <typename RP, int MODE>
+template <typename RP, int MODE, int BT>
 void launch_block(const RP* rp, const Csr& g, const CycArgs& a, int cls, cudaStream_t st) {
-  const size_t smem = block_smem(MODE);
-  cudaFuncSetAttribute(k_cyc_block<RP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = block_smem(MODE, BT);
+  cudaFuncSetAttribute(k_cyc_block<RP, MODE, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int grid = MODE == 3 ? gmem_blocks()
-                             : num_sms() * occupancy((const void*)k_cyc_block<RP, MODE>, BLOCK_T, smem);
-  k_cyc_block<RP, MODE><<<grid, BLOCK_T, smem, st>>>(rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc,
-                                                     a.lists + cls * a.list_stride, a.counts + cls, a.next + cls,
-                                                     a.r12r, g.n, a.hub_lo, a.gbits, a.gkeys, a.gcnt, a.err);
+                             : num_sms() * occupancy((const void*)k_cyc_block<RP, MODE, BT>, BT, smem);
+  k_cyc_block<RP, MODE, BT><<<grid, BT, smem, st>>>(rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc,
+                                                    a.lists + cls * a.list_stride, a.counts + cls, a.next + cls,
+                                                    a.r12r, g.n, a.hub_lo, a.gbits, a.gkeys, a.gcnt, a.err);
 }
 
 template <typename RP>
@@ -628,10 +632,10 @@ cudaError_t launch_rp(const Csr& g, const CycArgs& a, cudaStream_t st) {
   cudaFuncSetAttribute(k_cyc_warp<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
   k_cyc_warp<RP><<<sms * occupancy((const void*)k_cyc_warp<RP>, WARP_T, wsmem), WARP_T, wsmem, st>>>(
       rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc, a.lists, a.counts, a.next + 0, a.r12r, g.n, a.err);
-  launch_block<RP, 0>(rp, g, a, 1, st);
-  if (a.c16) launch_block<RP, 1>(rp, g, a, 2, st);
-  else launch_block<RP, 2>(rp, g, a, 2, st);
-  if (a.gkeys) launch_block<RP, 3>(rp, g, a, 3, st);
+  launch_block<RP, 0, BT_HASH>(rp, g, a, 1, st);
+  if (a.c16) launch_block<RP, 1, BT_HEAVY>(rp, g, a, 2, st);
+  else launch_block<RP, 2, BT_HEAVY>(rp, g, a, 2, st);
+  if (a.gkeys) launch_block<RP, 3, BT_HEAVY>(rp, g, a, 3, st);
   return cudaGetLastError();
 }
 
