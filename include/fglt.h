@@ -167,6 +167,31 @@ fglt_status fglt_stage_times(fglt_t handle, const char** names, float* ms,
  * FGLT_ERR_NOT_FOUND if no transform has completed on the handle. */
 fglt_status fglt_work_counters(fglt_t handle, int64_t* counters, int max_counters, int* count);
 
+/*
+ * Single-graph transform that allocates nothing (no cudaMalloc, cudaFree or
+ * other allocating call) — for callers that cannot allocate device memory at
+ * call time: a process whose device memory is already owned by another
+ * allocator (so cudaMalloc could fail at any point), a latency-bound loop that
+ * cannot afford the device-wide synchronisation allocation may cause, or code
+ * that must fix its memory use when the library loads. The paper has no
+ * counterpart; this is a library facility.
+ *   Same arguments and results as fglt_transform, without a handle; stream may
+ *   be NULL (the legacy default stream). Returns after the work completed.
+ *   Scratch: one file-scope device array of FGLT_NOALLOC_SCRATCH_BYTES held by
+ *   every device that loads the library until exit. Limits: n <=
+ *   FGLT_NOALLOC_MAX_VERTICES, rowptr[n] <= FGLT_NOALLOC_MAX_ENTRIES, and a
+ *   largest out-degree in the degree order of about 1100 (the triangle pass's
+ *   shared-memory bitmap); larger inputs return FGLT_ERR_UNSUPPORTED.
+ *   The first call on each device looks up the array's address; make it before
+ *   any stream capture. All calls share the array and each leaves its data
+ *   there: calls whose device work overlaps race — serialise them.
+ */
+#define FGLT_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define FGLT_NOALLOC_MAX_VERTICES 32768
+#define FGLT_NOALLOC_MAX_ENTRIES 1048576
+fglt_status fglt_transform_noalloc(const void* rowptr, int rowptr_is_64bit, const int32_t* colidx,
+                                   int64_t n, int64_t* out_raw, int64_t* out_net, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Serving: requests arrive one by one from host memory; the library admits
  * them into resident device slots within fglt_options.serve_memory_budget,

@@ -65,7 +65,7 @@ class fglt_graph_host(ctypes.Structure):
 EXPORTED = [
     "fglt_options_default", "fglt_create", "fglt_destroy", "fglt_status_string", "fglt_last_cuda_error",
     "fglt_transform", "fglt_transform_host", "fglt_transform_batched", "fglt_stage_times", "fglt_work_counters",
-    "fglt_stream_submit", "fglt_stream_poll", "fglt_stream_cancel",
+    "fglt_stream_submit", "fglt_stream_poll", "fglt_stream_cancel", "fglt_transform_noalloc",
 ]
 
 _lib = None
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.fglt_transform_batched.argtypes = [h_t, vp, c_int, vp, ctypes.POINTER(i64), i64, vp, vp, vp]
     lib.fglt_stage_times.argtypes = [h_t, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                      c_int, ctypes.POINTER(c_int)]
+    lib.fglt_transform_noalloc.argtypes = [vp, c_int, vp, i64, vp, vp, vp]
     lib.fglt_work_counters.argtypes = [h_t, ctypes.POINTER(ctypes.c_int64), c_int, ctypes.POINTER(c_int)]
     lib.fglt_stream_submit.argtypes = [h_t, ctypes.POINTER(fglt_graph_host), ctypes.POINTER(ctypes.c_uint64)]
     lib.fglt_stream_poll.argtypes = [h_t, ctypes.c_uint64, c_int, ctypes.POINTER(ctypes.c_double)]
@@ -194,6 +195,13 @@ def fglt_transform_batched(h, rowptr, rowptr_is_64bit: int, colidx, graph_offset
                                          off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(num_graphs),
                                          _ptr(out_raw), _ptr(out_net), _stream_ptr(stream)),
            "fglt_transform_batched", h)
+
+
+def fglt_transform_noalloc(rowptr, rowptr_is_64bit: int, colidx, n: int, out_raw, out_net, stream=None) -> None:
+    """Transform without any device allocation (no handle). For callers that
+    cannot allocate at call time; limited to small graphs (see include/fglt.h)."""
+    _check(load().fglt_transform_noalloc(_ptr(rowptr), int(rowptr_is_64bit), _ptr(colidx), int(n), _ptr(out_raw),
+                                         _ptr(out_net), _stream_ptr(stream)), "fglt_transform_noalloc")
 
 
 def fglt_stage_times(h) -> dict:

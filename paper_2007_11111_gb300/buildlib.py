@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfglt.so")
 
-SOURCES = ["k_prep.cu", "k_tri.cu", "k_cyc.cu", "fglt_capi.cu", "fglt_serve.cu"]
+SOURCES = ["k_prep.cu", "k_tri.cu", "k_cyc.cu", "fglt_capi.cu", "fglt_serve.cu", "fglt_noalloc.cu"]
 HEADERS = ["fglt_device.cuh", "fglt_kernels.h", "fglt_serve.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
