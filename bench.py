@@ -49,8 +49,8 @@ WORKLOADS = {
 }
 # Bounded sample for the CPU oracle: the same generator and parameters at a
 # smaller scale.
-CPU_SAMPLE = dict(kind="rmat", scale=14, ef=16, seed=0,
-                  desc="R-MAT scale 14, edge factor 16, a=.57 b=.19 c=.19, seed 0 (same generator, 1/64 of the vertices)")
+CPU_SAMPLE = dict(kind="rmat", scale=15, ef=16, seed=0,
+                  desc="R-MAT scale 15, edge factor 16, a=.57 b=.19 c=.19, seed 0 (same generator, 1/32 of the vertices)")
 
 
 def make_graph(spec):
@@ -184,6 +184,117 @@ def cpu_baseline(threads=0):
             "sample": CPU_SAMPLE["desc"] + f"; full transform of m={g.m} edges in {dt:.2f} s"}
 
 
+# ---------------------------------------------------------------------------
+# Batched (20,000 small graphs in one block-diagonal launch) and served
+# (continuous batching of a Poisson request stream) forms, each against one
+# single-graph transform per graph on the same GPU.
+# ---------------------------------------------------------------------------
+def bench_batched(fg, torch, dev, num_graphs=20000, reps=5):
+    batch = gg.small_graph_batch(num_graphs, seed=0, n_lo=10, n_hi=500)
+    G = batch.graph
+    rp = torch.from_numpy(G.rowptr).to(dev)
+    ci = torch.from_numpy(G.colidx).to(dev)
+    raw = torch.empty((G.n, 16), dtype=torch.int64, device=dev)
+    net = torch.empty((G.n, 16), dtype=torch.int64, device=dev)
+    with fg.Handle(device=dev.index or 0) as h:
+        h.transform_batched(rp, ci, batch.offsets, raw, net)  # runs and captures the CUDA graph
+        h.transform_batched(rp, ci, batch.offsets, raw, net)  # first replay
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            h.transform_batched(rp, ci, batch.offsets, raw, net)
+            times.append(time.perf_counter() - t0)
+        t_batch = statistics.median(times)
+        # one transform per graph (device-resident per-graph CSRs)
+        per = []
+        for g in range(num_graphs):
+            lo, hi = int(batch.offsets[g]), int(batch.offsets[g + 1])
+            e0, e1 = int(G.rowptr[lo]), int(G.rowptr[hi])
+            per.append((hi - lo, torch.from_numpy(G.rowptr[lo:hi + 1] - e0).to(dev),
+                        torch.from_numpy((G.colidx[e0:e1].astype(np.int64) - lo).astype(np.int32)
+                                         if e1 > e0 else np.zeros(1, np.int32)).to(dev)))
+        outs = [(torch.empty((k, 16), dtype=torch.int64, device=dev),
+                 torch.empty((k, 16), dtype=torch.int64, device=dev)) for k, _, _ in per]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (k, prp, pci), (oraw, onet) in zip(per, outs):
+            h.transform(prp, pci, k, oraw, onet)
+        torch.cuda.synchronize()
+        t_per = time.perf_counter() - t0
+        ok = all(torch.equal(net[int(batch.offsets[g]):int(batch.offsets[g + 1])], outs[g][1])
+                 for g in range(0, num_graphs, 97))
+    return {"workload": f"{num_graphs} graphs, n ~ U{{10..500}}, alternating BA (m ~ U{{2..5}}) and "
+                        "random-geometric (mean degree 8), block-diagonal CSR, seed 0",
+            "vertices": G.n, "edges": G.m, "graphs_per_s": num_graphs / t_batch,
+            "ms_per_batch": 1000 * t_batch, "per_graph_launch_graphs_per_s": num_graphs / t_per,
+            "speedup_vs_per_graph": t_per / t_batch, "cuda_graph_replay": True,
+            "bit_exact_vs_per_graph_sample": bool(ok)}
+
+
+def bench_serving(fg, torch, dev, num_requests=400, pool_size=24, seed=0, load=0.8):
+    """Poisson arrivals of graphs with |E| log-uniform in [1e3, 2e6] drawn from a
+    pool of distinct R-MAT and Barabasi-Albert graphs, served through
+    fglt_stream_submit/poll, against a sequential one-at-a-time queue of
+    fglt_transform_host calls fed the same arrivals."""
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(pool_size):
+        E = int(np.exp(rng.uniform(np.log(1e3), np.log(2e6))))
+        if i % 2 == 0:
+            sc = max(4, int(np.ceil(np.log2(max(E / 8, 2)))))
+            pool.append(gg.rmat(sc, max(1, E // (1 << sc)), seed=seed + i))
+        else:
+            pool.append(gg.barabasi_albert(max(16, E // 8), 8, seed + i))
+    picks = rng.integers(0, pool_size, num_requests)
+    with fg.Handle(device=dev.index or 0) as h:
+        # service time of each pool graph alone (sequential baseline)
+        svc = []
+        for g in pool:
+            h.transform_host(g.rowptr, g.colidx, g.n)
+            t0 = time.perf_counter()
+            h.transform_host(g.rowptr, g.colidx, g.n)
+            svc.append(time.perf_counter() - t0)
+        mean_svc = float(np.mean([svc[k] for k in picks]))
+        rate = load / mean_svc
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, num_requests))
+        # sequential FIFO queue with the measured service times
+        t, seq_lat = 0.0, []
+        for a, k in zip(arrivals, picks):
+            t = max(t, a) + svc[k]
+            seq_lat.append(t - a)
+        seq_total = t - arrivals[0]
+        outs = [(np.empty((pool[k].n, 16), np.int64), np.empty((pool[k].n, 16), np.int64)) for k in picks]
+        rps = [np.ascontiguousarray(g.rowptr, dtype=np.int64) for g in pool]
+        ids = [None] * num_requests
+        start = time.perf_counter()
+        for i, (a, k) in enumerate(zip(arrivals, picks)):
+            wait = start + a - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            g = pool[k]
+            ids[i] = fg.fglt_stream_submit(h.h, g.n, rps[k], g.colidx, outs[i][0], outs[i][1])
+        lat = []
+        for rid in ids:
+            st, us = fg.fglt_stream_poll(h.h, rid, -1)
+            if st != fg.FGLT_OK:
+                raise RuntimeError(f"request failed with status {st}")
+            lat.append(us / 1e6)
+        total = time.perf_counter() - start - arrivals[0]
+        ok = all(np.array_equal(outs[i][1], h.transform_host(pool[picks[i]].rowptr, pool[picks[i]].colidx,
+                                                              pool[picks[i]].n)[1])
+                 for i in range(0, num_requests, 37))
+    edges = sum(pool[k].m for k in picks)
+    return {"workload": f"{num_requests} Poisson requests at {load:.1f}x the sequential capacity, |E| "
+                        f"log-uniform in [1e3, 2e6] from a pool of {pool_size} R-MAT/BA graphs, seed {seed}",
+            "graphs_per_s": num_requests / total, "edges_per_s": edges / total,
+            "p50_ms": 1000 * float(np.percentile(lat, 50)), "p99_ms": 1000 * float(np.percentile(lat, 99)),
+            "sequential_graphs_per_s": num_requests / seq_total,
+            "sequential_p50_ms": 1000 * float(np.percentile(seq_lat, 50)),
+            "sequential_p99_ms": 1000 * float(np.percentile(seq_lat, 99)),
+            "bit_exact_vs_alone_sample": bool(ok)}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -261,7 +372,7 @@ def run_gpu(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     work = h.work_counters()
-    launches = KERNELS_PER_STEP * args.steps
+    launches = int(work.get("launches", 0)) * args.steps
 
     # End to end through the public API with host buffers (pinned host memory).
     e2e = None
@@ -310,18 +421,15 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if not args.no_batched:
+        line["batched"] = bench_batched(fg, torch, dev)
+    if not args.no_serving:
+        line["serving"] = bench_serving(fg, torch, dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
     h.close()
     return 0
-
-
-# Kernel launches of one transform (degree-ordered pipeline):
-# degree, spmv1 (2), hist, scan (3), rank, orient count (2), scan (3),
-# orient fill (2), sort (2), worklist, tri1, edge terms, unrank, spmv2 (2),
-# tri2, wedge count (2), cyc worklists, cyc (2), epilogue.
-KERNELS_PER_STEP = 34
 
 
 def main():
@@ -333,6 +441,8 @@ def main():
     ap.add_argument("--workload", default="rmat-s20-ef16", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

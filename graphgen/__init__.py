@@ -147,37 +147,64 @@ def rmat(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19,
     return csr_from_pairs(n, src, dst)
 
 
-def barabasi_albert(n: int, m: int, seed: int) -> Graph:
-    """Preferential attachment: vertices m..n-1 each attach to m distinct earlier
-    vertices drawn with probability proportional to degree (the first new vertex
-    attaches to all of 0..m-1)."""
+def _ba_pairs(n: int, m: int, seed: int):
+    """Edge pairs of barabasi_albert (n > m).
+
+    Preferential attachment (Barabasi-Albert): vertices m..n-1 arrive in
+    order and each draws m targets with probability proportional to degree,
+    i.e. uniformly from the list of all edge endpoints so far (the m initial
+    vertices listed once each). Repeated draws of the same target merge into
+    one edge. Vectorised: a draw that lands on the target end of an earlier
+    edge takes that edge's target, resolved by pointer doubling."""
     rng = np.random.default_rng(seed)
+    E = m * (n - m)
+    e = np.arange(E, dtype=np.int64)
+    src = m + e // m                          # the arriving vertex of draw e
+    L = m + 2 * m * (src - m)                  # endpoint-list length before src arrives
+    p = (rng.random(E) * L).astype(np.int64)
+    q = p - m
+    tgt = np.where(p < m, p, -1).astype(np.int64)
+    is_src = (p >= m) & (q % 2 == 0)
+    tgt[is_src] = m + (q[is_src] // 2) // m    # the arriving end of an earlier edge
+    ref = np.where(tgt < 0, q // 2, e)         # the target end: copy that edge's target
+    while True:
+        todo = tgt < 0
+        if not todo.any():
+            break
+        r = ref[todo]
+        tgt[todo] = tgt[r]
+        ref[todo] = ref[r]
+    return src, tgt
+
+
+def barabasi_albert(n: int, m: int, seed: int) -> Graph:
+    """Barabasi-Albert graph with n vertices and m attachments per arriving vertex."""
     if n <= m:
         return complete(n)
-    src, dst = [], []
-    repeated: list[int] = []
-    targets = list(range(m))
-    for v in range(m, n):
-        for t in targets:
-            src.append(v)
-            dst.append(t)
-        repeated.extend(targets)
-        repeated.extend([v] * m)
-        chosen: set[int] = set()
-        while len(chosen) < m:
-            chosen.add(repeated[int(rng.integers(len(repeated)))])
-        targets = sorted(chosen)
-    return csr_from_pairs(n, src, dst)
+    src, tgt = _ba_pairs(n, m, seed)
+    return csr_from_pairs(n, src, tgt)
+
+
+def _rgg_pairs(n: int, radius: float, seed: int):
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, 2))
+    try:
+        from scipy.spatial import cKDTree
+        pairs = cKDTree(pts).query_pairs(radius, output_type="ndarray")
+        if pairs.size:
+            return pairs[:, 0].astype(np.int64), pairs[:, 1].astype(np.int64)
+        return np.zeros(0, np.int64), np.zeros(0, np.int64)
+    except ImportError:
+        i, j = np.triu_indices(n, k=1)
+        dd = ((pts[i] - pts[j]) ** 2).sum(axis=1)
+        keep = dd < radius * radius
+        return i[keep], j[keep]
 
 
 def random_geometric(n: int, radius: float, seed: int) -> Graph:
     """n points uniform in the unit square; an edge joins points closer than radius."""
-    rng = np.random.default_rng(seed)
-    pts = rng.random((n, 2))
-    i, j = np.triu_indices(n, k=1)
-    dd = ((pts[i] - pts[j]) ** 2).sum(axis=1)
-    keep = dd < radius * radius
-    return csr_from_pairs(n, i[keep], j[keep])
+    i, j = _rgg_pairs(n, radius, seed)
+    return csr_from_pairs(n, i, j)
 
 
 def rgg_radius(n: int, mean_degree: float = 8.0) -> float:
@@ -211,17 +238,30 @@ def pack_block_diagonal(graphs: Sequence[Graph]) -> Batch:
 
 def small_graph_batch(num_graphs: int, seed: int, n_lo: int = 10, n_hi: int = 500) -> Batch:
     """Graph g has n ~ U{n_lo..n_hi} and seed seed+g; even g are Barabasi-Albert with
-    m ~ U{2..5}, odd g random-geometric with mean degree 8."""
-    graphs = []
+    m ~ U{2..5}, odd g random-geometric with mean degree 8. Packed block-diagonally."""
+    ns = np.zeros(num_graphs, np.int64)
+    srcs, dsts = [], []
+    off = 0
     for g in range(num_graphs):
         rng = np.random.default_rng(seed + g)
         n = int(rng.integers(n_lo, n_hi + 1))
         if g % 2 == 0:
             m = int(rng.integers(2, 6))
-            graphs.append(barabasi_albert(n, m, seed + g))
+            if n <= m:
+                i, j = np.triu_indices(n, k=1)
+            else:
+                i, j = _ba_pairs(n, m, seed + g)
         else:
-            graphs.append(random_geometric(n, rgg_radius(n), seed + g))
-    return pack_block_diagonal(graphs)
+            i, j = _rgg_pairs(n, rgg_radius(n), seed + g)
+        srcs.append(np.asarray(i, np.int64) + off)
+        dsts.append(np.asarray(j, np.int64) + off)
+        ns[g] = n
+        off += n
+    offsets = np.zeros(num_graphs + 1, dtype=np.int64)
+    np.cumsum(ns, out=offsets[1:])
+    src = np.concatenate(srcs) if srcs else np.zeros(0, np.int64)
+    dst = np.concatenate(dsts) if dsts else np.zeros(0, np.int64)
+    return Batch(csr_from_pairs(int(offsets[-1]), src, dst), offsets)
 
 
 def permute_vertices(g: Graph, perm: np.ndarray) -> Graph:

@@ -164,6 +164,7 @@ fglt_status fglt_stage_times(fglt_t handle, const char** names, float* ms,
  *   7 4-cliques (each once)
  *   8 wedges enumerated by the 4-cycle stage
  *   9 largest wedge count of one vertex
+ *  10 kernel launches the transform issued (memsets not included)
  * FGLT_ERR_NOT_FOUND if no transform has completed on the handle. */
 fglt_status fglt_work_counters(fglt_t handle, int64_t* counters, int max_counters, int* count);
 

@@ -216,7 +216,7 @@ def fglt_stage_times(h) -> dict:
 
 
 WORK_COUNTER_NAMES = ["n", "nnz", "m", "max_degree", "max_out_degree", "tri_scanned", "triangles",
-                      "k4", "wedges", "max_wedges"]
+                      "k4", "wedges", "max_wedges", "launches"]
 
 
 def fglt_work_counters(h) -> dict:
@@ -243,11 +243,11 @@ def fglt_stream_submit(h, n: int, rowptr: np.ndarray, colidx: np.ndarray, out_ra
 
 
 def fglt_stream_poll(h, request_id: int, timeout_ms: int):
-    """Returns (status, latency_us); FGLT_ERR_PENDING / FGLT_ERR_TIMEOUT are returned, not raised."""
+    """Returns (status, latency_us). The status is the request's own result
+    (FGLT_OK, or the error its transform returned) or FGLT_ERR_PENDING /
+    FGLT_ERR_TIMEOUT / FGLT_ERR_NOT_FOUND; it is returned, not raised."""
     lat = ctypes.c_double()
     st = load().fglt_stream_poll(h, ctypes.c_uint64(request_id), int(timeout_ms), ctypes.byref(lat))
-    if st not in (FGLT_OK, FGLT_ERR_PENDING, FGLT_ERR_TIMEOUT):
-        _check(st, "fglt_stream_poll", h)
     return st, lat.value
 
 

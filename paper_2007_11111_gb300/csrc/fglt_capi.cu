@@ -43,7 +43,7 @@ enum CounterId {
 enum Counter64Id { W_PROBES, W_TRIANGLES, W_K4, W_WMAX, W_WSUM, W_GCAP, W_NUM };
 
 // Host copy of the last transform's work counters (fglt_work_counters order).
-enum WorkOut { O_N, O_NNZ, O_M, O_DMAX, O_DPMAX, O_PROBES, O_TRIANGLES, O_K4, O_WEDGES, O_WMAX, O_NUM };
+enum WorkOut { O_N, O_NNZ, O_M, O_DMAX, O_DPMAX, O_PROBES, O_TRIANGLES, O_K4, O_WEDGES, O_WMAX, O_LAUNCHES, O_NUM };
 
 const char* const STAGE_NAMES[] = {"degree", "spmv1", "rank", "orient", "sort", "tri1", "c3_edges",
                                    "spmv2", "tri2", "wedges", "cyc", "epilogue"};
@@ -65,7 +65,22 @@ struct fglt_handle {
   int64_t work[O_NUM] = {};
   bool work_valid = false;
   serve::Server* server = nullptr;
+  std::mutex server_mu;  // guards creation of the server
   std::mutex mu;  // serialises transforms issued by the serving thread and the caller
+  // Batched calls: the stage sequence captured as a CUDA graph for one batch
+  // shape and buffer set, replayed while they stay the same.
+  struct {
+    bool valid = false;
+    const void* rowptr = nullptr;
+    const void* colidx = nullptr;
+    int64_t* raw = nullptr;
+    int64_t* net = nullptr;
+    int rp64 = 0;
+    int64_t n = 0, nnz = 0, maxg = 0;
+    cudaGraphExec_t exec = nullptr;
+  } batch;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int64_t batch_replays = 0;
 };
 
 namespace {
@@ -136,19 +151,42 @@ int bits_for(int64_t cap) {
   return hb;
 }
 
+}  // namespace
+
+// Host-side bounds that replace the pipeline's read-backs (block-diagonal
+// batches: every degree, out-degree and per-vertex count of distinct 4-cycle
+// tops is below the largest graph's vertex count). With them the stage
+// sequence has no host synchronisation and can be captured as a CUDA graph.
+struct Bounds {
+  int64_t nnz;            // exact stored entries (read before capture)
+  int32_t dmax;           // bound on every degree
+  int64_t cap;            // bound on distinct tops per vertex
+  const int64_t* off;     // device graph offsets for validation (or NULL)
+  int64_t num_graphs;
+};
+
+namespace {
+
 // The whole transform on stream st. Inputs and outputs are device pointers.
-fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out_net, cudaStream_t st) {
+// With b, every read-back is replaced by b's bounds; with capturing, nothing
+// that synchronises or allocates is issued (buffers were sized by an earlier
+// run with the same bounds).
+fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out_net, cudaStream_t st,
+                         const Bounds* b = nullptr, bool capturing = false) {
   Csr g = in;
   const int64_t n = g.n;
-  const bool prof = h->opt.profile_stages != 0;
+  const bool prof = h->opt.profile_stages != 0 && !capturing;
   h->stages_valid = false;
   h->cur = st;
+  const int64_t launches0 = g_launches;
   auto mark = [&](int i) {
     if (prof) cudaEventRecord(h->ev[i], st);
   };
 
   // Number of stored entries.
-  {
+  if (b) {
+    g.nnz = b->nnz;
+  } else {
     const size_t elt = g.rp64 ? 8 : 4;
     CK(cudaMemcpyAsync(h->pinned, static_cast<const char*>(g.rowptr) + (size_t)n * elt, elt,
                        cudaMemcpyDeviceToHost, st));
@@ -171,9 +209,11 @@ fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out
   int* err = cnt + C_ERR;
 
   mark(0);
-  CK(launch_degree(g, d, cnt + C_DMAX, heavy, cnt + C_NHEAVY, err, st));
+  CK(launch_degree(g, d, cnt + C_DMAX, heavy, cnt + C_NHEAVY, err, st, b ? b->dmax : 0x7fffffff));
   int32_t dmax = 0;
-  {
+  if (b) {
+    dmax = b->dmax;
+  } else {
     int32_t c[C_NUM];
     CK(cudaMemcpyAsync(h->pinned, cnt, sizeof c, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -182,8 +222,9 @@ fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out
     dmax = c[C_DMAX];
   }
   if (dmax > MAX_DEGREE_EXACT) return FGLT_ERR_OVERFLOW;
-  if (h->opt.validate) {
+  if (h->opt.validate && !capturing) {
     CK(launch_validate(g, heavy, cnt + C_NHEAVY, heavy_cap, err, st));
+    if (b && b->off) CK(launch_validate_batch(g, b->off, b->num_graphs, err, st));
     int e = 0;
     fglt_status s = read_scalar(h, st, err, &e);
     if (s != FGLT_OK) return s;
@@ -227,13 +268,13 @@ fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out
   CK(launch_orient_count(g, rank, heavy, cnt + C_NHEAVY, heavy_cap, opc, cnt + C_DPMAX, st));
   CK(launch_scan_i32_to_i64(opc, n, orp, scan_tmp, st));
   int64_t m_or = 0;
-  {
-    fglt_status s = read_scalar(h, st, orp + n, &m_or);
-    if (s != FGLT_OK) return s;
-  }
   int32_t dpmax = 0;
-  {
-    fglt_status s = read_scalar(h, st, cnt + C_DPMAX, &dpmax);
+  if (b) {
+    m_or = g.nnz;  // upper bound; the kernels read the exact row pointers
+    dpmax = dmax;
+  } else {
+    fglt_status s = read_scalar(h, st, orp + n, &m_or);
+    if (s == FGLT_OK) s = read_scalar(h, st, cnt + C_DPMAX, &dpmax);
     if (s != FGLT_OK) return s;
   }
   NEED(B_OCOL, m_or, ocol);
@@ -321,10 +362,16 @@ fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out
                         ctr + W_WSUM, st));
   int32_t* lists;
   NEED(B_LS, 4 * n, lists);
-  CK(launch_cyc_worklists(wc, wcn, n, lists, n, cnt + C_NCYC0, ctr + W_GCAP, hub_lo < n, st));
+  const int64_t cap_bound = b ? std::min<int64_t>(b->cap, n) : n;
+  CK(launch_cyc_worklists(wc, wcn, n, lists, n, cnt + C_NCYC0, ctr + W_GCAP, hub_lo < n, st, cap_bound));
   int32_t n_gmem = 0;
   u64 gcap = 0;
-  {
+  if (b) {
+    if (cap_bound > cyc_block_cap()) {  // the global class may be needed: size it for the bound
+      n_gmem = 1;
+      gcap = (u64)cap_bound;
+    }
+  } else {
     fglt_status s = read_scalar(h, st, cnt + C_NCYC3, &n_gmem);
     if (s == FGLT_OK) s = read_scalar(h, st, ctr + W_GCAP, &gcap);
     if (s != FGLT_OK) return s;
@@ -348,6 +395,7 @@ fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out
     ca.hub_lo = hub_lo;
     ca.r12r = r12r;
     ca.err = err;
+    ca.cap_bound = cap_bound;
     if (n_gmem > 0) {
       ca.gbits = bits_for((int64_t)gcap);
       const size_t slots = (size_t)cyc_gmem_blocks() << ca.gbits;
@@ -362,6 +410,7 @@ fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out
   EpilogueIn ein{d, rank, p2, p3, r7, r9, c3r, r10r, r12r, r13r, r14r, k4r};
   CK(launch_epilogue(ein, n, out_raw, out_net, st));
   mark(12);
+  if (capturing) return FGLT_OK;
 
   int e = 0;
   {
@@ -383,6 +432,7 @@ fglt_status run_pipeline(fglt_t h, const Csr& in, int64_t* out_raw, int64_t* out
     h->work[O_K4] = (int64_t)w[W_K4];
     h->work[O_WEDGES] = (int64_t)w[W_WSUM];
     h->work[O_WMAX] = (int64_t)w[W_WMAX];
+    h->work[O_LAUNCHES] = g_launches - launches0;
     h->work_valid = true;
   }
   if (prof) {
@@ -447,6 +497,8 @@ fglt_status fglt_create(fglt_t* out, const fglt_options* opt, int device) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMallocHost(&h->pinned, 256);
   for (int i = 0; e == cudaSuccess && i <= NUM_STAGES; ++i) e = cudaEventCreate(&h->ev[i]);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     fglt_status s = cuda_fail(h, e);
     fglt_destroy(h);
@@ -464,6 +516,9 @@ fglt_status fglt_destroy(fglt_t h) {
     h->server = nullptr;
   }
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->batch.exec) cudaGraphExecDestroy(h->batch.exec);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
   for (auto& b : h->bufs)
     if (b.p) cudaFree(b.p);
   for (int i = 0; i <= NUM_STAGES; ++i)
@@ -520,12 +575,93 @@ fglt_status fglt_transform_batched(fglt_t h, const void* rowptr, int rowptr_is_6
                                    int64_t* out_net, void* stream) {
   if (!h || !graph_offsets || num_graphs < 0) return FGLT_ERR_INVALID_ARG;
   if (graph_offsets[0] != 0) return FGLT_ERR_INVALID_ARG;
-  for (int64_t i = 0; i < num_graphs; ++i)
+  int64_t maxg = 0;
+  for (int64_t i = 0; i < num_graphs; ++i) {
     if (graph_offsets[i + 1] < graph_offsets[i]) return FGLT_ERR_INVALID_ARG;
+    maxg = std::max(maxg, graph_offsets[i + 1] - graph_offsets[i]);
+  }
   const int64_t n = graph_offsets[num_graphs];
-  // The union of vertex-disjoint graphs is one graph; its transform is the
-  // concatenation of the per-graph transforms.
-  return fglt_transform(h, rowptr, rowptr_is_64bit, colidx, n, out_raw, out_net, stream);
+  fglt_status s = check_common(h, rowptr, rowptr_is_64bit, n, out_raw, out_net);
+  if (s != FGLT_OK || n == 0) return s;
+  if (maxg - 1 > MAX_DEGREE_EXACT) return FGLT_ERR_OVERFLOW;
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (cudaSetDevice(h->device) != cudaSuccess) return FGLT_ERR_CUDA;
+  // The union of vertex-disjoint graphs is one graph whose transform is the
+  // concatenation of theirs (every graphlet is connected). It runs on the
+  // handle's stream, ordered after and before the caller's stream.
+  cudaStream_t us = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+  cudaStream_t cs = h->stream;
+  if (us != cs) {
+    CK(cudaEventRecord(h->ev_in, us));
+    CK(cudaStreamWaitEvent(cs, h->ev_in, 0));
+  }
+  auto finish = [&](fglt_status st) -> fglt_status {
+    if (us != cs) {
+      if (cudaEventRecord(h->ev_out, cs) != cudaSuccess) return FGLT_ERR_CUDA;
+      if (cudaStreamWaitEvent(us, h->ev_out, 0) != cudaSuccess) return FGLT_ERR_CUDA;
+    }
+    return st;
+  };
+  const size_t elt = rowptr_is_64bit ? 8 : 4;
+  CK(cudaMemcpyAsync(h->pinned, static_cast<const char*>(rowptr) + (size_t)n * elt, elt, cudaMemcpyDeviceToHost,
+                     cs));
+  CK(cudaStreamSynchronize(cs));
+  const int64_t nnz = rowptr_is_64bit ? h->pinned[0] : (int64_t) * reinterpret_cast<int32_t*>(h->pinned);
+  if (nnz < 0) return finish(FGLT_ERR_INVALID_GRAPH);
+  if (nnz > 0 && !colidx) return finish(FGLT_ERR_INVALID_ARG);
+  const int64_t* off_dev = nullptr;
+  if (h->opt.validate) {
+    void* p = nullptr;
+    if ((s = need(h, B_BATCH_OFF, (size_t)(num_graphs + 1) * 8, &p)) != FGLT_OK) return finish(s);
+    CK(cudaMemcpyAsync(p, graph_offsets, (size_t)(num_graphs + 1) * 8, cudaMemcpyHostToDevice, cs));
+    off_dev = static_cast<const int64_t*>(p);
+  }
+  Bounds b{nnz, (int32_t)std::max<int64_t>(maxg - 1, 0), std::max<int64_t>(maxg - 1, 1), off_dev, num_graphs};
+  Csr g{rowptr, rowptr_is_64bit != 0, colidx, n, nnz};
+  auto& bc = h->batch;
+  const bool same = bc.valid && bc.rowptr == rowptr && bc.colidx == colidx && bc.raw == out_raw &&
+                    bc.net == out_net && bc.rp64 == rowptr_is_64bit && bc.n == n && bc.nnz == nnz &&
+                    bc.maxg == maxg;
+  if (same && !h->opt.validate && !h->opt.profile_stages) {
+    // Replay: the graph re-zeroes its counters and accumulators itself.
+    CK(cudaGraphLaunch(bc.exec, cs));
+    ++h->batch_replays;
+    int e = 0;
+    s = read_scalar(h, cs, h->bufs[B_CNT].p ? static_cast<int*>(h->bufs[B_CNT].p) + C_ERR : nullptr, &e);
+    if (s != FGLT_OK) return finish(s);
+    h->work_valid = false;
+    h->stages_valid = false;
+    if (e & (ERR_BAD_GRAPH | ERR_BAD_ROWPTR)) return finish(FGLT_ERR_INVALID_GRAPH);
+    return finish(e ? FGLT_ERR_INTERNAL : FGLT_OK);
+  }
+  s = run_pipeline(h, g, out_raw, out_net, cs, &b, false);
+  if (s != FGLT_OK || h->opt.validate || h->opt.profile_stages) return finish(s);
+  // Capture the same sequence (its buffers are sized now) for later calls.
+  if (bc.exec) {
+    cudaGraphExecDestroy(bc.exec);
+    bc.exec = nullptr;
+  }
+  bc.valid = false;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    const fglt_status cap = run_pipeline(h, g, out_raw, out_net, cs, &b, true);
+    const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+    if (cap == FGLT_OK && ee == cudaSuccess && graph &&
+        cudaGraphInstantiate(&bc.exec, graph, 0) == cudaSuccess) {
+      bc.valid = true;
+      bc.rowptr = rowptr;
+      bc.colidx = colidx;
+      bc.raw = out_raw;
+      bc.net = out_net;
+      bc.rp64 = rowptr_is_64bit;
+      bc.n = n;
+      bc.nnz = nnz;
+      bc.maxg = maxg;
+    }
+    if (graph) cudaGraphDestroy(graph);
+  }
+  cudaGetLastError();  // a failed capture only disables replay
+  return finish(FGLT_OK);
 }
 
 fglt_status fglt_work_counters(fglt_t h, int64_t* counters, int max_counters, int* count) {
@@ -563,6 +699,25 @@ fglt_status transform_locked(fglt_t h, const Csr& g, int64_t* raw, int64_t* net,
   std::lock_guard<std::mutex> lock(h->mu);
   if (cudaSetDevice(h->device) != cudaSuccess) return FGLT_ERR_CUDA;
   return run_pipeline(h, g, raw, net, st);
+}
+cudaStream_t handle_stream(fglt_t h) { return h->stream; }
+const fglt_options* options_of(fglt_t h) { return &h->opt; }
+int device_of(fglt_t h) { return h->device; }
+Server* server_of(fglt_t h) {
+  std::lock_guard<std::mutex> lock(h->server_mu);
+  return h->server;
+}
+fglt_status ensure_server(fglt_t h, Server** out, fglt_status (*factory)(fglt_t, Server**)) {
+  std::lock_guard<std::mutex> lock(h->server_mu);
+  if (!h->server) {
+    fglt_status s = factory(h, &h->server);
+    if (s != FGLT_OK) {
+      h->server = nullptr;
+      return s;
+    }
+  }
+  *out = h->server;
+  return FGLT_OK;
 }
 }  // namespace serve
 }  // namespace fglt

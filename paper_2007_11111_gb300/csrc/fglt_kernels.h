@@ -9,6 +9,11 @@ namespace fglt {
 
 typedef unsigned long long u64;
 
+// Kernel launches issued by the calling host thread (the pipeline reports the
+// count per transform).
+extern thread_local int64_t g_launches;
+inline void note_launch(int k = 1) { g_launches += k; }
+
 // Input CSR as given by the caller (device pointers).
 struct Csr {
   const void* rowptr;
@@ -24,8 +29,11 @@ constexpr int HEAVY_DEGREE = 512;
 
 // --- input CSR passes ------------------------------------------------------
 // Degrees, max degree, heavy-row list; flags malformed row pointers in *err.
+// Degrees above dcap (a caller-supplied bound) are flagged and clamped.
 cudaError_t launch_degree(const Csr& g, int32_t* d, int32_t* dmax, int32_t* heavy, int32_t* nheavy, int* err,
-                          cudaStream_t st);
+                          cudaStream_t st, int32_t dcap = 0x7fffffff);
+// Batched inputs: flags an edge that joins two graphs (graph offsets on the device).
+cudaError_t launch_validate_batch(const Csr& g, const int64_t* off, int64_t num_graphs, int* err, cudaStream_t st);
 cudaError_t launch_validate(const Csr& g, const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap,
                             int* err, cudaStream_t st);
 // p2 = A p1 - p1 and d^7 = A((p1-1)o(p1-2))/2 (SpMV chain 1)
@@ -95,14 +103,19 @@ cudaError_t launch_wedge_count(const Csr& g, const int32_t* rank, const int64_t*
 // Dense counter span of the heavy-vertex kernel (16-bit counters when every
 // degree is below 65536, else 32-bit).
 int cyc_dense_span(bool c16);
+// Largest per-vertex table need served by shared-memory tables; vertices above
+// it may need the global-memory class.
+int cyc_block_cap();
 int cyc_gmem_blocks();
 // Splits the vertices with at least two wedges into four classes (lists at
 // lists + c * list_stride, counts[c]): warp table, block hash table, dense hub
 // counters (only if dense_ok), global hash table; *gcap_max = largest table
 // need of the last class.
+// cap_bound caps the distinct tops of one vertex (e.g. the largest graph of a
+// block-diagonal batch minus one); pass n when unknown.
 cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, int64_t n, int32_t* lists,
                                  int64_t list_stride, int32_t* counts, u64* gcap_max, bool dense_ok,
-                                 cudaStream_t st);
+                                 cudaStream_t st, int64_t cap_bound);
 struct CycArgs {
   const int32_t* rank;
   const int32_t* perm;
@@ -120,6 +133,7 @@ struct CycArgs {
   uint32_t* gcnt;
   u64* r12r;
   int* err;
+  int64_t cap_bound;      // bound on distinct tops of one vertex (n when unknown)
 };
 cudaError_t launch_cyc(const Csr& g, const CycArgs& a, cudaStream_t st);
 

@@ -203,7 +203,7 @@ fglt_status run(const Csr& g0, int64_t* out_raw, int64_t* out_net, cudaStream_t 
   CK(launch_wedge_count(g, rank, orp, ocol, heavy, cnt + K_NHEAVY, heavy_cap, hub_lo, wc, wcn, ctr + W_WMAX,
                         ctr + W_WSUM, st));
   TAKE(int32_t, lists, 4 * n);
-  CK(launch_cyc_worklists(wc, wcn, n, lists, n, cnt + K_NCYC0, ctr + W_GCAP, true, st));
+  CK(launch_cyc_worklists(wc, wcn, n, lists, n, cnt + K_NCYC0, ctr + W_GCAP, true, st, n));
   int32_t n_gmem = 0;
   RB(cnt + K_NCYC3, &n_gmem);
   if (n_gmem != 0) return FGLT_ERR_INTERNAL;
@@ -223,6 +223,7 @@ fglt_status run(const Csr& g0, int64_t* out_raw, int64_t* out_net, cudaStream_t 
   ca.hub_lo = hub_lo;
   ca.r12r = r12r;
   ca.err = err;
+  ca.cap_bound = n;
   CK(launch_cyc(g, ca, st));
 
   EpilogueIn ein{d, rank, p2, p3, r7, r9, c3r, r10r, r12r, r13r, r14r, k4r};

@@ -12,6 +12,14 @@ struct Server;
 // One transform on the handle's workspace, serialised with the caller's calls.
 fglt_status transform_locked(fglt_t h, const Csr& g, int64_t* raw, int64_t* net, cudaStream_t st);
 
+// Accessors of the opaque handle used by the serving runtime.
+cudaStream_t handle_stream(fglt_t h);
+const fglt_options* options_of(fglt_t h);
+int device_of(fglt_t h);
+Server* server_of(fglt_t h);
+// Returns the handle's server, creating it with factory on first use.
+fglt_status ensure_server(fglt_t h, Server** out, fglt_status (*factory)(fglt_t, Server**));
+
 void destroy(Server* s);
 
 }  // namespace serve

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const RP* __restrict__ rp, 
                                                      const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
                                                      const int64_t* __restrict__ wc, const int32_t* __restrict__ list,
                                                      const int32_t* __restrict__ cnt, int* next, u64* r12r, int64_t n,
-                                                     int* err) {
+                                                     int64_t cap_bound, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u64* acc = reinterpret_cast<u64*>(smem) + warp * 32;
@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const RP* __restrict__ rp, 
     const int32_t w = list[item];
     int64_t cap = wc[w];
     if (cap > n - 1 - w) cap = n - 1 - w;
+    if (cap > cap_bound) cap = cap_bound;
     int hb = 5;
     while ((1LL << hb) < 2 * cap) ++hb;
     const uint32_t H = 1u << hb;
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const RP* __restrict__ rp, con
                                                        const int32_t* __restrict__ list,
                                                        const int32_t* __restrict__ cnt, int* next, u64* r12r,
                                                        int64_t n, int32_t hub_lo, int gbits, uint32_t* gkeys,
-                                                       uint32_t* gcnt, int* err) {
+                                                       uint32_t* gcnt, int64_t cap_bound, int* err) {
   constexpr bool DENSE = MODE == 1 || MODE == 2;
   constexpr bool C16 = MODE == 1;
   constexpr bool GMEM = MODE == 3;
@@ -478,6 +479,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const RP* __restrict__ rp, con
     if (!DENSE) {
       int64_t cap = wc[w];
       if (cap > n - 1 - w) cap = n - 1 - w;
+      if (cap > cap_bound) cap = cap_bound;
       hb = 5;
       while ((1LL << hb) < 2 * cap) ++hb;
     }
@@ -566,7 +568,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const RP* __restrict__ rp, con
 // hub counters + shared hash, 3 = block + global hash.
 __global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* __restrict__ wcn, int64_t n,
                                 int32_t* lists, int64_t list_stride, int32_t* counts, u64* gcap_max,
-                                int dense_ok) {
+                                int dense_ok, int64_t cap_bound) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < n; r0 += stride) {
@@ -576,6 +578,7 @@ __global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* _
     if (r < n && wc[r] >= 2) {
       cap = wc[r];
       if (cap > n - 1 - r) cap = n - 1 - r;
+      if (cap > cap_bound) cap = cap_bound;
       if (wc[r] <= WARP_CAP) cls = 0;
       else if (cap <= BLOCK_CAP) cls = 1;
       else if (dense_ok && wcn[r] <= (1 << (DHASH_BITS - 1))) cls = 2;
@@ -621,7 +624,9 @@ void launch_block(const RP* rp, const Csr& g, const CycArgs& a, int cls, cudaStr
                              : num_sms() * occupancy((const void*)k_cyc_block<RP, MODE, BT>, BT, smem);
   k_cyc_block<RP, MODE, BT><<<grid, BT, smem, st>>>(rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc,
                                                     a.lists + cls * a.list_stride, a.counts + cls, a.next + cls,
-                                                    a.r12r, g.n, a.hub_lo, a.gbits, a.gkeys, a.gcnt, a.err);
+                                                    a.r12r, g.n, a.hub_lo, a.gbits, a.gkeys, a.gcnt, a.cap_bound,
+                                                    a.err);
+  note_launch();
 }
 
 template <typename RP>
@@ -631,7 +636,9 @@ cudaError_t launch_rp(const Csr& g, const CycArgs& a, cudaStream_t st) {
   const size_t wsmem = (size_t)(WARP_T / 32) * (32 * 8 + 2 * WARP_HASH * 4);
   cudaFuncSetAttribute(k_cyc_warp<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
   k_cyc_warp<RP><<<sms * occupancy((const void*)k_cyc_warp<RP>, WARP_T, wsmem), WARP_T, wsmem, st>>>(
-      rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc, a.lists, a.counts, a.next + 0, a.r12r, g.n, a.err);
+      rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc, a.lists, a.counts, a.next + 0, a.r12r, g.n, a.cap_bound,
+      a.err);
+  note_launch();
   launch_block<RP, 0, BT_HASH>(rp, g, a, 1, st);
   if (a.c16) launch_block<RP, 1, BT_HEAVY>(rp, g, a, 2, st);
   else launch_block<RP, 2, BT_HEAVY>(rp, g, a, 2, st);
@@ -642,16 +649,18 @@ cudaError_t launch_rp(const Csr& g, const CycArgs& a, cudaStream_t st) {
 }  // namespace
 
 int cyc_dense_span(bool c16) { return c16 ? 2 * DENSE_WORDS : DENSE_WORDS; }
+int cyc_block_cap() { return BLOCK_CAP; }
 int cyc_gmem_blocks() { return gmem_blocks(); }
 
 cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, int64_t n, int32_t* lists,
                                  int64_t list_stride, int32_t* counts, u64* gcap_max, bool dense_ok,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, int64_t cap_bound) {
   if (n <= 0) return cudaSuccess;
   int64_t blocks = (n + 255) / 256;
   if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
   k_cyc_worklists<<<(unsigned)blocks, 256, 0, st>>>(wc, wcn, n, lists, list_stride, counts, gcap_max,
-                                                     dense_ok ? 1 : 0);
+                                                     dense_ok ? 1 : 0, cap_bound);
+  note_launch();
   return cudaGetLastError();
 }
 

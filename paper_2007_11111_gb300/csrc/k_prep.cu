@@ -11,6 +11,8 @@
 
 namespace fglt {
 
+thread_local int64_t g_launches = 0;
+
 namespace {
 
 constexpr int G = 8;          // lanes per light row
@@ -88,10 +90,12 @@ cudaError_t run_rows(const Csr& g, const int32_t* heavy, const int32_t* nheavy, 
   const RP* rp = static_cast<const RP*>(g.rowptr);
   if (g.n <= 0) return cudaSuccess;
   k_rows_light<RP, Op><<<(unsigned)light_blocks(g.n), ROW_BLOCK, 0, st>>>(rp, g.colidx, g.n, op);
+  note_launch();
   if (heavy_cap > 0) {
     int64_t hb = heavy_cap < (int64_t)num_sms() * 4 ? heavy_cap : (int64_t)num_sms() * 4;
     if (hb < 1) hb = 1;
     k_rows_heavy<RP, Op><<<(unsigned)hb, ROW_BLOCK, 0, st>>>(rp, g.colidx, heavy, nheavy, op);
+    note_launch();
   }
   return cudaGetLastError();
 }
@@ -239,12 +243,32 @@ struct ValidateOp {  // simple, symmetric, strictly increasing rows
   __device__ __forceinline__ void done(int64_t, long long, long long) const {}
 };
 
+// Batched inputs: every neighbour of v lies in v's own graph [off[g], off[g+1]).
+template <typename RP>
+__global__ void k_validate_batch(const RP* __restrict__ rp, const int32_t* __restrict__ ci, int64_t n,
+                                 const int64_t* __restrict__ off, int64_t num_graphs, int* err) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = num_graphs - 1;  // last g with off[g] <= v
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    const int64_t a = off[lo], b = off[lo + 1];
+    bool bad = false;
+    for (int64_t k = ld_rp(rp, v); k < ld_rp(rp, v + 1); ++k) {
+      const int64_t j = __ldg(ci + k);
+      bad |= (j < a) || (j >= b);
+    }
+    if (bad) atomicOr(err, ERR_BAD_GRAPH);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Degrees
 // ---------------------------------------------------------------------------
 template <typename RP>
 __global__ void k_degree(const RP* __restrict__ rp, int64_t n, int64_t nnz, int32_t* d, int32_t* dmax,
-                         int32_t* heavy, int32_t* nheavy, int64_t heavy_cap, int* err) {
+                         int32_t* heavy, int32_t* nheavy, int64_t heavy_cap, int32_t dcap, int* err) {
   int local_max = 0;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t lo = ld_rp(rp, v), hi = ld_rp(rp, v + 1);
@@ -252,6 +276,10 @@ __global__ void k_degree(const RP* __restrict__ rp, int64_t n, int64_t nnz, int3
     if (lo < 0 || hi > nnz || dv < 0 || dv > 0x7fffffff || (v == 0 && lo != 0)) {
       atomicOr(err, ERR_BAD_ROWPTR);
       dv = 0;
+    }
+    if (dv > dcap) {  // above the caller's bound (batched inputs): flag it and clamp
+      atomicOr(err, ERR_BAD_GRAPH);
+      dv = dcap;
     }
     const int32_t dd = (int32_t)dv;
     d[v] = dd;
@@ -638,15 +666,16 @@ unsigned grid_for(int64_t items, int threads, int per_sm = 8) {
 // ===========================================================================
 
 cudaError_t launch_degree(const Csr& g, int32_t* d, int32_t* dmax, int32_t* heavy, int32_t* nheavy, int* err,
-                          cudaStream_t st) {
+                          cudaStream_t st, int32_t dcap) {
   if (g.n <= 0) return cudaSuccess;
   const int64_t cap = g.nnz / HEAVY_DEGREE + 1;
   if (g.rp64)
     k_degree<int64_t><<<grid_for(g.n, 256), 256, 0, st>>>(static_cast<const int64_t*>(g.rowptr), g.n, g.nnz, d,
-                                                          dmax, heavy, nheavy, cap, err);
+                                                          dmax, heavy, nheavy, cap, dcap, err);
   else
     k_degree<int32_t><<<grid_for(g.n, 256), 256, 0, st>>>(static_cast<const int32_t*>(g.rowptr), g.n, g.nnz, d,
-                                                          dmax, heavy, nheavy, cap, err);
+                                                          dmax, heavy, nheavy, cap, dcap, err);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -658,6 +687,18 @@ cudaError_t launch_validate(const Csr& g, const int32_t* heavy, const int32_t* n
   }
   ValidateOp<int32_t> op{static_cast<const int32_t*>(g.rowptr), g.colidx, g.n, err};
   return run_rows<int32_t>(g, heavy, nheavy, heavy_cap, op, st);
+}
+
+cudaError_t launch_validate_batch(const Csr& g, const int64_t* off, int64_t num_graphs, int* err, cudaStream_t st) {
+  if (g.n <= 0 || num_graphs <= 0) return cudaSuccess;
+  if (g.rp64)
+    k_validate_batch<int64_t><<<grid_for(g.n, 256), 256, 0, st>>>(static_cast<const int64_t*>(g.rowptr), g.colidx,
+                                                                  g.n, off, num_graphs, err);
+  else
+    k_validate_batch<int32_t><<<grid_for(g.n, 256), 256, 0, st>>>(static_cast<const int32_t*>(g.rowptr), g.colidx,
+                                                                  g.n, off, num_graphs, err);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_spmv1(const Csr& g, const int32_t* d, const int32_t* heavy, const int32_t* nheavy,
@@ -674,6 +715,7 @@ cudaError_t launch_spmv2(const Csr& g, const int32_t* d, const int64_t* p2, cons
 cudaError_t launch_degree_hist(const int32_t* d, int64_t n, int32_t* hist, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_degree_hist<<<grid_for(n, 256, 4), 256, 0, st>>>(d, n, hist);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -681,6 +723,7 @@ cudaError_t launch_rank_assign(const int32_t* d, int64_t n, const int64_t* base,
                                int32_t* rank, int32_t* perm, int32_t* dr, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_rank_assign<<<grid_for(n, RANK_T * RANK_I, 4), RANK_T, 0, st>>>(d, n, base, cursor, rank, perm, dr);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -700,14 +743,19 @@ cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int32
                              cudaStream_t st) {
   if (n <= 0 || dpmax < 2) return cudaSuccess;
   k_sort_rows_warp<<<grid_for(n * 32, 256), 256, 0, st>>>(orp, n, ocol);
+  note_launch();
   if (dpmax > 32) {
     int P = 64;
     while (P < dpmax && P < SORT_SMEM_MAX) P <<= 1;
     const size_t smem = (size_t)P * sizeof(int32_t);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_sort_rows_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_sort_rows_block<<<grid_for(n, 1, 4), 256, smem, st>>>(orp, n, ocol);
+    note_launch();
   }
-  if (dpmax > SORT_SMEM_MAX) k_sort_rows_global<<<1, 1024, 0, st>>>(orp, n, ocol, gscratch);
+  if (dpmax > SORT_SMEM_MAX) {
+    k_sort_rows_global<<<1, 1024, 0, st>>>(orp, n, ocol, gscratch);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 
@@ -715,6 +763,7 @@ cudaError_t launch_worklist_outdeg(const int32_t* opc, int64_t n, int min_out, i
                                    cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_worklist_outdeg<<<grid_for(n, 256), 256, 0, st>>>(opc, n, min_out, list, count);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -722,6 +771,7 @@ cudaError_t launch_worklist_outdeg3(const int32_t* opc, int64_t n, int min_out, 
                                     int64_t stride, int32_t* counts, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_worklist_outdeg3<<<grid_for(n, 256), 256, 0, st>>>(opc, n, min_out, t0, t1, lists, stride, counts);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -735,8 +785,11 @@ cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t n, int64_t* out, v
   const int64_t nb = (n + SCAN_B - 1) / SCAN_B;
   int64_t* bsum = static_cast<int64_t*>(temp);
   k_scan_reduce<<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, bsum);
+  note_launch();
   k_scan_bsums<<<1, 1024, 0, st>>>(bsum, nb);
+  note_launch();
   k_scan_down<<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, bsum, out);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -744,12 +797,14 @@ cudaError_t launch_c3_edge_terms(const int64_t* orp, const int32_t* ocol, const 
                                  int64_t n, u64* r10r, u64* r14r, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_c3_edge_terms<<<grid_for(n * 32, 256), 256, 0, st>>>(orp, ocol, C3o, dr, n, r10r, r14r);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_unrank_u64(const u64* src_r, const int32_t* perm, int64_t n, int64_t* dst_o, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_unrank_u64<<<grid_for(n, 256), 256, 0, st>>>(src_r, perm, n, dst_o);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -765,6 +820,7 @@ cudaError_t launch_epilogue(const EpilogueIn& in, int64_t n, int64_t* raw, int64
   const bool vec = ((uintptr_t)raw % 16 == 0) && ((uintptr_t)net % 16 == 0);
   if (vec) k_epilogue<true><<<grid_for(n, 256), 256, 0, st>>>(in, n, raw, net);
   else k_epilogue<false><<<grid_for(n, 256), 256, 0, st>>>(in, n, raw, net);
+  note_launch();
   return cudaGetLastError();
 }
 

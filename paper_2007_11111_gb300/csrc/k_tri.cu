@@ -382,6 +382,7 @@ cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* 
                                             err);
   else
     k_tri1<false><<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, C3o, c3r, k4r, gbm, work_ctr, err);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -393,6 +394,7 @@ cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* 
   cudaFuncSetAttribute(k_tri2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int grid = occupancy_grid((const void*)k_tri2, smem);
   k_tri2<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hash_bits_for(dpmax), C3o, r13r, err);
+  note_launch();
   return cudaGetLastError();
 }
 
