@@ -232,11 +232,11 @@ def bench_batched(fg, torch, dev, num_graphs=20000, reps=5):
             "bit_exact_vs_per_graph_sample": bool(ok)}
 
 
-def bench_serving(fg, torch, dev, num_requests=400, pool_size=24, seed=0, load=0.8):
+def bench_serving(fg, torch, dev, num_requests=400, pool_size=24, seed=0, loads=(1.0, 2.0)):
     """Poisson arrivals of graphs with |E| log-uniform in [1e3, 2e6] drawn from a
     pool of distinct R-MAT and Barabasi-Albert graphs, served through
-    fglt_stream_submit/poll, against a sequential one-at-a-time queue of
-    fglt_transform_host calls fed the same arrivals."""
+    fglt_stream_submit/poll, against a sequential one-at-a-time FIFO of
+    fglt_transform_host calls fed the same arrivals (both measured live)."""
     rng = np.random.default_rng(seed)
     pool = []
     for i in range(pool_size):
@@ -247,8 +247,11 @@ def bench_serving(fg, torch, dev, num_requests=400, pool_size=24, seed=0, load=0
         else:
             pool.append(gg.barabasi_albert(max(16, E // 8), 8, seed + i))
     picks = rng.integers(0, pool_size, num_requests)
+    rps = [np.ascontiguousarray(g.rowptr, dtype=np.int64) for g in pool]
+    out = {"workload": f"{num_requests} Poisson requests per load point, |E| log-uniform in [1e3, 2e6], "
+                       f"from a pool of {pool_size} distinct R-MAT/BA graphs, seed {seed}; "
+                       "load = arrival rate / sequential capacity", "points": []}
     with fg.Handle(device=dev.index or 0) as h:
-        # service time of each pool graph alone (sequential baseline)
         svc = []
         for g in pool:
             h.transform_host(g.rowptr, g.colidx, g.n)
@@ -256,43 +259,47 @@ def bench_serving(fg, torch, dev, num_requests=400, pool_size=24, seed=0, load=0
             h.transform_host(g.rowptr, g.colidx, g.n)
             svc.append(time.perf_counter() - t0)
         mean_svc = float(np.mean([svc[k] for k in picks]))
-        rate = load / mean_svc
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, num_requests))
-        # sequential FIFO queue with the measured service times
-        t, seq_lat = 0.0, []
-        for a, k in zip(arrivals, picks):
-            t = max(t, a) + svc[k]
-            seq_lat.append(t - a)
-        seq_total = t - arrivals[0]
-        outs = [(np.empty((pool[k].n, 16), np.int64), np.empty((pool[k].n, 16), np.int64)) for k in picks]
-        rps = [np.ascontiguousarray(g.rowptr, dtype=np.int64) for g in pool]
-        ids = [None] * num_requests
-        start = time.perf_counter()
-        for i, (a, k) in enumerate(zip(arrivals, picks)):
-            wait = start + a - time.perf_counter()
-            if wait > 0:
-                time.sleep(wait)
-            g = pool[k]
-            ids[i] = fg.fglt_stream_submit(h.h, g.n, rps[k], g.colidx, outs[i][0], outs[i][1])
-        lat = []
-        for rid in ids:
-            st, us = fg.fglt_stream_poll(h.h, rid, -1)
-            if st != fg.FGLT_OK:
-                raise RuntimeError(f"request failed with status {st}")
-            lat.append(us / 1e6)
-        total = time.perf_counter() - start - arrivals[0]
-        ok = all(np.array_equal(outs[i][1], h.transform_host(pool[picks[i]].rowptr, pool[picks[i]].colidx,
-                                                              pool[picks[i]].n)[1])
-                 for i in range(0, num_requests, 37))
-    edges = sum(pool[k].m for k in picks)
-    return {"workload": f"{num_requests} Poisson requests at {load:.1f}x the sequential capacity, |E| "
-                        f"log-uniform in [1e3, 2e6] from a pool of {pool_size} R-MAT/BA graphs, seed {seed}",
-            "graphs_per_s": num_requests / total, "edges_per_s": edges / total,
-            "p50_ms": 1000 * float(np.percentile(lat, 50)), "p99_ms": 1000 * float(np.percentile(lat, 99)),
-            "sequential_graphs_per_s": num_requests / seq_total,
-            "sequential_p50_ms": 1000 * float(np.percentile(seq_lat, 50)),
-            "sequential_p99_ms": 1000 * float(np.percentile(seq_lat, 99)),
-            "bit_exact_vs_alone_sample": bool(ok)}
+        for load in loads:
+            arrivals = np.cumsum(rng.exponential(mean_svc / load, num_requests))
+            outs = [(np.empty((pool[k].n, 16), np.int64), np.empty((pool[k].n, 16), np.int64)) for k in picks]
+            ids = [None] * num_requests
+            start = time.perf_counter()
+            for i, (a, k) in enumerate(zip(arrivals, picks)):
+                wait = start + a - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+                g = pool[k]
+                ids[i] = fg.fglt_stream_submit(h.h, g.n, rps[k], g.colidx, outs[i][0], outs[i][1])
+            lat = []
+            for rid in ids:
+                st, us = fg.fglt_stream_poll(h.h, rid, -1)
+                if st != fg.FGLT_OK:
+                    raise RuntimeError(f"request failed with status {st}")
+                lat.append(us / 1e6)
+            served_total = max(a + l for a, l in zip(arrivals, lat)) - arrivals[0]
+            ok = all(np.array_equal(outs[i][1], h.transform_host(pool[picks[i]].rowptr, pool[picks[i]].colidx,
+                                                                  pool[picks[i]].n)[1])
+                     for i in range(0, num_requests, 37))
+            # sequential FIFO, live: one fglt_transform_host at a time, in arrival order
+            seq_lat = []
+            start = time.perf_counter()
+            for a, k in zip(arrivals, picks):
+                wait = start + a - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+                g = pool[k]
+                h.transform_host(g.rowptr, g.colidx, g.n)
+                seq_lat.append(time.perf_counter() - start - a)
+            seq_total = max(a + l for a, l in zip(arrivals, seq_lat)) - arrivals[0]
+            edges = sum(pool[k].m for k in picks)
+            out["points"].append({
+                "load": load, "graphs_per_s": num_requests / served_total, "edges_per_s": edges / served_total,
+                "p50_ms": 1000 * float(np.percentile(lat, 50)), "p99_ms": 1000 * float(np.percentile(lat, 99)),
+                "sequential_graphs_per_s": num_requests / seq_total,
+                "sequential_p50_ms": 1000 * float(np.percentile(seq_lat, 50)),
+                "sequential_p99_ms": 1000 * float(np.percentile(seq_lat, 99)),
+                "bit_exact_vs_alone_sample": bool(ok)})
+    return out
 
 
 def run_reference(args, rank, world):

@@ -153,18 +153,6 @@ int bits_for(int64_t cap) {
 
 }  // namespace
 
-// Host-side bounds that replace the pipeline's read-backs (block-diagonal
-// batches: every degree, out-degree and per-vertex count of distinct 4-cycle
-// tops is below the largest graph's vertex count). With them the stage
-// sequence has no host synchronisation and can be captured as a CUDA graph.
-struct Bounds {
-  int64_t nnz;            // exact stored entries (read before capture)
-  int32_t dmax;           // bound on every degree
-  int64_t cap;            // bound on distinct tops per vertex
-  const int64_t* off;     // device graph offsets for validation (or NULL)
-  int64_t num_graphs;
-};
-
 namespace {
 
 // The whole transform on stream st. Inputs and outputs are device pointers.
@@ -695,10 +683,11 @@ fglt_status fglt_stage_times(fglt_t h, const char** names, float* ms, int max_st
 // Used by the serving runtime: one transform on the handle's workspace.
 namespace fglt {
 namespace serve {
-fglt_status transform_locked(fglt_t h, const Csr& g, int64_t* raw, int64_t* net, cudaStream_t st) {
+fglt_status transform_locked(fglt_t h, const Csr& g, int64_t* raw, int64_t* net, cudaStream_t st,
+                             const Bounds* b) {
   std::lock_guard<std::mutex> lock(h->mu);
   if (cudaSetDevice(h->device) != cudaSuccess) return FGLT_ERR_CUDA;
-  return run_pipeline(h, g, raw, net, st);
+  return run_pipeline(h, g, raw, net, st, b, false);
 }
 cudaStream_t handle_stream(fglt_t h) { return h->stream; }
 const fglt_options* options_of(fglt_t h) { return &h->opt; }

@@ -67,4 +67,18 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
   return s;  // valid in warp 0
 }
 
+// Lets fn use the device's full opt-in shared memory per block. Every caller
+// sets the same value, so concurrent host threads launching the kernel with
+// different dynamic sizes cannot shrink the limit under one another.
+template <typename F>
+inline void allow_max_smem(F* fn) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return;
+  const int dyn = optin - (int)fa.sharedSizeBytes;  // the limit covers static + dynamic
+  if (dyn > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+}
+
 }  // namespace fglt

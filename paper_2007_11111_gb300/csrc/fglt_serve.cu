@@ -130,6 +130,9 @@ struct Server {
 
 namespace {
 
+constexpr int64_t BOUNDED_MAX_GRAPH = 4096;      // packs whose graphs are all this small skip read-backs
+constexpr int64_t PACK_MAX_ENTRIES = 1LL << 22;  // a pack stops growing past this many CSR entries
+
 // Runs one pack on a lane. Returns the status of the whole pack.
 fglt_status run_pack(Server* S, Lane* L, const std::vector<Request*>& pack) {
   int64_t n = 0, nnz = 0;
@@ -159,7 +162,17 @@ fglt_status run_pack(Server* S, Lane* L, const std::vector<Request*>& pack) {
       cudaMemcpyAsync(L->d_colidx.p, L->h_colidx.p, (size_t)nnz * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return FGLT_ERR_CUDA;
   Csr g{L->d_rowptr.p, true, L->d_colidx.p, n, nnz};
-  fglt_status s = transform_locked(L->h, g, L->d_raw.p, L->d_net.p, st);
+  // Packs of small graphs run the stage sequence without host read-backs:
+  // the largest request bounds every degree and every per-vertex table.
+  int64_t maxg = 0;
+  for (Request* r : pack) maxg = std::max(maxg, r->n);
+  fglt_status s;
+  if (maxg <= BOUNDED_MAX_GRAPH) {
+    Bounds b{nnz, (int32_t)std::max<int64_t>(maxg - 1, 0), std::max<int64_t>(maxg - 1, 1), nullptr, 0};
+    s = transform_locked(L->h, g, L->d_raw.p, L->d_net.p, st, &b);
+  } else {
+    s = transform_locked(L->h, g, L->d_raw.p, L->d_net.p, st);
+  }
   if (s != FGLT_OK) return s;
   if (cudaMemcpyAsync(L->h_raw.p, L->d_raw.p, (size_t)n * 128, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaMemcpyAsync(L->h_net.p, L->d_net.p, (size_t)n * 128, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -185,9 +198,13 @@ void lane_loop(Server* S, Lane* L) {
         if (S->stop && S->queue.empty()) return;
         if (!S->queue.empty()) {
           // Admit from the front while the pack fits this lane's share of the budget.
+          int64_t pack_nnz = 0;
           while (!S->queue.empty() && (int)pack.size() < S->max_batch) {
             Request* r = S->queue.front();
             if (pack_est + r->est > S->lane_cap || S->reserved + r->est > S->budget) break;
+            // a large request runs alone rather than holding small ones back
+            if (!pack.empty() && pack_nnz + r->nnz > PACK_MAX_ENTRIES) break;
+            pack_nnz += r->nnz;
             S->queue.pop_front();
             r->state = RUNNING;
             pack.push_back(r);
@@ -224,7 +241,7 @@ void lane_loop(Server* S, Lane* L) {
   }
 }
 
-constexpr int NUM_LANES = 2;
+constexpr int NUM_LANES = 3;
 
 fglt_status start(fglt_t owner, Server** out) {
   const fglt_options* o = options_of(owner);

@@ -619,7 +619,7 @@ int gmem_blocks() { return num_sms(); }
 template <typename RP, int MODE, int BT>
 void launch_block(const RP* rp, const Csr& g, const CycArgs& a, int cls, cudaStream_t st) {
   const size_t smem = block_smem(MODE, BT);
-  cudaFuncSetAttribute(k_cyc_block<RP, MODE, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_max_smem(k_cyc_block<RP, MODE, BT>);
   const int grid = MODE == 3 ? gmem_blocks()
                              : num_sms() * occupancy((const void*)k_cyc_block<RP, MODE, BT>, BT, smem);
   k_cyc_block<RP, MODE, BT><<<grid, BT, smem, st>>>(rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc,
@@ -634,7 +634,7 @@ cudaError_t launch_rp(const Csr& g, const CycArgs& a, cudaStream_t st) {
   const RP* rp = static_cast<const RP*>(g.rowptr);
   const int sms = num_sms();
   const size_t wsmem = (size_t)(WARP_T / 32) * (32 * 8 + 2 * WARP_HASH * 4);
-  cudaFuncSetAttribute(k_cyc_warp<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
+  allow_max_smem(k_cyc_warp<RP>);
   k_cyc_warp<RP><<<sms * occupancy((const void*)k_cyc_warp<RP>, WARP_T, wsmem), WARP_T, wsmem, st>>>(
       rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc, a.lists, a.counts, a.next + 0, a.r12r, g.n, a.cap_bound,
       a.err);

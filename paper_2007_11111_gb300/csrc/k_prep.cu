@@ -748,7 +748,7 @@ cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int32
     int P = 64;
     while (P < dpmax && P < SORT_SMEM_MAX) P <<= 1;
     const size_t smem = (size_t)P * sizeof(int32_t);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_sort_rows_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k_sort_rows_block);
     k_sort_rows_block<<<grid_for(n, 1, 4), 256, smem, st>>>(orp, n, ocol);
     note_launch();
   }

@@ -356,10 +356,10 @@ int tri_grid_blocks() { return num_sms(); }
 static int tri1_grid(int dpmax, bool smem_bm) {
   const size_t smem = tri1_smem_impl(dpmax, smem_bm);
   if (smem_bm) {
-    cudaFuncSetAttribute(k_tri1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k_tri1<true>);
     return occupancy_grid((const void*)k_tri1<true>, smem);
   }
-  cudaFuncSetAttribute(k_tri1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_max_smem(k_tri1<false>);
   return occupancy_grid((const void*)k_tri1<false>, smem);
 }
 
@@ -391,7 +391,7 @@ cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* 
   if (dpmax < 2) return cudaSuccess;
   const size_t smem = tri2_smem_bytes(dpmax);
   if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
-  cudaFuncSetAttribute(k_tri2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_max_smem(k_tri2);
   const int grid = occupancy_grid((const void*)k_tri2, smem);
   k_tri2<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hash_bits_for(dpmax), C3o, r13r, err);
   note_launch();
