@@ -302,6 +302,22 @@ def bench_serving(fg, torch, dev, num_requests=400, pool_size=24, seed=0, loads=
     return out
 
 
+def slowest_rank_ms(ms: float, world: int, device=None) -> float:
+    """Max over ranks of a per-rank time (the job is as fast as its slowest rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(m_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: every rank transforms its own replica of m edges."""
+    return world * m_per_rank / (ms / 1000.0)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -373,11 +389,7 @@ def run_gpu(args, rank, world, local_rank):
     clocks = sampler.stop()
     if dist is not None:
         dist.barrier()
-    ms = statistics.mean(step_ms)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank_ms(statistics.mean(step_ms), world, dev)
     work = h.work_counters()
     launches = int(work.get("launches", 0)) * args.steps
 
@@ -413,7 +425,7 @@ def run_gpu(args, rank, world, local_rank):
                 "kernel": dom, "kernel_ms": stage_ms[dom], "algorithmic_bytes": ab,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s"}
-    value = world * g.m / (ms / 1000)
+    value = job_value(g.m, world, ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
