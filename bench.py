@@ -46,6 +46,12 @@ WORKLOADS = {
                                "symmetric simple CSR (profiling size)"),
     "er-2000-d10": dict(kind="er", n=2000, deg=10, seed=0,
                         desc="Erdos-Renyi G(n=2000, avg degree 10), seed 0, symmetric simple CSR"),
+    "rmat-s24-ef32": dict(kind="rmat_dev", scale=24, ef=32, seed=0,
+                          desc="R-MAT scale 24, edge factor 32, a=.57 b=.19 c=.19, seed 0, permuted, "
+                               "symmetric simple CSR generated on the device, int32 colidx, int64 rowptr"),
+    "rmat-s22-ef16": dict(kind="rmat_dev", scale=22, ef=16, seed=0,
+                          desc="R-MAT scale 22, edge factor 16, a=.57 b=.19 c=.19, seed 0, permuted, "
+                               "symmetric simple CSR generated on the device"),
 }
 # Bounded sample for the CPU oracle: the same generator and parameters at a
 # smaller scale.
@@ -53,7 +59,9 @@ CPU_SAMPLE = dict(kind="rmat", scale=15, ef=16, seed=0,
                   desc="R-MAT scale 15, edge factor 16, a=.57 b=.19 c=.19, seed 0 (same generator, 1/32 of the vertices)")
 
 
-def make_graph(spec):
+def make_graph(spec, device=None):
+    if spec["kind"] == "rmat_dev":
+        return gg.rmat_device(spec["scale"], spec["ef"], seed=spec["seed"], device=device or "cuda")
     if spec["kind"] == "rmat":
         return gg.rmat(spec["scale"], spec["ef"], seed=spec["seed"])
     return gg.erdos_renyi(spec["n"], spec["deg"], seed=spec["seed"])
@@ -349,9 +357,12 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     spec = WORKLOADS[args.workload]
-    g = make_graph(spec)
-    rp = torch.from_numpy(g.rowptr).to(dev)
-    ci = torch.from_numpy(g.colidx).to(dev)
+    g = make_graph(spec, dev)
+    if isinstance(g, gg.DeviceGraph):
+        rp, ci = g.rowptr, g.colidx
+    else:
+        rp = torch.from_numpy(g.rowptr).to(dev)
+        ci = torch.from_numpy(g.colidx).to(dev)
     raw = torch.empty((g.n, 16), dtype=torch.int64, device=dev)
     net = torch.empty((g.n, 16), dtype=torch.int64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
@@ -396,8 +407,8 @@ def run_gpu(args, rank, world, local_rank):
     # End to end through the public API with host buffers (pinned host memory).
     e2e = None
     if rank == 0 and not args.no_e2e:
-        prp = torch.from_numpy(g.rowptr).pin_memory().numpy()
-        pci = torch.from_numpy(g.colidx).pin_memory().numpy()
+        prp = rp.cpu().pin_memory().numpy()
+        pci = ci.cpu().pin_memory().numpy()
         hraw = torch.empty((g.n, 16), dtype=torch.int64).pin_memory().numpy()
         hnet = torch.empty((g.n, 16), dtype=torch.int64).pin_memory().numpy()
         fg.fglt_transform_host(h.h, prp, 1, pci, g.n, hraw, hnet)

@@ -269,3 +269,73 @@ def permute_vertices(g: Graph, perm: np.ndarray) -> Graph:
     rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.rowptr))
     perm = np.asarray(perm, dtype=np.int64)
     return csr_from_pairs(g.n, perm[rows], perm[g.colidx.astype(np.int64)])
+
+
+# ---------------------------------------------------------------------------
+# Large R-MAT graphs generated on a CUDA device (scale 22-26): the host
+# generator above needs tens of minutes and tens of GB for scale 24.
+# ---------------------------------------------------------------------------
+
+class DeviceGraph(NamedTuple):
+    n: int
+    rowptr: "object"  # torch int64[n+1] on the device
+    colidx: "object"  # torch int32[nnz] on the device
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.numel())
+
+    @property
+    def m(self) -> int:
+        return self.nnz // 2
+
+    def to_host(self) -> Graph:
+        return Graph(self.n, self.rowptr.cpu().numpy(), self.colidx.cpu().numpy())
+
+
+def rmat_device(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+                seed: int = 0, device: str = "cuda", chunk: int = 1 << 26) -> DeviceGraph:
+    """R-MAT graph of the same family as rmat() (quadrant per level with
+    probabilities a, b, c, d = 1-a-b-c; seeded vertex permutation; self-loops
+    dropped; symmetrised; deduplicated; sorted CSR), drawn with torch's
+    counter-based device generator. The draws differ from rmat()'s for the same
+    seed, so the two give different graphs of the same distribution. Rows are
+    int64 row pointers and int32 column indices on the device."""
+    import torch
+
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    n = 1 << scale
+    total = n * edge_factor
+    ab, abc = a + b, a + b + c
+    perm = torch.randperm(n, generator=gen, device=dev)
+    keys = []
+    done = 0
+    while done < total:
+        cnt = min(chunk, total - done)
+        s = torch.zeros(cnt, dtype=torch.int64, device=dev)
+        d = torch.zeros(cnt, dtype=torch.int64, device=dev)
+        for lvl in range(scale):
+            r = torch.rand(cnt, generator=gen, device=dev, dtype=torch.float64)
+            bit = 1 << (scale - 1 - lvl)
+            s += (r >= ab).to(torch.int64) * bit
+            d += (((r >= a) & (r < ab)) | (r >= abc)).to(torch.int64) * bit
+            del r
+        s = perm[s]
+        d = perm[d]
+        keep = s != d
+        s, d = s[keep], d[keep]
+        keys.append(torch.unique(torch.cat([(s << scale) | d, (d << scale) | s])))
+        del s, d, keep
+        done += cnt
+    k = torch.unique(torch.cat(keys)) if len(keys) > 1 else keys[0]
+    del keys
+    rows = k >> scale
+    colidx = (k & (n - 1)).to(torch.int32)
+    del k
+    counts = torch.bincount(rows, minlength=n)
+    del rows
+    rowptr = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(counts, 0, out=rowptr[1:])
+    return DeviceGraph(n, rowptr, colidx)

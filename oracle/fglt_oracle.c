@@ -82,17 +82,6 @@ typedef struct {
 
 static inline i64 deg(const graph* g, i64 i) { return g->rp[i + 1] - g->rp[i]; }
 
-/* |N(i) ∩ N(j)| by sorted merge. */
-static i64 merge_count(const i32* a, i64 na, const i32* b, i64 nb) {
-    i64 x = 0, y = 0, c = 0;
-    while (x < na && y < nb) {
-        if (a[x] < b[y]) x++;
-        else if (a[x] > b[y]) y++;
-        else { c++; x++; y++; }
-    }
-    return c;
-}
-
 /* Position of key in the sorted list a[0..na), or -1. */
 static i64 find_pos(const i32* a, i64 na, i32 key) {
     i64 lo = 0, hi = na;
@@ -101,6 +90,25 @@ static i64 find_pos(const i32* a, i64 na, i32 key) {
         if (a[mid] < key) lo = mid + 1; else hi = mid;
     }
     return (lo < na && a[lo] == key) ? lo : -1;
+}
+
+/* |N(i) ∩ N(j)| of two sorted lists: a sorted merge, or, when one list is
+ * much longer, a binary search of each element of the shorter one. */
+static i64 merge_count(const i32* a, i64 na, const i32* b, i64 nb) {
+    if (na > 8 * nb || nb > 8 * na) {
+        const i32* s = na < nb ? a : b;
+        const i32* l = na < nb ? b : a;
+        i64 ns = na < nb ? na : nb, nl = na < nb ? nb : na, c = 0;
+        for (i64 x = 0; x < ns; x++) c += find_pos(l, nl, s[x]) >= 0;
+        return c;
+    }
+    i64 x = 0, y = 0, c = 0;
+    while (x < na && y < nb) {
+        if (a[x] < b[y]) x++;
+        else if (a[x] > b[y]) y++;
+        else { c++; x++; y++; }
+    }
+    return c;
 }
 
 /* A(k, l) for a vertex pair. */
@@ -112,10 +120,11 @@ static int adjacent(const graph* g, i64 k, i32 l) {
  * Step 2: C3(i,j) = (A o A^2)(i,j) = a_i^T a_j for every directed edge, stored
  * aligned with the column indices.
  * ------------------------------------------------------------------------- */
-static void step_C3(const graph* g, i64* C3, int nthreads) {
+static void step_C3(const graph* g, i64* C3, const unsigned char* rows_needed, int nthreads) {
     (void)nthreads;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
     for (i64 i = 0; i < g->n; i++) {
+        if (rows_needed && !rows_needed[i]) continue;
         const i32* Ni = g->ci + g->rp[i];
         i64 di = deg(g, i);
         for (i64 e = g->rp[i]; e < g->rp[i + 1]; e++) {
@@ -234,9 +243,12 @@ void oracle_raw_to_net(i64 n, const i64* raw, i64* net) {
 
 /* ---------------------------------------------------------------------------
  * Driver. verts == NULL: all vertices, rows written in vertex order.
- * Otherwise rows for verts[0..nv) in that order (the per-vertex vectors p2, c3
- * and the per-edge C3 are still computed for the whole graph, since the rows of
- * Table I read them at the neighbours).
+ * Otherwise rows for verts[0..nv) in that order. The rows of Table I at a
+ * vertex i read C3 on the edges of i and of its neighbours (c3 at the
+ * neighbours, the C3(j,k) of D4,c), so C3 and c3 are then computed only on the
+ * rows of the closed neighbourhoods of the requested vertices, and p3 only at
+ * the requested vertices; every value the requested rows read is the same as
+ * in the full computation.
  * Returns 0 on success, -1 on allocation failure.
  * ------------------------------------------------------------------------- */
 int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i64 nv,
@@ -255,10 +267,19 @@ int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i
     i64* p2 = (i64*)malloc(sizeof(i64) * (n ? n : 1));
     i64* c3 = (i64*)malloc(sizeof(i64) * (n ? n : 1));
     i64* p3 = (i64*)malloc(sizeof(i64) * (n ? n : 1));
-    i64* C3 = (i64*)malloc(sizeof(i64) * (nnz ? nnz : 1));
-    if (!p1 || !p2 || !c3 || !p3 || !C3) {
-        free(p1); free(p2); free(c3); free(p3); free(C3);
+    i64* C3 = (i64*)calloc((size_t)(nnz ? nnz : 1), sizeof(i64));
+    unsigned char* need = verts ? (unsigned char*)calloc((size_t)(n ? n : 1), 1) : NULL;
+    if (!p1 || !p2 || !c3 || !p3 || !C3 || (verts && !need)) {
+        free(p1); free(p2); free(c3); free(p3); free(C3); free(need);
         return -1;
+    }
+    if (verts) {
+        for (i64 r = 0; r < nv; r++) {
+            i64 i = verts[r];
+            need[i] = 2; /* requested row */
+            for (i64 e = rowptr[i]; e < rowptr[i + 1]; e++)
+                if (!need[colidx[e]]) need[colidx[e]] = 1;
+        }
     }
 
     /* Step 1: p1 = A e (= d1), p2 = A p1 - c2, c2 = d1. */
@@ -271,8 +292,9 @@ int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i
     }
 
     /* Step 2: C3 and c3 = C3 e / 2. */
-    step_C3(g, C3, nthreads);
+    step_C3(g, C3, need, nthreads);
     for (i64 i = 0; i < n; i++) {
+        if (need && !need[i]) { c3[i] = 0; continue; }
         i64 s = 0;
         for (i64 e = rowptr[i]; e < rowptr[i + 1]; e++) s += C3[e];
         c3[i] = s / 2;
@@ -281,6 +303,7 @@ int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i
     /* Step 3: p3 = A p2 - p1 o (p1 - 1) - 2 c3. */
 #pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
     for (i64 i = 0; i < n; i++) {
+        if (need && need[i] != 2) { p3[i] = 0; continue; }
         i64 s = 0;
         for (i64 e = rowptr[i]; e < rowptr[i + 1]; e++) s += p2[colidx[e]];
         p3[i] = rsub(rsub(s, p1[i] * rsub(p1[i], 1)), 2 * c3[i]);
@@ -333,7 +356,7 @@ int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i
         free(acc);
         free(touched);
     }
-    free(p1); free(p2); free(c3); free(p3); free(C3);
+    free(p1); free(p2); free(c3); free(p3); free(C3); free(need);
     return failed ? -1 : 0;
 }
 

@@ -1,0 +1,67 @@
+"""R-MAT scale 24, edge factor 32 (n = 16.8 M, ~5.1e8 undirected edges, max degree
+~6.7e5): the largest single-graph configuration, generated on the device and
+transformed in the benchmark's launch configuration. Every row is checked
+against identities that hold at any size; a sample of vertices whose
+neighbourhoods the oracle can afford is checked element by element."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _oracle_cost(g):
+    """Per vertex i, a bound on the oracle's intersection work for row i:
+    sum over j in {i} + N(i), k in N(j) of min(d_j, d_k)."""
+    rp, ci = g.rowptr, g.colidx.long()
+    d = (rp[1:] - rp[:-1])
+    rows = torch.repeat_interleave(torch.arange(g.n, device=rp.device), d)
+    edge = torch.minimum(d[rows], d[ci]).double()
+    rc = torch.zeros(g.n, dtype=torch.float64, device=rp.device).index_add_(0, rows, edge)
+    cost = rc.clone().index_add_(0, rows, rc[ci])
+    return d.cpu().numpy(), cost.cpu().numpy()
+
+
+def test_rmat_s24_full_size_sampled():
+    import paper_2007_11111_gb300 as fg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dg = gg.rmat_device(24, 32, seed=0, device="cuda:0")
+    with fg.Handle(device=0) as h:
+        raw_d, net_d = h.transform(dg.rowptr, dg.colidx, dg.n)
+        torch.cuda.synchronize()
+    # identities on every row, on the device
+    deg = dg.rowptr[1:] - dg.rowptr[:-1]
+    assert bool((raw_d[:, 0] == 1).all()) and bool((raw_d[:, 1] == deg).all())
+    assert bool((net_d >= 0).all())
+    u16 = torch.from_numpy(oracle.u16()).to(raw_d.device)
+    for lo in range(0, dg.n, 1 << 18):  # raw = U16 net, in slices (integer product written out)
+        nv = net_d[lo:lo + (1 << 18)]
+        assert torch.equal(raw_d[lo:lo + (1 << 18)], (nv.unsqueeze(1) * u16.unsqueeze(0)).sum(-1)), \
+            f"raw != U16 net near {lo}"
+    s = net_d.sum(dim=0).cpu().numpy()
+    assert s[1] == dg.nnz and s[2] == 2 * s[3] and s[5] == s[6] and s[7] == 3 * s[8]
+    assert s[10] == 2 * s[9] and s[9] == s[11] and s[13] == s[14]
+    assert s[4] % 3 == 0 and s[12] % 4 == 0 and s[15] % 4 == 0
+    # sampled rows vs the oracle: vertices from every degree range whose
+    # neighbourhood intersections cost the oracle at most 2e8 steps
+    d, cost = _oracle_cost(dg)
+    rng = np.random.default_rng(24)
+    picks = []
+    for lo, hi in ((0, 1), (1, 2), (2, 9), (9, 65), (65, 513), (513, 4097), (4097, 1 << 30)):
+        cand = np.flatnonzero((d >= lo) & (d < hi) & (cost <= 2e8))
+        if cand.size:
+            picks.append(rng.choice(cand, size=min(6, cand.size), replace=False))
+    cheap = np.flatnonzero(cost <= 2e8)
+    picks.append(cheap[np.argsort(d[cheap])[-4:]])  # the highest degrees the oracle affords
+    verts = np.unique(np.concatenate(picks))
+    assert verts.size >= 30 and d[verts].max() >= 1000
+    g = dg.to_host()
+    oraw, onet = oracle.fglt(g, vertices=verts)
+    vt = torch.from_numpy(verts).to(raw_d.device)
+    np.testing.assert_array_equal(raw_d[vt].cpu().numpy(), oraw)
+    np.testing.assert_array_equal(net_d[vt].cpu().numpy(), onet)

@@ -240,12 +240,23 @@ def test_disjoint_union_is_concatenation():
 
 
 def test_vertex_subset_rows_match_full():
+    """The sampled mode computes C3 only around the requested rows; every
+    requested row must equal the full computation's (hubs, leaves, repeats)."""
     g = gg.rmat(10, 8, seed=9)
     raw, net = oracle.fglt(g)
     verts = np.array([0, 5, g.n - 1, 17, 17, 300])
     raw_s, net_s = oracle.fglt(g, vertices=verts)
     np.testing.assert_array_equal(raw_s, raw[verts])
     np.testing.assert_array_equal(net_s, net[verts])
+    # a hub-heavy graph: degree ratios far above 8 take the binary-search intersection
+    h = gg.rmat(12, 16, seed=4)
+    raw, net = oracle.fglt(h)
+    deg = np.diff(h.rowptr)
+    rng = np.random.default_rng(7)
+    for verts in (np.argsort(deg)[-5:], rng.integers(0, h.n, 30), np.array([int(np.argmax(deg))])):
+        raw_s, net_s = oracle.fglt(h, vertices=verts)
+        np.testing.assert_array_equal(raw_s, raw[verts])
+        np.testing.assert_array_equal(net_s, net[verts])
 
 
 def test_threads_do_not_change_result():
