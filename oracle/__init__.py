@@ -44,6 +44,8 @@ def _bind(path):
     lib.oracle_fglt.restype = ctypes.c_int
     lib.oracle_raw_to_net.argtypes = [ctypes.c_int64, i64p, i64p]
     lib.oracle_raw_to_net.restype = None
+    lib.oracle_raw_to_net_sub.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64p, i64p]
+    lib.oracle_raw_to_net_sub.restype = None
     lib.oracle_u16.argtypes = [i64p]
     lib.oracle_u16.restype = None
     lib.oracle_max_threads.argtypes = []
@@ -68,12 +70,19 @@ def _p32(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
 
 
-def fglt(graph, vertices=None, threads: int = 0, _lib_override=None):
-    """Raw and net frequencies (int64, shape [rows, 16]).
+def fglt(graph, vertices=None, threads: int = 0, _lib_override=None, dictionary: int = 0):
+    """Raw and net frequencies (int64, shape [rows, 16], or [rows, |s|] for a
+    sub-dictionary).
 
     graph: any object with n, rowptr (int64[n+1]) and colidx (int32[nnz]).
     vertices: None for all vertices, else the rows to compute (in that order).
-    threads: OpenMP threads (0 = all available)."""
+    threads: OpenMP threads (0 = all available).
+    dictionary: 0 for Sigma16, else the bit mask of a sub-dictionary s (bit k
+    = sigma_k): raw(s) are the Table I rows in s and net(s) = U16(s,s)^{-1}
+    raw(s), the conversion the caption of Table II gives for s."""
+    if dictionary not in (0, 0xFFFF):
+        raw, _ = fglt(graph, vertices, threads, _lib_override)
+        return sub_dictionary(raw, dictionary)
     lib = _lib_override if _lib_override is not None else _load()
     n = int(graph.n)
     rowptr = np.ascontiguousarray(graph.rowptr, dtype=np.int64)
@@ -94,6 +103,18 @@ def fglt(graph, vertices=None, threads: int = 0, _lib_override=None):
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return raw[:rows], net[:rows]
+
+
+def sub_dictionary(raw16: np.ndarray, mask: int):
+    """(raw(s), net(s)) of sub-dictionary s (bit mask) from Sigma16 raw rows."""
+    cols = [k for k in range(16) if (mask >> k) & 1]
+    if mask >> 16 or 0 not in cols or 1 not in cols:
+        raise ValueError("a sub-dictionary holds sigma_0 and sigma_1 and indices below 16")
+    raw = np.ascontiguousarray(raw16[:, cols], dtype=np.int64)
+    net = np.zeros_like(raw)
+    c = (ctypes.c_int * len(cols))(*cols)
+    _load().oracle_raw_to_net_sub(raw.shape[0], len(cols), c, _p64(raw), _p64(net))
+    return raw, net
 
 
 def raw_to_net(raw: np.ndarray) -> np.ndarray:

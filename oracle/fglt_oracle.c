@@ -111,6 +111,31 @@ static i64 merge_count(const i32* a, i64 na, const i32* b, i64 nb) {
     return c;
 }
 
+/* The common elements of two sorted lists a[0..na), b[0..nb): writes each
+ * common value to val[] and its position in b to posb[], in increasing order,
+ * and returns how many there are. A sorted merge, or, when one list is much
+ * longer, a binary search of each element of the shorter one. */
+static i64 intersect(const i32* a, i64 na, const i32* b, i64 nb, i64* val, i64* posb) {
+    i64 c = 0;
+    if (na > 8 * nb) {
+        for (i64 y = 0; y < nb; y++)
+            if (find_pos(a, na, b[y]) >= 0) { val[c] = b[y]; posb[c] = y; c++; }
+    } else if (nb > 8 * na) {
+        for (i64 x = 0; x < na; x++) {
+            i64 y = find_pos(b, nb, a[x]);
+            if (y >= 0) { val[c] = a[x]; posb[c] = y; c++; }
+        }
+    } else {
+        i64 x = 0, y = 0;
+        while (x < na && y < nb) {
+            if (a[x] < b[y]) x++;
+            else if (a[x] > b[y]) y++;
+            else { val[c] = a[x]; posb[c] = y; c++; x++; y++; }
+        }
+    }
+    return c;
+}
+
 /* A(k, l) for a vertex pair. */
 static int adjacent(const graph* g, i64 k, i32 l) {
     return find_pos(g->ci + g->rp[k], deg(g, k), l) >= 0;
@@ -136,7 +161,7 @@ static void step_C3(const graph* g, i64* C3, const unsigned char* rows_needed, i
 
 /* ---------------------------------------------------------------------------
  * Steps 5-7 for one vertex i. acc is a zeroed int64 scratch of length n and
- * touched a scratch of length n; both are left zeroed / unused on return.
+ * touched a scratch of length 2n; both are left zeroed / unused on return.
  * ------------------------------------------------------------------------- */
 typedef struct { i64 c4, d43, d4c, T; } quad_terms;
 
@@ -174,33 +199,23 @@ static quad_terms quad_row(const graph* g, i64 i, const i64* C3, i64* acc, i64* 
 
     /* Step 6: D4,c(i,j) = sum_{k in N(i)} (C3(k,j) - A(k,j))_+ for j in N(i).
      * C3(k,j) is non-zero only on edges, so the terms are C3(k,j) - 1 over the
-     * common neighbours k of i and j; the merge of N(i) and N(j) yields k
-     * together with its position in N(j), where C3(j,k) = C3(k,j) is stored. */
+     * common neighbours k of i and j; the intersection of N(i) and N(j) yields
+     * k together with its position in N(j), where C3(j,k) = C3(k,j) is stored. */
+    i64* q = touched;       /* common neighbours (reuses the scratch) */
+    i64* qpos = touched + g->n; /* their positions in N(j) */
     i64 d4c = 0;
     for (i64 x = 0; x < di; x++) {
         i64 j = Ni[x];
-        const i32* Nj = g->ci + g->rp[j];
-        i64 dj = deg(g, j), a = 0, b = 0;
-        while (a < di && b < dj) {
-            if (Ni[a] < Nj[b]) a++;
-            else if (Ni[a] > Nj[b]) b++;
-            else { d4c += rsub(C3[g->rp[j] + b], 1); a++; b++; }
-        }
+        i64 nq = intersect(Ni, di, g->ci + g->rp[j], deg(g, j), q, qpos);
+        for (i64 s = 0; s < nq; s++) d4c += rsub(C3[g->rp[j] + qpos[s]], 1);
     }
     r.d4c = d4c; /* row sum of D4,c; halved by the caller */
 
     /* Step 7: T(i,j) = q_ij^T A q_ij with q_ij = a_i o a_j, for j in N(i). */
     i64 T = 0;
-    i64* q = touched; /* reuse as the list of q's support */
     for (i64 x = 0; x < di; x++) {
         i64 j = Ni[x];
-        const i32* Nj = g->ci + g->rp[j];
-        i64 dj = deg(g, j), a = 0, b = 0, nq = 0;
-        while (a < di && b < dj) {
-            if (Ni[a] < Nj[b]) a++;
-            else if (Ni[a] > Nj[b]) b++;
-            else { q[nq++] = Ni[a]; a++; b++; }
-        }
+        i64 nq = intersect(Ni, di, g->ci + g->rp[j], deg(g, j), q, qpos);
         /* q^T A q = sum over k, l in supp(q) of A(k,l) */
         for (i64 s = 0; s < nq; s++) {
             i64 k = q[s];
@@ -239,6 +254,21 @@ static void raw_to_net_row(const i64* raw, i64* net) {
 
 void oracle_raw_to_net(i64 n, const i64* raw, i64* net) {
     for (i64 v = 0; v < n; v++) raw_to_net_row(raw + NG * v, net + NG * v);
+}
+
+/* Sub-dictionary with index set s = cols[0..k) (increasing): the conversion
+ * matrix is U16(s,s) (Table II caption), so net(s) solves U16(s,s) net = raw(s),
+ * by back substitution. raw and net are [n][k]. */
+void oracle_raw_to_net_sub(i64 n, int k, const int* cols, const i64* raw, i64* net) {
+    for (i64 v = 0; v < n; v++) {
+        const i64* r = raw + (i64)k * v;
+        i64* f = net + (i64)k * v;
+        for (int a = k - 1; a >= 0; a--) {
+            i64 s = r[a];
+            for (int b = a + 1; b < k; b++) s -= U16[cols[a]][cols[b]] * f[b];
+            f[a] = s; /* U16[cols[a]][cols[a]] == 1 */
+        }
+    }
 }
 
 /* ---------------------------------------------------------------------------
@@ -314,7 +344,7 @@ int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i
 #pragma omp parallel num_threads(nthreads)
     {
         i64* acc = (i64*)calloc((size_t)(n ? n : 1), sizeof(i64));
-        i64* touched = (i64*)malloc(sizeof(i64) * (n ? n : 1));
+        i64* touched = (i64*)malloc(sizeof(i64) * (n ? 2 * n : 1));
         if (!acc || !touched) {
 #pragma omp atomic write
             failed = 1;

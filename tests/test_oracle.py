@@ -92,6 +92,20 @@ def test_brute_force_random(block):
         np.testing.assert_array_equal(net, net_b, err_msg=f"seed {seed}")
 
 
+def test_brute_force_hub_graphs():
+    """A hub joined to every other vertex (degree ratios above 8): the oracle's
+    binary-search intersections against enumeration."""
+    from test_oracle_mutants import hub_graph
+    for seed in range(30):
+        g = hub_graph(seed)
+        deg = np.diff(g.rowptr)
+        assert (deg.max() > 8 * deg[deg > 0]).any()
+        raw_b, net_b = brute_fglt(g.n, edges_of(g))
+        raw, net = oracle.fglt(g)
+        np.testing.assert_array_equal(raw, raw_b)
+        np.testing.assert_array_equal(net, net_b)
+
+
 def test_brute_force_structured():
     cases = [gg.complete(5), gg.star(5), gg.path(6), gg.cycle(4), gg.cycle(6),
              gg.from_edge_list(5, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4)]),
@@ -265,3 +279,69 @@ def test_threads_do_not_change_result():
     b = oracle.fglt(g, threads=4)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
+
+
+# --------------------------------------------------------------------------
+# Sub-dictionaries (Table II caption: s has the conversion matrix U16(s,s))
+# --------------------------------------------------------------------------
+
+def _golden_u16():
+    return np.array(read_golden_sections("u16_table2.txt")[None], dtype=np.int64)
+
+
+def _closed(mask, U):
+    """s is closed when every graphlet that raw rows in s count (U[k][l] != 0)
+    is itself in s; then the induced counts of s need no graphlet outside s."""
+    s = [k for k in range(16) if (mask >> k) & 1]
+    return all((mask >> l) & 1 for k in s for l in range(16) if U[k, l])
+
+
+CLOSED = [0x1F, 0x13, 0x3, 0x1 | 0x2 | (1 << 8) | (1 << 11) | (1 << 14) | (1 << 15),
+          0x3 | (1 << 12) | (1 << 13) | (1 << 14) | (1 << 15), 0x3 | (1 << 15)]
+
+
+def test_sub_dictionary_closed_sets_are_induced_counts():
+    """For a closed s (Sigma5 among them), net(s) are the induced orbit counts
+    of the graphlets in s: brute-force enumeration, no Table I or II."""
+    U = _golden_u16()
+    for mask in CLOSED:
+        assert _closed(mask, U), hex(mask)
+    cols = lambda m: [k for k in range(16) if (m >> k) & 1]  # noqa: E731
+    for seed in range(60):
+        g = _random_small(seed)
+        raw_b, net_b = brute_fglt(g.n, edges_of(g))
+        for mask in CLOSED:
+            raw, net = oracle.fglt(g, dictionary=mask)
+            np.testing.assert_array_equal(raw, raw_b[:, cols(mask)], err_msg=f"{hex(mask)} seed {seed}")
+            np.testing.assert_array_equal(net, net_b[:, cols(mask)], err_msg=f"{hex(mask)} seed {seed}")
+
+
+def test_sigma5_fig2_tables():
+    """Sigma5 on the Fig. 2 example: the first five columns of both printed tables."""
+    g, _, raw_ref, net_ref = _fig2()
+    raw, net = oracle.fglt(g, dictionary=0x1F)
+    np.testing.assert_array_equal(raw, raw_ref[:, :5])
+    np.testing.assert_array_equal(net, net_ref[:, :5])
+
+
+def test_sub_dictionary_any_set_solves_its_conversion():
+    """Any s containing {0,1}: U16(s,s) net(s) = raw(s), with U16 from the
+    golden Table II and raw from brute-force enumeration."""
+    U = _golden_u16()
+    rng = np.random.default_rng(5)
+    masks = [0x3 | (int(rng.integers(0, 1 << 14)) << 2) for _ in range(25)] + [0x3 | (1 << 5), 0x3 | (1 << 12)]
+    for seed in range(12):
+        g = _random_small(100 + seed)
+        raw_b, _ = brute_fglt(g.n, edges_of(g))
+        for mask in masks:
+            s = [k for k in range(16) if (mask >> k) & 1]
+            raw, net = oracle.fglt(g, dictionary=mask)
+            np.testing.assert_array_equal(raw, raw_b[:, s])
+            np.testing.assert_array_equal(net @ U[np.ix_(s, s)].T, raw)
+
+
+def test_sub_dictionary_rejects_sets_without_sigma0_sigma1():
+    g = gg.complete(4)
+    for mask in (0x1, 0x2, 0x1C, 1 << 16 | 0x3):
+        with pytest.raises(ValueError):
+            oracle.fglt(g, dictionary=mask)

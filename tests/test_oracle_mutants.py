@@ -34,7 +34,13 @@ MUTANTS = {
     "d11 transposed": ("f[11] = rsub(d, 2) * c3[i];", "f[11] = rsub(d, 2) * p2[i];"),
     "c4 not halved": ("r.c4 = c42 / 2;", "r.c4 = c42;"),
     "c4 keeps l == i": ("if (l == i) continue;", ""),
-    "D4c without -A": ("d4c += rsub(C3[g->rp[j] + b], 1);", "d4c += C3[g->rp[j] + b];"),
+    "D4c without -A": ("d4c += rsub(C3[g->rp[j] + qpos[s]], 1);", "d4c += C3[g->rp[j] + qpos[s]];"),
+    "intersect (long first list) position": ("{ val[c] = b[y]; posb[c] = y; c++; }",
+                                             "{ val[c] = b[y]; posb[c] = 0; c++; }"),
+    "intersect (long second list) value": ("if (y >= 0) { val[c] = a[x]; posb[c] = y; c++; }",
+                                           "if (y >= 0) { val[c] = b[0]; posb[c] = y; c++; }"),
+    "C3 binary search misses": ("for (i64 x = 0; x < ns; x++) c += find_pos(l, nl, s[x]) >= 0;",
+                                "for (i64 x = 1; x < ns; x++) c += find_pos(l, nl, s[x]) >= 0;"),
     "D4,3 wrong index": ("i64 p = acc[Ni[x]];", "i64 p = acc[x];"),
     "T divisor": ("f[15] = qt.T / 6;", "f[15] = qt.T / 3;"),
     "U16 entry": ("/* 5 */ { 0, 0, 0, 0, 0, 1, 0, 0, 0, 2, 1, 0, 2, 4, 2, 6 },",
@@ -73,7 +79,28 @@ def _pins_pass(lib):
         r, nn = oracle.fglt(h, _lib_override=lib)
         if not (np.array_equal(r, rb) and np.array_equal(nn, nb)):
             return False
+    for seed in range(12):  # hub graphs: degree ratios above 8 take the binary-search intersections
+        h = hub_graph(seed)
+        rb, nb = brute_fglt(h.n, edges_of(h))
+        r, nn = oracle.fglt(h, _lib_override=lib)
+        if not (np.array_equal(r, rb) and np.array_equal(nn, nb)):
+            return False
     return True
+
+
+def hub_graph(seed, n=27):
+    """Vertex n//2 joined to every other vertex, plus a few random edges among
+    the others (two of them stay pendant): the hub's degree is more than 8
+    times that of the vertices of degree up to 3, and it sits in the middle of
+    their sorted neighbour lists."""
+    rng = np.random.default_rng(2000 + seed)
+    hub = n // 2
+    others = np.array([v for v in range(n) if v != hub], np.int64)
+    i, j = np.triu_indices(n - 1, 1)
+    keep = (rng.random(i.size) < 0.08) & (i >= 2)  # others[0] and others[1] stay pendant
+    src = np.concatenate([np.full(n - 1, hub, np.int64), others[i[keep]]])
+    dst = np.concatenate([others, others[j[keep]]])
+    return gg.csr_from_pairs(n, src, dst)
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
