@@ -21,9 +21,11 @@
  *    fglt_options.validate = 1 these preconditions are checked on the device
  *    and a violation returns FGLT_ERR_INVALID_GRAPH; otherwise a violating
  *    input gives unspecified counts (never a fault).
- *  - Output is row-major int64 [n][16]: row v, column k = frequency of sigma_k
- *    at vertex v (the orientation of the tables of Fig. 2). Either output
- *    pointer may be NULL to skip it (not both).
+ *  - Output is row-major int64 [n][C]: row v, column k = frequency of sigma_k
+ *    at vertex v (the orientation of the tables of Fig. 2); C = 16 for
+ *    Sigma16, or the size of the handle's sub-dictionary (see
+ *    fglt_options.dictionary_mask). Either output pointer may be NULL to skip
+ *    it (not both).
  *  - Ownership: the caller owns every buffer it passes; the library never frees
  *    them and keeps no pointer to them after the call returns. The handle owns
  *    its device workspace, its stream and its serving slots.
@@ -77,12 +79,42 @@ typedef struct {
     /* 1: record CUDA events around every stage of each transform so that
      * fglt_stage_times can report per-stage device time. */
     int profile_stages;
-    /* Tuning: number of top-ranked (highest-degree) vertices that get dense
-     * shared-memory counters in the 4-cycle stage. 0 selects the largest span
-     * that fits (32768, or 16384 when some degree is >= 65536); smaller values
-     * move work to the hash-table paths. Results do not depend on it. */
+    /* Tuning (fglt_autotune picks these; the counts never depend on them; 0
+     * selects the default):
+     * cyc_hub_span: number of top-ranked (highest-degree) vertices that get
+     *   dense 16-bit shared-memory counters in the 4-cycle stage (at most
+     *   90112). 0 selects 32768, or 65536 for graphs above 2^21 vertices.
+     *   Smaller values move work to the hash-table paths and raise occupancy. */
     int cyc_hub_span;
+    /* tri_class_bounds: the triangle passes split the vertices by out-degree
+     *   d+ in the degree order into (2, t0], (t0, t1], (t1, ...), each launched
+     *   with shared memory sized for its largest d+ (default 64, 256;
+     *   2 <= t0 < t1). */
+    int tri_class_bounds[2];
+    /* cyc_warp_bits: log2 of the per-warp hash-table slots of the 4-cycle
+     *   stage's warp class, which takes vertices with at most 2^(bits-1)
+     *   wedges (6..10, default 10). */
+    int cyc_warp_bits;
+    /* cyc_mid_threads: thread-block size (256, 512 or 1024; default 256) of
+     *   the three block hash-table classes of the 4-cycle stage (tables of
+     *   2^11, 2^12, 2^13 slots). */
+    int cyc_mid_threads[3];
+    /* cyc_heavy_threads: block size of the dense-counter and global-table
+     *   classes of the 4-cycle stage (256, 512 or 1024; default 1024). */
+    int cyc_heavy_threads;
+    /* Sub-dictionary s of Sigma16 (Table II caption): bit k set = sigma_k in
+     * s; 0 (or 0xFFFF) selects Sigma16. Bits 0 and 1 must be set and no bit
+     * above 15. Outputs then hold C = popcount(s) columns, sigma indices in
+     * increasing order: raw = the Table I rows in s, net = U16(s,s)^{-1} raw.
+     * Stages that no row in s needs are skipped; e.g. Sigma5 = 0x1F (the
+     * graphlets on up to 3 nodes, the Sigma5 theorem of Sec. 3) needs only
+     * degrees, p2 and the triangle counts c3. Applies to every entry point of
+     * the handle (fglt_transform_noalloc always computes Sigma16). */
+    unsigned int dictionary_mask;
 } fglt_options;
+
+/* dictionary_mask of Sigma5 = {sigma_0 .. sigma_4}. */
+#define FGLT_DICT_SIGMA5 0x1Fu
 
 /* Fills *opt with the defaults (all fields 0 = automatic). */
 fglt_status fglt_options_default(fglt_options* opt);
@@ -106,7 +138,7 @@ const char* fglt_last_cuda_error(fglt_t handle);
  *   rowptr          device pointer, n+1 entries, int64 if rowptr_is_64bit else int32
  *   colidx          device pointer, rowptr[n] int32 entries (NULL allowed if no edges)
  *   n               number of vertices (0 allowed: nothing is written)
- *   out_raw/out_net device pointers to n*16 int64, or NULL to skip one
+ *   out_raw/out_net device pointers to n*C int64 (C = 16 for Sigma16), or NULL to skip one
  *   stream          cudaStream_t to order the work on, or NULL for the handle's stream
  * Computes Table I (raw) and Table II's inverse (net) for every vertex:
  * degrees and the SpMV chains of Sec. 3-4 (p1, p2, p3, d^7, d^9, d^10),
@@ -133,7 +165,7 @@ fglt_status fglt_transform_host(fglt_t handle, const void* rowptr, int rowptr_is
  *                     join two graphs)
  *   graph_offsets     HOST array, num_graphs+1 entries: graph g owns vertices
  *                     [graph_offsets[g], graph_offsets[g+1]); graph_offsets[0] = 0
- *   out_raw, out_net  device n*16 int64 (n = graph_offsets[num_graphs])
+ *   out_raw, out_net  device n*C int64 (n = graph_offsets[num_graphs])
  * The transform of a disjoint union is the concatenation of the transforms
  * (every graphlet is connected, Fig. 1), so the whole batch runs as one
  * sequence of launches captured once as a CUDA graph and replayed for batches
@@ -144,9 +176,52 @@ fglt_status fglt_transform_batched(fglt_t handle, const void* rowptr, int rowptr
                                    int64_t num_graphs, int64_t* out_raw, int64_t* out_net,
                                    void* stream);
 
+/*
+ * Autotuner: times the transform of the given graph (device buffers, as for
+ * fglt_transform) under candidate settings of the tuning fields of
+ * fglt_options (degree-class bounds of the triangle passes, hash-table sizes
+ * and thread-block shapes of the 4-cycle classes, dense hub span), one
+ * parameter at a time from the current settings, keeps every change that
+ * lowers the device time of the stage it affects, and installs the result
+ * on the handle for its later single-graph, host and batched calls (serving
+ * lanes take the handle's settings when the first request is submitted).
+ * The counts never depend on these settings. Runs about 12 + 2 *
+ * reps transforms on `stream`; reps >= 1 timings per candidate (minimum
+ * taken). chosen (nullable) receives the full option set in use afterwards.
+ * tuned_ms / default_ms (nullable) receive the device time of one transform
+ * with the chosen and with the starting settings.
+ */
+fglt_status fglt_autotune(fglt_t handle, const void* rowptr, int rowptr_is_64bit, const int32_t* colidx,
+                          int64_t n, int reps, void* stream, fglt_options* chosen, float* tuned_ms,
+                          float* default_ms);
+
+/*
+ * Builds the CSR input of the transform from an undirected edge list (device
+ * buffers). The paper assumes a simple undirected graph (Sec. 1); this entry
+ * makes one from any list of vertex pairs: vertex set {0 .. n-1}, an edge
+ * {src[e], dst[e]} for every e, pairs in any order, in either or both
+ * directions, repeated or not; self-loops are dropped and repeats merged.
+ *   src, dst     device int32[num_edges], ids in [0, n)
+ *   out_rowptr   device int64[n+1]
+ *   out_colidx   device int32 with room for 2 * num_edges entries (the most
+ *                the graph can have)
+ *   out_nnz      host; receives rowptr[n] (twice the number of edges)
+ * Rows come out sorted, symmetric and duplicate-free, ready for
+ * fglt_transform. FGLT_ERR_INVALID_GRAPH if an id is outside [0, n) (the
+ * outputs are then unspecified). Uses the handle's workspace; returns after
+ * the work completed on stream (NULL = the handle's stream).
+ */
+fglt_status fglt_csr_from_edges(fglt_t handle, const int32_t* src, const int32_t* dst, int64_t num_edges,
+                                int64_t n, int64_t* out_rowptr, int32_t* out_colidx, int64_t* out_nnz,
+                                void* stream);
+
 /* Per-stage device times (ms) of the last transform on this handle; requires
  * fglt_options.profile_stages = 1. names[i] points to static strings.
- * *count receives the number of stages (at most max_stages are written). */
+ * *count receives the number of entries (at most max_stages are written):
+ * the stages in order (degree, spmv1, rank, orient, sort, tri1, c3_edges,
+ * spmv2, tri2, wedges, cyc, epilogue), then the six 4-cycle vertex classes
+ * inside "cyc" (cyc.warp, cyc.hash11, cyc.hash12, cyc.hash13, cyc.dense,
+ * cyc.global; 0 when the stage did not run). */
 fglt_status fglt_stage_times(fglt_t handle, const char** names, float* ms,
                              int max_stages, int* count);
 
@@ -165,6 +240,9 @@ fglt_status fglt_stage_times(fglt_t handle, const char** names, float* ms,
  *   8 wedges enumerated by the 4-cycle stage
  *   9 largest wedge count of one vertex
  *  10 kernel launches the transform issued (memsets not included)
+ *  11..16 vertices in each 4-cycle vertex class (the order of the cyc.*
+ *         entries of fglt_stage_times)
+ *  17..22 wedges of the vertices in each class
  * FGLT_ERR_NOT_FOUND if no transform has completed on the handle. */
 fglt_status fglt_work_counters(fglt_t handle, int64_t* counters, int max_counters, int* count);
 
@@ -203,8 +281,8 @@ typedef struct {
     int64_t n;              /* vertices */
     const int64_t* rowptr;  /* host, n+1 entries */
     const int32_t* colidx;  /* host, rowptr[n] entries */
-    int64_t* out_raw;       /* host, n*16, or NULL */
-    int64_t* out_net;       /* host, n*16, or NULL */
+    int64_t* out_raw;       /* host, n*C (C as for fglt_transform), or NULL */
+    int64_t* out_net;       /* host, n*C, or NULL */
 } fglt_graph_host;
 
 /* Queues a request. The CSR is copied into a staging buffer before the call

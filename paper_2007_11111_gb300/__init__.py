@@ -19,6 +19,19 @@ import numpy as np
 from . import buildlib as _build
 
 NUM_GRAPHLETS = 16
+DICT_SIGMA5 = 0x1F  # sigma_0 .. sigma_4
+
+
+def dictionary_mask(sigmas) -> int:
+    """Bit mask of a sub-dictionary given as sigma indices (e.g. range(5))."""
+    m = 0
+    for k in sigmas:
+        m |= 1 << int(k)
+    return m
+
+
+def dictionary_columns(mask: int) -> int:
+    return 16 if mask in (0, 0xFFFF) else bin(mask).count("1")
 
 FGLT_OK = 0
 FGLT_ERR_INVALID_ARG = 1
@@ -49,7 +62,18 @@ class fglt_options(ctypes.Structure):
         ("serve_max_queue", ctypes.c_int),
         ("profile_stages", ctypes.c_int),
         ("cyc_hub_span", ctypes.c_int),
+        ("tri_class_bounds", ctypes.c_int * 2),
+        ("cyc_warp_bits", ctypes.c_int),
+        ("cyc_mid_threads", ctypes.c_int * 3),
+        ("cyc_heavy_threads", ctypes.c_int),
+        ("dictionary_mask", ctypes.c_uint),
     ]
+
+    def tuning(self) -> dict:
+        """The tuning fields (0 = default)."""
+        return {"cyc_hub_span": self.cyc_hub_span, "tri_class_bounds": list(self.tri_class_bounds),
+                "cyc_warp_bits": self.cyc_warp_bits, "cyc_mid_threads": list(self.cyc_mid_threads),
+                "cyc_heavy_threads": self.cyc_heavy_threads}
 
 
 class fglt_graph_host(ctypes.Structure):
@@ -65,7 +89,8 @@ class fglt_graph_host(ctypes.Structure):
 EXPORTED = [
     "fglt_options_default", "fglt_create", "fglt_destroy", "fglt_status_string", "fglt_last_cuda_error",
     "fglt_transform", "fglt_transform_host", "fglt_transform_batched", "fglt_stage_times", "fglt_work_counters",
-    "fglt_stream_submit", "fglt_stream_poll", "fglt_stream_cancel", "fglt_transform_noalloc",
+    "fglt_stream_submit", "fglt_stream_poll", "fglt_stream_cancel", "fglt_transform_noalloc", "fglt_autotune",
+    "fglt_csr_from_edges",
 ]
 
 _lib = None
@@ -101,6 +126,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.fglt_stage_times.argtypes = [h_t, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                      c_int, ctypes.POINTER(c_int)]
     lib.fglt_transform_noalloc.argtypes = [vp, c_int, vp, i64, vp, vp, vp]
+    lib.fglt_csr_from_edges.argtypes = [h_t, vp, vp, i64, i64, vp, vp, ctypes.POINTER(i64), vp]
+    lib.fglt_autotune.argtypes = [h_t, vp, c_int, vp, i64, c_int, vp, ctypes.POINTER(fglt_options),
+                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
     lib.fglt_work_counters.argtypes = [h_t, ctypes.POINTER(ctypes.c_int64), c_int, ctypes.POINTER(c_int)]
     lib.fglt_stream_submit.argtypes = [h_t, ctypes.POINTER(fglt_graph_host), ctypes.POINTER(ctypes.c_uint64)]
     lib.fglt_stream_poll.argtypes = [h_t, ctypes.c_uint64, c_int, ctypes.POINTER(ctypes.c_double)]
@@ -204,6 +232,27 @@ def fglt_transform_noalloc(rowptr, rowptr_is_64bit: int, colidx, n: int, out_raw
                                          _ptr(out_net), _stream_ptr(stream)), "fglt_transform_noalloc")
 
 
+def fglt_autotune(h, rowptr, rowptr_is_64bit: int, colidx, n: int, reps: int = 1, stream=None):
+    """Runs the autotuner on one graph (device buffers) and installs the result
+    on the handle. Returns (chosen fglt_options, tuned_ms, default_ms)."""
+    opt = fglt_options()
+    tuned = ctypes.c_float()
+    default = ctypes.c_float()
+    _check(load().fglt_autotune(h, _ptr(rowptr), int(rowptr_is_64bit), _ptr(colidx), int(n), int(reps),
+                                _stream_ptr(stream), ctypes.byref(opt), ctypes.byref(tuned), ctypes.byref(default)),
+           "fglt_autotune", h)
+    return opt, tuned.value, default.value
+
+
+def fglt_csr_from_edges(h, src, dst, num_edges: int, n: int, out_rowptr, out_colidx, stream=None) -> int:
+    """Edge list -> sorted symmetric simple CSR (device buffers); returns nnz."""
+    nnz = ctypes.c_int64()
+    _check(load().fglt_csr_from_edges(h, _ptr(src), _ptr(dst), int(num_edges), int(n), _ptr(out_rowptr),
+                                      _ptr(out_colidx), ctypes.byref(nnz), _stream_ptr(stream)),
+           "fglt_csr_from_edges", h)
+    return nnz.value
+
+
 def fglt_stage_times(h) -> dict:
     names = (ctypes.c_char_p * 32)()
     ms = (ctypes.c_float * 32)()
@@ -215,14 +264,16 @@ def fglt_stage_times(h) -> dict:
     return {names[i].decode(): float(ms[i]) for i in range(min(cnt.value, 32))}
 
 
-WORK_COUNTER_NAMES = ["n", "nnz", "m", "max_degree", "max_out_degree", "tri_scanned", "triangles",
-                      "k4", "wedges", "max_wedges", "launches"]
+CYC_CLASSES = ["warp", "hash11", "hash12", "hash13", "dense", "global"]
+WORK_COUNTER_NAMES = (["n", "nnz", "m", "max_degree", "max_out_degree", "tri_scanned", "triangles",
+                       "k4", "wedges", "max_wedges", "launches"] + [f"cls_vertices.{c}" for c in CYC_CLASSES]
+                      + [f"cls_wedges.{c}" for c in CYC_CLASSES])
 
 
 def fglt_work_counters(h) -> dict:
-    vals = (ctypes.c_int64 * 16)()
+    vals = (ctypes.c_int64 * 32)()
     cnt = ctypes.c_int()
-    st = load().fglt_work_counters(h, vals, 16, ctypes.byref(cnt))
+    st = load().fglt_work_counters(h, vals, 32, ctypes.byref(cnt))
     if st == FGLT_ERR_NOT_FOUND:
         return {}
     _check(st, "fglt_work_counters")
@@ -264,9 +315,18 @@ class Handle:
 
     def __init__(self, device: int = 0, validate: bool = False, profile_stages: bool = False,
                  serve_memory_budget: int = 0, serve_max_batch: int = 0, serve_max_queue: int = 0,
-                 cyc_hub_span: int = 0):
+                 cyc_hub_span: int = 0, tri_class_bounds=(0, 0), cyc_warp_bits: int = 0,
+                 cyc_mid_threads=(0, 0, 0), cyc_heavy_threads: int = 0, dictionary: int = 0):
+        """dictionary: sub-dictionary bit mask (0 = Sigma16; DICT_SIGMA5 = Sigma5)."""
         opt = fglt_options_default()
+        opt.dictionary_mask = int(dictionary)
+        self.cols = dictionary_columns(int(dictionary))
         opt.cyc_hub_span = int(cyc_hub_span)
+        opt.tri_class_bounds[0], opt.tri_class_bounds[1] = (int(x) for x in tri_class_bounds)
+        opt.cyc_warp_bits = int(cyc_warp_bits)
+        for i, x in enumerate(cyc_mid_threads):
+            opt.cyc_mid_threads[i] = int(x)
+        opt.cyc_heavy_threads = int(cyc_heavy_threads)
         opt.validate = int(validate)
         opt.profile_stages = int(profile_stages)
         opt.serve_memory_budget = int(serve_memory_budget)
@@ -295,16 +355,16 @@ class Handle:
         """Device transform; rowptr/colidx/out_* are torch CUDA tensors."""
         import torch
         if out_raw is None:
-            out_raw = torch.empty((n, 16), dtype=torch.int64, device=rowptr.device)
+            out_raw = torch.empty((n, self.cols), dtype=torch.int64, device=rowptr.device)
         if out_net is None:
-            out_net = torch.empty((n, 16), dtype=torch.int64, device=rowptr.device)
+            out_net = torch.empty((n, self.cols), dtype=torch.int64, device=rowptr.device)
         rp64 = 1 if rowptr.dtype == torch.int64 else 0
         fglt_transform(self.h, rowptr, rp64, colidx, n, out_raw, out_net, stream)
         return out_raw, out_net
 
     def transform_host(self, rowptr: np.ndarray, colidx: np.ndarray, n: int):
-        raw = np.empty((n, 16), dtype=np.int64)
-        net = np.empty((n, 16), dtype=np.int64)
+        raw = np.empty((n, self.cols), dtype=np.int64)
+        net = np.empty((n, self.cols), dtype=np.int64)
         rp = np.ascontiguousarray(rowptr)
         rp64 = 1 if rp.dtype == np.int64 else 0
         ci = np.ascontiguousarray(colidx, dtype=np.int32)
@@ -318,12 +378,30 @@ class Handle:
         off = np.ascontiguousarray(graph_offsets, dtype=np.int64)
         n = int(off[-1])
         if out_raw is None:
-            out_raw = torch.empty((n, 16), dtype=torch.int64, device=rowptr.device)
+            out_raw = torch.empty((n, self.cols), dtype=torch.int64, device=rowptr.device)
         if out_net is None:
-            out_net = torch.empty((n, 16), dtype=torch.int64, device=rowptr.device)
+            out_net = torch.empty((n, self.cols), dtype=torch.int64, device=rowptr.device)
         rp64 = 1 if rowptr.dtype == torch.int64 else 0
         fglt_transform_batched(self.h, rowptr, rp64, colidx, off, len(off) - 1, out_raw, out_net, stream)
         return out_raw, out_net
+
+    def csr_from_edges(self, src, dst, n: int, stream=None):
+        """Edge list (torch CUDA int32 tensors) -> (rowptr int64[n+1], colidx
+        int32[nnz]) on the same device: symmetric, sorted, no self-loops or
+        repeats."""
+        import torch
+        rowptr = torch.empty(n + 1, dtype=torch.int64, device=src.device)
+        colidx = torch.empty(max(2 * src.numel(), 1), dtype=torch.int32, device=src.device)
+        nnz = fglt_csr_from_edges(self.h, src, dst, src.numel(), n, rowptr, colidx, stream)
+        return rowptr, colidx[:nnz]
+
+    def autotune(self, rowptr, colidx, n: int, reps: int = 1, stream=None):
+        """Autotunes on this graph (torch CUDA tensors); returns (tuning dict,
+        tuned ms, default ms). Later calls on this handle use the result."""
+        import torch
+        rp64 = 1 if rowptr.dtype == torch.int64 else 0
+        opt, tuned, default = fglt_autotune(self.h, rowptr, rp64, colidx, n, reps, stream)
+        return opt.tuning(), tuned, default
 
     def stage_times(self) -> dict:
         return fglt_stage_times(self.h)

@@ -19,8 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfglt.so")
 
-SOURCES = ["k_prep.cu", "k_tri.cu", "k_cyc.cu", "fglt_capi.cu", "fglt_serve.cu", "fglt_noalloc.cu"]
-HEADERS = ["fglt_device.cuh", "fglt_kernels.h", "fglt_serve.h"]
+SOURCES = ["k_prep.cu", "k_tri.cu", "k_cyc.cu", "k_ingest.cu", "fglt_pipeline.cu", "fglt_capi.cu", "fglt_serve.cu", "fglt_noalloc.cu"]
+HEADERS = ["fglt_device.cuh", "fglt_kernels.h", "fglt_pipeline.h", "fglt_serve.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-Xptxas", "-v", f"-I{INCLUDE}", f"-I{CSRC}"]

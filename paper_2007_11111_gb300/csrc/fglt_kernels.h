@@ -78,11 +78,12 @@ size_t tri1_smem_bytes(int dpmax, bool bitmap_in_smem);
 size_t tri2_smem_bytes(int dpmax);
 bool tri1_bitmap_fits_smem(int dpmax);
 int tri_grid_blocks();
-// C3 per oriented edge, c3 per vertex, 4-clique count per vertex.
-// work_ctr[0..2] += (scanned out-list entries, triangles, 4-cliques).
+// C3 per oriented edge, c3 per vertex, 4-clique count per vertex (only with
+// cliques = true). work_ctr[0..2] += (scanned out-list entries, triangles,
+// 4-cliques).
 cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm,
-                        u64* work_ctr, int* err, cudaStream_t st);
+                        u64* work_ctr, int* err, cudaStream_t st, bool cliques = true);
 size_t tri1_gbm_bytes(int dpmax);
 // d^13 (diamond, off-cord) per vertex from the final C3.
 cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
@@ -95,47 +96,71 @@ cudaError_t launch_unrank_u64(const u64* src_r, const int32_t* perm, int64_t n, 
                               cudaStream_t st);
 
 // --- 4-cycles (rank space) ---------------------------------------------------
-// wc[rank w] = wedges w - v - u (u in N+(v), u > w); wcn[rank w] = those with
-// u < hub_lo; *wmax = max wc, *wsum = total wedges.
-cudaError_t launch_wedge_count(const Csr& g, const int32_t* rank, const int64_t* orp, const int32_t* ocol,
-                               const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap, int32_t hub_lo,
-                               int64_t* wc, int64_t* wcn, u64* wmax, u64* wsum, cudaStream_t st);
-// Dense counter span of the heavy-vertex kernel (16-bit counters when every
-// degree is below 65536, else 32-bit).
-int cyc_dense_span(bool c16);
+constexpr int CYC_CLASSES = 6;
+// Largest window of top ranks the dense class can hold (16-bit counters in
+// shared memory).
+int cyc_dense_span_max();
 // Largest per-vertex table need served by shared-memory tables; vertices above
 // it may need the global-memory class.
 int cyc_block_cap();
 int cyc_gmem_blocks();
-// Splits the vertices with at least two wedges into four classes (lists at
-// lists + c * list_stride, counts[c]): warp table, block hash table, dense hub
-// counters (only if dense_ok), global hash table; *gcap_max = largest table
-// need of the last class.
-// cap_bound caps the distinct tops of one vertex (e.g. the largest graph of a
-// block-diagonal batch minus one); pass n when unknown.
-cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, int64_t n, int32_t* lists,
-                                 int64_t list_stride, int32_t* counts, u64* gcap_max, bool dense_ok,
-                                 cudaStream_t st, int64_t cap_bound);
+int cyc_warp_bits_max();
+// In-lists of the oriented graph and the stage's wedge counts. For each rank w:
+// iin[irp[w] .. irp[w+1]) = (v, j) with w = N+(v)[j] (any order; capacity
+// dr[w] - opc[w]); wc[w] = wedges w - v - u with u in N+(v) above w; wcn[w] =
+// those with u < hub_lo. hc, indeg: n int32 scratch; irp: n+1; icur: n int32
+// zeroed; iin: m entries set to -1 bytes beforehand; wc, wcn zeroed.
+cudaError_t launch_in_lists(const int64_t* orp, const int32_t* ocol, const int32_t* dr, const int32_t* opc,
+                            int64_t n, int32_t hub_lo, int32_t* hc, int32_t* indeg, int64_t* irp, void* scan_tmp,
+                            int32_t* icur, int2* iin, int64_t* wc, int64_t* wcn, cudaStream_t st);
+// Splits the vertices with at least two wedges into CYC_CLASSES classes (lists
+// at lists + c * list_stride, counts[c]): warp table (wc <= 2^(wbits-1)),
+// three block hash-table sizes, dense hub counters (only if dense_ok, for
+// vertices of degree dr < 65536), global hash table; *gcap_max = largest table need of the last class; *wmax, *wsum =
+// largest and total wedge count. cap_bound caps the distinct tops of one
+// vertex (e.g. the largest graph of a block-diagonal batch minus one); pass n
+// when unknown.
+// cls_wedges[c] += wedges of the vertices in class c.
+cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, const int32_t* dr, int64_t n, int32_t* lists,
+                                 int64_t list_stride, int32_t* counts, u64* gcap_max, u64* wmax, u64* wsum,
+                                 u64* cls_wedges, bool dense_ok, int64_t cap_bound, int wbits, cudaStream_t st);
 struct CycArgs {
-  const int32_t* rank;
-  const int32_t* perm;
+  int64_t n;
   const int64_t* orp;
   const int32_t* ocol;
+  const int64_t* irp;
+  const int2* iin;
   const int64_t* wc;
   const int32_t* lists;
   int64_t list_stride;
-  const int32_t* counts;  // 4 class sizes
-  int* next;              // 4 scheduling counters (zeroed)
-  bool c16;
+  const int32_t* counts;  // CYC_CLASSES class sizes
+  int* next;              // CYC_CLASSES scheduling counters (zeroed)
   int32_t hub_lo;
-  int gbits;              // class-3 tables: cyc_gmem_blocks() << gbits slots each array
-  uint32_t* gkeys;        // NULL when class 3 is empty
+  int wbits;              // warp-class table slots (log2, at most cyc_warp_bits_max())
+  int mid_threads[3];     // block sizes of the three hash-table classes (256, 512 or 1024)
+  int heavy_threads;      // block size of the dense and global classes
+  int gbits;              // global class: cyc_gmem_blocks() << gbits slots each array
+  uint32_t* gkeys;        // NULL when the global class is empty
   uint32_t* gcnt;
   u64* r12r;
   int* err;
   int64_t cap_bound;      // bound on distinct tops of one vertex (n when unknown)
+  cudaEvent_t* ev;        // CYC_CLASSES + 1 events around the class launches, or NULL
 };
-cudaError_t launch_cyc(const Csr& g, const CycArgs& a, cudaStream_t st);
+cudaError_t launch_cyc(const CycArgs& a, cudaStream_t st);
+
+// --- edge-list ingest (k_ingest.cu) ---------------------------------------------
+// deg0[v] += entries of v (both directions, self-loops skipped; zeroed
+// beforehand); *dmax = max deg0 (zeroed); ids outside [0, n) flag ERR_BAD_GRAPH.
+cudaError_t launch_edge_count(const int32_t* src, const int32_t* dst, int64_t E, int64_t n, int32_t* deg0,
+                              int32_t* dmax, int* err, cudaStream_t st);
+// tmp[rp0[v] + k] = the other end of v's k-th entry (cursor zeroed).
+cudaError_t launch_edge_fill(const int32_t* src, const int32_t* dst, int64_t E, int64_t n, const int64_t* rp0,
+                             int32_t* cursor, int32_t* tmp, cudaStream_t st);
+// Rows of tmp sorted: colidx == NULL counts the distinct entries of each row
+// into deg; otherwise writes them to colidx at rowptr.
+cudaError_t launch_row_unique(const int64_t* rp0, const int32_t* tmp, int64_t n, int32_t* deg, const int64_t* rowptr,
+                              int32_t* colidx, cudaStream_t st);
 
 // --- epilogue ------------------------------------------------------------------
 struct EpilogueIn {
@@ -154,5 +179,15 @@ struct EpilogueIn {
 };
 // Table I assembly and the exact int64 U16^{-1} product.
 cudaError_t launch_epilogue(const EpilogueIn& in, int64_t n, int64_t* raw, int64_t* net, cudaStream_t st);
+
+// Sub-dictionary s (Table II caption): the k columns col[0..k) of Table I
+// (increasing sigma index) and the inverse of U16(s,s), row-major k x k.
+struct SubDict {
+  int k;
+  int col[16];
+  long long uinv[16][16];
+};
+cudaError_t launch_epilogue_sub(const EpilogueIn& in, const SubDict& sd, int64_t n, int64_t* raw, int64_t* net,
+                                cudaStream_t st);
 
 }  // namespace fglt

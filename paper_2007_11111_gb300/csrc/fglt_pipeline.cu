@@ -1,0 +1,467 @@
+// The stage sequence of one transform (every entry point runs it).
+//
+//   degree            p1 = A e                                   (Sec. 3.1)
+//   spmv1             p2 = A p1 - p1, d^7 = A((p1-1)o(p1-2))/2   (Sec. 3.1, 4.2)
+//   rank, orient      degree order; oriented out-lists N+ sorted by rank
+//   sort              (the cost model of Appendix A)
+//   tri1              C3 = A o A^2 per edge, c3, 4-cliques T     (Lemma 2, Sec. 4.3)
+//   c3_edges          d^10 = C3 (p1 - 2), d^14 = D4,3 e / 2      (Sec. 4.2, 4.3)
+//   spmv2             p3 = A p2 - p1 o (p1-1) - 2 c3, d^9        (Sec. 4.1, 4.2)
+//   tri2              d^13 = D4,c e / 2                          (Sec. 4.3)
+//   wedges            in-lists and wedge counts of the 4-cycle stage
+//   cyc               c4 = C4,2 e / 2                            (Lemma on c4)
+//   epilogue          Table I, then f = U16^{-1} f^              (Table II)
+#include "fglt_pipeline.h"
+
+#include <algorithm>
+#include <cstring>
+#include <initializer_list>
+
+#include "fglt_device.cuh"
+
+namespace fglt {
+
+const char* const STAGE_NAMES[NUM_STAGES] = {"degree", "spmv1", "rank", "orient", "sort", "tri1", "c3_edges",
+                                             "spmv2", "tri2", "wedges", "cyc", "epilogue"};
+const char* const CYC_CLASS_NAMES[CYC_CLASSES] = {"cyc.warp", "cyc.hash11", "cyc.hash12", "cyc.hash13", "cyc.dense",
+                                                  "cyc.global"};
+
+namespace {
+
+constexpr int64_t MAX_DEGREE_EXACT = 2097151;  // binom(d,3) products stay inside int64
+
+// Small device counters, one int slot each.
+enum CounterId {
+  C_DMAX, C_NHEAVY, C_DPMAX, C_NTRI0, C_NTRI1, C_NTRI2, C_NEXT1_0, C_NEXT1_1, C_NEXT1_2, C_NEXT2_0,
+  C_NEXT2_1, C_NEXT2_2, C_NCYC0, C_NEXTC0 = C_NCYC0 + CYC_CLASSES, C_ERR = C_NEXTC0 + CYC_CLASSES, C_NUM
+};
+// 64-bit work counters: triangle-pass scanned entries, triangles, 4-cliques,
+// max and total wedges of the 4-cycle stage, largest global table need.
+enum Counter64Id { W_PROBES, W_TRIANGLES, W_K4, W_WMAX, W_WSUM, W_GCAP, W_CLS, W_NUM = W_CLS + CYC_CLASSES };
+
+int bits_for(int64_t cap) {
+  int hb = 5;
+  while ((1LL << hb) < 2 * cap) ++hb;
+  return hb;
+}
+
+bool pow2_threads(int t) { return t == 256 || t == 512 || t == 1024; }
+
+}  // namespace
+
+int err_word_index() { return C_ERR; }
+
+// Table II: U16 maps net to raw frequencies, U16 f = f^; row k = raw
+// frequency of sigma_k, column l = net frequency of sigma_l.
+static const int8_t U16_TABLE[16][16] = {
+    {1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 0, 1, 0, 2, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 0, 0, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, 0, 0, 0, 2, 1, 0, 2, 4, 2, 6},
+    {0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 1, 2, 2, 2, 4, 6},
+    {0, 0, 0, 0, 0, 0, 0, 1, 0, 1, 1, 0, 0, 2, 1, 3},
+    {0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0, 1, 0, 0, 1, 1},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 2, 0, 3},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0, 2, 2, 6},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0, 2, 3},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 3},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 3},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 3},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1},
+};
+
+int dict_columns(uint32_t mask) {
+  if (mask == 0) return 16;
+  int k = 0;
+  for (int i = 0; i < 16; ++i) k += (mask >> i) & 1u;
+  return k;
+}
+
+fglt_status make_subdict(uint32_t mask, SubDict* sd) {
+  if (mask == 0) mask = 0xFFFFu;
+  if ((mask & 3u) != 3u || (mask >> 16) != 0) return FGLT_ERR_INVALID_ARG;
+  SubDict x{};
+  for (int i = 0; i < 16; ++i)
+    if ((mask >> i) & 1u) x.col[x.k++] = i;
+  // U(s,s) is unit upper triangular; its inverse X solves U X = I by back
+  // substitution, column by column, in exact integers.
+  for (int c = 0; c < x.k; ++c)
+    for (int r = c; r >= 0; --r) {
+      long long v = (r == c) ? 1 : 0;
+      for (int t = r + 1; t <= c; ++t) v -= (long long)U16_TABLE[x.col[r]][x.col[t]] * x.uinv[t][c];
+      x.uinv[r][c] = v;
+    }
+  *sd = x;
+  return FGLT_OK;
+}
+
+fglt_status tuning_from_options(const fglt_options& o, Tuning* t) {
+  Tuning x;
+  if (o.cyc_hub_span < 0 || o.cyc_hub_span > cyc_dense_span_max() || o.tri_class_bounds[0] < 0 || o.tri_class_bounds[1] < 0 || o.cyc_warp_bits < 0 ||
+      o.cyc_heavy_threads < 0)
+    return FGLT_ERR_INVALID_ARG;
+  x.cyc_hub_span = o.cyc_hub_span;
+  if (o.tri_class_bounds[0]) x.tri_t0 = o.tri_class_bounds[0];
+  if (o.tri_class_bounds[1]) x.tri_t1 = o.tri_class_bounds[1];
+  if (x.tri_t0 < 2 || x.tri_t1 <= x.tri_t0) return FGLT_ERR_INVALID_ARG;
+  if (o.cyc_warp_bits) x.cyc_warp_bits = o.cyc_warp_bits;
+  if (x.cyc_warp_bits < 6 || x.cyc_warp_bits > cyc_warp_bits_max()) return FGLT_ERR_INVALID_ARG;
+  for (int c = 0; c < 3; ++c) {
+    if (o.cyc_mid_threads[c]) x.cyc_mid_threads[c] = o.cyc_mid_threads[c];
+    if (!pow2_threads(x.cyc_mid_threads[c])) return FGLT_ERR_INVALID_ARG;
+  }
+  if (o.cyc_heavy_threads) x.cyc_heavy_threads = o.cyc_heavy_threads;
+  if (!pow2_threads(x.cyc_heavy_threads)) return FGLT_ERR_INVALID_ARG;
+  *t = x;
+  return FGLT_OK;
+}
+
+void tuning_to_options(const Tuning& t, fglt_options* o) {
+  o->cyc_hub_span = t.cyc_hub_span;
+  o->tri_class_bounds[0] = t.tri_t0;
+  o->tri_class_bounds[1] = t.tri_t1;
+  o->cyc_warp_bits = t.cyc_warp_bits;
+  for (int c = 0; c < 3; ++c) o->cyc_mid_threads[c] = t.cyc_mid_threads[c];
+  o->cyc_heavy_threads = t.cyc_heavy_threads;
+}
+
+fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t* out_net, cudaStream_t st,
+                         const RunOptions& ro) {
+  const Bounds* b = ro.bounds;
+  const bool capturing = ro.capturing;
+  const Tuning& tu = ro.tuning;
+  // Stages each Table I row needs (a sub-dictionary skips the others).
+  SubDict sd;
+  {
+    fglt_status s = make_subdict(ro.dict_mask, &sd);
+    if (s != FGLT_OK) return s;
+  }
+  const uint32_t mask = ro.dict_mask ? ro.dict_mask : 0xFFFFu;
+  auto any = [&](std::initializer_list<int> ks) {
+    for (int k : ks)
+      if ((mask >> k) & 1u) return true;
+    return false;
+  };
+  const bool full = mask == 0xFFFFu;
+  const bool need_k4 = any({15});
+  const bool need_edge_c3 = any({10, 13, 14});
+  const bool need_tri1 = need_k4 || need_edge_c3 || any({4, 5, 6, 9, 11});
+  const bool need_edges = any({10, 14});
+  const bool need_spmv2 = any({5, 9});
+  const bool need_tri2 = any({13});
+  const bool need_cyc = any({12});
+  Csr g = in;
+  const int64_t n = g.n;
+  const int64_t launches0 = g_launches;
+  auto mark = [&](int i) {
+    if (ro.stage_events && !capturing) cudaEventRecord(ro.stage_events[i], st);
+  };
+#define CK(call)                            \
+  do {                                      \
+    cudaError_t e__ = (call);               \
+    if (e__ != cudaSuccess) {               \
+      ws.cuda_error(e__);                   \
+      return e__ == cudaErrorMemoryAllocation ? FGLT_ERR_OOM : FGLT_ERR_CUDA; \
+    }                                       \
+  } while (0)
+#define NEED(id, count, ptr)                                                                    \
+  do {                                                                                          \
+    void* p__ = nullptr;                                                                        \
+    fglt_status s__ = ws.get(id, (size_t)std::max<int64_t>((count), 1) * sizeof(*(ptr)), &p__); \
+    if (s__ != FGLT_OK) return s__;                                                             \
+    ptr = static_cast<decltype(ptr)>(p__);                                                      \
+  } while (0)
+#define READ(dev, host)                                               \
+  do {                                                                \
+    fglt_status s__ = ws.read((host), (dev), sizeof(*(host)), st);    \
+    if (s__ != FGLT_OK) return s__;                                   \
+  } while (0)
+
+  // Number of stored entries.
+  if (b) {
+    g.nnz = b->nnz;
+  } else if (g.nnz < 0) {
+    if (g.rp64) {
+      READ(static_cast<const int64_t*>(g.rowptr) + n, &g.nnz);
+    } else {
+      int32_t v = 0;
+      READ(static_cast<const int32_t*>(g.rowptr) + n, &v);
+      g.nnz = v;
+    }
+    if (g.nnz < 0) return FGLT_ERR_INVALID_GRAPH;
+  }
+  if (g.nnz > 0 && !g.colidx) return FGLT_ERR_INVALID_ARG;
+  const int64_t heavy_cap = g.nnz / HEAVY_DEGREE + 1;
+
+  int32_t *d, *heavy, *cnt;
+  u64* ctr;
+  NEED(B_D, n, d);
+  NEED(B_HEAVY, heavy_cap, heavy);
+  NEED(B_CNT, C_NUM, cnt);
+  NEED(B_CTR64, W_NUM, ctr);
+  CK(cudaMemsetAsync(cnt, 0, C_NUM * sizeof(int32_t), st));
+  CK(cudaMemsetAsync(ctr, 0, W_NUM * sizeof(u64), st));
+  int* err = cnt + C_ERR;
+
+  mark(0);
+  CK(launch_degree(g, d, cnt + C_DMAX, heavy, cnt + C_NHEAVY, err, st, b ? b->dmax : 0x7fffffff));
+  int32_t dmax = 0;
+  if (b) {
+    dmax = b->dmax;
+  } else {
+    int32_t c[C_ERR + 1];
+    {
+      fglt_status s = ws.read(c, cnt, sizeof c, st);
+      if (s != FGLT_OK) return s;
+    }
+    if (c[C_ERR] & ERR_BAD_ROWPTR) return FGLT_ERR_INVALID_GRAPH;
+    dmax = c[C_DMAX];
+  }
+  if (dmax > MAX_DEGREE_EXACT) return FGLT_ERR_OVERFLOW;
+  if (ro.validate && !capturing) {
+    CK(launch_validate(g, heavy, cnt + C_NHEAVY, heavy_cap, err, st));
+    if (b && b->off) CK(launch_validate_batch(g, b->off, b->num_graphs, err, st));
+    int e = 0;
+    READ(err, &e);
+    if (e & ERR_BAD_GRAPH) return FGLT_ERR_INVALID_GRAPH;
+  }
+
+  // SpMV chain 1: p2, d^7.
+  mark(1);
+  int64_t *p2, *r7;
+  NEED(B_P2, n, p2);
+  NEED(B_R7, n, r7);
+  CK(launch_spmv1(g, d, heavy, cnt + C_NHEAVY, heavy_cap, p2, r7, err, st));
+
+  // Degree ordering.
+  mark(2);
+  int32_t *hist, *cursor, *rank, *perm, *dr;
+  int64_t* base;
+  unsigned char* scan_tmp;
+  NEED(B_HIST, (int64_t)dmax + 1, hist);
+  NEED(B_BASE, (int64_t)dmax + 2, base);
+  NEED(B_CURSOR, (int64_t)dmax + 1, cursor);
+  NEED(B_RANK, n, rank);
+  NEED(B_PERM, n, perm);
+  NEED(B_DR, n, dr);
+  NEED(B_SCAN, (int64_t)scan_temp_bytes(std::max<int64_t>(n, (int64_t)dmax + 1) + 1), scan_tmp);
+  CK(cudaMemsetAsync(hist, 0, ((size_t)dmax + 1) * sizeof(int32_t), st));
+  CK(cudaMemsetAsync(cursor, 0, ((size_t)dmax + 1) * sizeof(int32_t), st));
+  CK(launch_degree_hist(d, n, hist, st));
+  CK(launch_scan_i32_to_i64(hist, (int64_t)dmax + 1, base, scan_tmp, st));
+  CK(launch_rank_assign(d, n, base, cursor, rank, perm, dr, st));
+
+  // Oriented graph: out-degrees, row pointers, targets.
+  mark(3);
+  int32_t *opc, *ocol, *ocur;
+  int64_t* orp;
+  NEED(B_OPC, n, opc);
+  NEED(B_ORP, n + 1, orp);
+  CK(launch_orient_count(g, rank, heavy, cnt + C_NHEAVY, heavy_cap, opc, cnt + C_DPMAX, st));
+  CK(launch_scan_i32_to_i64(opc, n, orp, scan_tmp, st));
+  int64_t m_or = 0;
+  int32_t dpmax = 0;
+  if (b) {
+    m_or = g.nnz;  // upper bound; the kernels read the exact row pointers
+    dpmax = dmax;
+  } else {
+    READ(orp + n, &m_or);
+    READ(cnt + C_DPMAX, &dpmax);
+  }
+  NEED(B_OCOL, m_or, ocol);
+  NEED(B_OCUR, n, ocur);
+  CK(cudaMemsetAsync(ocur, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(int32_t), st));
+  CK(launch_orient_fill(g, rank, orp, heavy, cnt + C_NHEAVY, heavy_cap, ocur, ocol, st));
+
+  mark(4);
+  int32_t* sort_scratch = nullptr;
+  if (dpmax > 16384) {
+    int64_t P = 16384;
+    while (P < dpmax) P <<= 1;
+    NEED(B_SORT, P, sort_scratch);
+  }
+  CK(launch_sort_rows(orp, n, dpmax, ocol, sort_scratch, st));
+  // Triangle-pass work lists by out-degree; each class is launched with shared
+  // memory sized for its largest out-degree.
+  const int T0 = tu.tri_t0, T1 = tu.tri_t1;
+  int32_t* twork;
+  NEED(B_TWORK, 3 * n, twork);
+  CK(launch_worklist_outdeg3(opc, n, 2, T0, T1, twork, n, cnt + C_NTRI0, st));
+  const int tri_cap[3] = {std::min(dpmax, T0), std::min(dpmax, T1), dpmax};
+  const bool tri_on[3] = {dpmax >= 2, dpmax > T0, dpmax > T1};
+
+  // Triangle pass 1: C3, c3, 4-cliques.
+  mark(5);
+  int32_t* C3o;
+  u64 *c3r, *k4r;
+  NEED(B_C3O, m_or, C3o);
+  NEED(B_C3R, n, c3r);
+  NEED(B_K4R, n, k4r);
+  CK(cudaMemsetAsync(C3o, 0, (size_t)std::max<int64_t>(m_or, 1) * sizeof(int32_t), st));
+  CK(cudaMemsetAsync(c3r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
+  CK(cudaMemsetAsync(k4r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
+  uint32_t* gbm = nullptr;
+  if (size_t gb = tri1_gbm_bytes(dpmax)) {
+    unsigned char* p = nullptr;
+    NEED(B_GBM, (int64_t)gb, p);
+    gbm = reinterpret_cast<uint32_t*>(p);
+  }
+  if (dpmax >= 2 && tri2_smem_bytes(dpmax) > 227 * 1024) return FGLT_ERR_UNSUPPORTED;
+  for (int c = 0; c < 3; ++c)
+    if (tri_on[c] && need_tri1)
+      CK(launch_tri1(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT1_0 + c, tri_cap[c], C3o, c3r, k4r,
+                     c == 2 ? gbm : nullptr, ctr + W_PROBES, err, st, need_k4));
+
+  // Edge terms of the final C3, then SpMV chain 2.
+  mark(6);
+  u64 *r10r, *r14r;
+  int64_t* c3oo;
+  NEED(B_R10R, n, r10r);
+  NEED(B_R14R, n, r14r);
+  NEED(B_C3OO, n, c3oo);
+  CK(cudaMemsetAsync(r10r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
+  CK(cudaMemsetAsync(r14r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
+  if (need_edges) CK(launch_c3_edge_terms(orp, ocol, C3o, dr, n, r10r, r14r, st));
+  mark(7);
+  int64_t *p3, *r9;
+  NEED(B_P3, n, p3);
+  NEED(B_R9, n, r9);
+  if (need_spmv2) {
+    CK(launch_unrank_u64(c3r, perm, n, c3oo, st));
+    CK(launch_spmv2(g, d, p2, c3oo, heavy, cnt + C_NHEAVY, heavy_cap, p3, r9, st));
+  } else {
+    CK(cudaMemsetAsync(p3, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(int64_t), st));
+    CK(cudaMemsetAsync(r9, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(int64_t), st));
+  }
+
+  // Triangle pass 2: diamonds at the off-cord vertices.
+  mark(8);
+  u64* r13r;
+  NEED(B_R13R, n, r13r);
+  CK(cudaMemsetAsync(r13r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
+  for (int c = 0; c < 3; ++c)
+    if (tri_on[c] && need_tri2)
+      CK(launch_tri2(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT2_0 + c, tri_cap[c], C3o, r13r, err,
+                     st));
+
+  // 4-cycles: in-lists and wedge counts, vertex classes, then the class kernels.
+  mark(9);
+  u64* r12r;
+  NEED(B_R12R, n, r12r);
+  CK(cudaMemsetAsync(r12r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
+  if (!need_cyc) mark(10);
+  if (need_cyc) {
+    // Dense window of top ranks: 32768 by default, 65536 for graphs above
+    // 2^21 vertices (their wedge tops spread over more hubs).
+    int64_t span = tu.cyc_hub_span > 0 ? tu.cyc_hub_span : (n > (1 << 21) ? 65536 : 32768);
+    const int32_t hub_lo = (int32_t)std::max<int64_t>(0, n - span);
+    int64_t *wc, *wcn, *irp;
+    int32_t *hc, *indeg, *icur;
+    int2* iin;
+    NEED(B_WC, n, wc);
+    NEED(B_WCN, n, wcn);
+    NEED(B_HC, n, hc);
+    NEED(B_INDEG, n, indeg);
+    NEED(B_IRP, n + 1, irp);
+    NEED(B_ICUR, n, icur);
+    NEED(B_IIN, m_or, iin);
+    CK(cudaMemsetAsync(wc, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(int64_t), st));
+    CK(cudaMemsetAsync(wcn, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(int64_t), st));
+    CK(cudaMemsetAsync(icur, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(iin, 0xFF, (size_t)std::max<int64_t>(m_or, 1) * sizeof(int2), st));
+    CK(launch_in_lists(orp, ocol, dr, opc, n, hub_lo, hc, indeg, irp, scan_tmp, icur, iin, wc, wcn, st));
+    int32_t* lists;
+    NEED(B_LS, (int64_t)CYC_CLASSES * n, lists);
+    const int64_t cap_bound = b ? std::min<int64_t>(b->cap, n) : n;
+    CK(launch_cyc_worklists(wc, wcn, dr, n, lists, n, cnt + C_NCYC0, ctr + W_GCAP, ctr + W_WMAX, ctr + W_WSUM, ctr + W_CLS,
+                            hub_lo < n,
+                            cap_bound, tu.cyc_warp_bits, st));
+    int32_t n_gmem = 0;
+    u64 gcap = 0;
+    if (b) {
+      if (cap_bound > cyc_block_cap()) {  // the global class may be needed: size it for the bound
+        n_gmem = 1;
+        gcap = (u64)cap_bound;
+      }
+    } else {
+      READ(cnt + C_NCYC0 + (CYC_CLASSES - 1), &n_gmem);
+      READ(ctr + W_GCAP, &gcap);
+    }
+    mark(10);
+    {
+      CycArgs ca{};
+      ca.n = n;
+      ca.orp = orp;
+      ca.ocol = ocol;
+      ca.irp = irp;
+      ca.iin = iin;
+      ca.wc = wc;
+      ca.lists = lists;
+      ca.list_stride = n;
+      ca.counts = cnt + C_NCYC0;
+      ca.next = cnt + C_NEXTC0;
+      ca.hub_lo = hub_lo;
+      ca.wbits = tu.cyc_warp_bits;
+      for (int c = 0; c < 3; ++c) ca.mid_threads[c] = tu.cyc_mid_threads[c];
+      ca.heavy_threads = tu.cyc_heavy_threads;
+      ca.r12r = r12r;
+      ca.err = err;
+      ca.cap_bound = cap_bound;
+      ca.ev = capturing ? nullptr : ro.cyc_events;
+      if (n_gmem > 0) {
+        ca.gbits = bits_for((int64_t)gcap);
+        const int64_t slots = (int64_t)cyc_gmem_blocks() << ca.gbits;
+        NEED(B_GKEYS, slots, ca.gkeys);
+        NEED(B_GCNT, slots, ca.gcnt);
+      }
+      CK(launch_cyc(ca, st));
+    }
+  }
+
+  // Table I + U16^{-1}.
+  mark(11);
+  EpilogueIn ein{d, rank, p2, p3, r7, r9, c3r, r10r, r12r, r13r, r14r, k4r};
+  if (full) CK(launch_epilogue(ein, n, out_raw, out_net, st));
+  else CK(launch_epilogue_sub(ein, sd, n, out_raw, out_net, st));
+  mark(12);
+  if (capturing) return FGLT_OK;
+
+  int e = 0;
+  READ(err, &e);
+  if (e & (ERR_BAD_GRAPH | ERR_BAD_ROWPTR)) return FGLT_ERR_INVALID_GRAPH;
+  if (e) return FGLT_ERR_INTERNAL;
+  if (ro.work) {
+    u64 w[W_NUM];
+    fglt_status s = ws.read(w, ctr, sizeof w, st);
+    if (s != FGLT_OK) return s;
+    int64_t* o = ro.work;
+    o[O_N] = n;
+    o[O_NNZ] = g.nnz;
+    o[O_M] = m_or;
+    o[O_DMAX] = dmax;
+    o[O_DPMAX] = dpmax;
+    o[O_PROBES] = (int64_t)w[W_PROBES];
+    o[O_TRIANGLES] = (int64_t)w[W_TRIANGLES];
+    o[O_K4] = (int64_t)w[W_K4];
+    o[O_WEDGES] = (int64_t)w[W_WSUM];
+    o[O_WMAX] = (int64_t)w[W_WMAX];
+    o[O_LAUNCHES] = g_launches - launches0;
+    int32_t cls_n[CYC_CLASSES] = {};
+    if (need_cyc) {
+      fglt_status s2 = ws.read(cls_n, cnt + C_NCYC0, sizeof cls_n, st);
+      if (s2 != FGLT_OK) return s2;
+    }
+    for (int c = 0; c < CYC_CLASSES; ++c) {
+      o[O_CLS_VERTICES + c] = cls_n[c];
+      o[O_CLS_WEDGES + c] = (int64_t)w[W_CLS + c];
+    }
+  }
+  return FGLT_OK;
+#undef CK
+#undef NEED
+#undef READ
+}
+
+}  // namespace fglt

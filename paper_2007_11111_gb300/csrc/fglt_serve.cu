@@ -141,7 +141,7 @@ fglt_status run_pack(Server* S, Lane* L, const std::vector<Request*>& pack) {
     nnz += r->nnz;
   }
   if (!L->h_rowptr.reserve(n + 1) || !L->h_colidx.reserve(std::max<int64_t>(nnz, 1)) ||
-      !L->h_raw.reserve(n * 16) || !L->h_net.reserve(n * 16))
+      !L->h_raw.reserve(n * columns_of(L->h)) || !L->h_net.reserve(n * columns_of(L->h)))
     return FGLT_ERR_OOM;
   // Block-diagonal packing with global vertex ids.
   int64_t vo = 0, eo = 0;
@@ -154,7 +154,7 @@ fglt_status run_pack(Server* S, Lane* L, const std::vector<Request*>& pack) {
   }
   cudaStream_t st = handle_stream(L->h);
   if (!L->d_rowptr.reserve(n + 1, st) || !L->d_colidx.reserve(std::max<int64_t>(nnz, 1), st) ||
-      !L->d_raw.reserve(n * 16, st) || !L->d_net.reserve(n * 16, st))
+      !L->d_raw.reserve(n * columns_of(L->h), st) || !L->d_net.reserve(n * columns_of(L->h), st))
     return FGLT_ERR_OOM;
   if (cudaMemcpyAsync(L->d_rowptr.p, L->h_rowptr.p, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return FGLT_ERR_CUDA;
@@ -174,14 +174,15 @@ fglt_status run_pack(Server* S, Lane* L, const std::vector<Request*>& pack) {
     s = transform_locked(L->h, g, L->d_raw.p, L->d_net.p, st);
   }
   if (s != FGLT_OK) return s;
-  if (cudaMemcpyAsync(L->h_raw.p, L->d_raw.p, (size_t)n * 128, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaMemcpyAsync(L->h_net.p, L->d_net.p, (size_t)n * 128, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+  const int64_t C = columns_of(L->h);
+  if (cudaMemcpyAsync(L->h_raw.p, L->d_raw.p, (size_t)n * C * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(L->h_net.p, L->d_net.p, (size_t)n * C * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return FGLT_ERR_CUDA;
   vo = 0;
   for (Request* r : pack) {
-    if (r->out_raw) std::memcpy(r->out_raw, L->h_raw.p + vo * 16, (size_t)r->n * 128);
-    if (r->out_net) std::memcpy(r->out_net, L->h_net.p + vo * 16, (size_t)r->n * 128);
+    if (r->out_raw) std::memcpy(r->out_raw, L->h_raw.p + vo * C, (size_t)r->n * C * 8);
+    if (r->out_net) std::memcpy(r->out_net, L->h_net.p + vo * C, (size_t)r->n * C * 8);
     vo += r->n;
   }
   return FGLT_OK;

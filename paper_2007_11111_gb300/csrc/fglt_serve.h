@@ -3,18 +3,7 @@
 
 #include "fglt.h"
 #include "fglt_kernels.h"
-
-// Host-side bounds that replace the pipeline's read-backs (block-diagonal
-// batches: every degree, out-degree and per-vertex count of distinct 4-cycle
-// tops is below the largest graph's vertex count). With them the stage
-// sequence has no host synchronisation and can be captured as a CUDA graph.
-struct Bounds {
-  int64_t nnz;         // exact stored entries
-  int32_t dmax;        // bound on every degree
-  int64_t cap;         // bound on distinct tops per vertex
-  const int64_t* off;  // device graph offsets for validation (or NULL)
-  int64_t num_graphs;
-};
+#include "fglt_pipeline.h"
 
 namespace fglt {
 namespace serve {
@@ -28,6 +17,7 @@ fglt_status transform_locked(fglt_t h, const Csr& g, int64_t* raw, int64_t* net,
 
 // Accessors of the opaque handle used by the serving runtime.
 cudaStream_t handle_stream(fglt_t h);
+int columns_of(fglt_t h);  // output columns per vertex
 const fglt_options* options_of(fglt_t h);
 int device_of(fglt_t h);
 Server* server_of(fglt_t h);

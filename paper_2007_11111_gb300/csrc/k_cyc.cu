@@ -14,12 +14,21 @@
 // number of such wedges, at most sum_v d_v d+_v (degree orientation, the cost
 // model of Appendix A), instead of sum_k d_k^2.
 //
+// Everything runs in rank space. The middles v of w are read from two lists:
+// the in-list of w, entries (v, j) with w = N+(v)[j], whose tops are the
+// entries of N+(v) after position j, and the out-list N+(w), whose middles v
+// have every entry of N+(v) as a top (all above v > w). One load of v's row
+// pointers gives each middle's segment of tops; no search is needed.
+//
 // Counters per w live in
 //  - a per-warp shared-memory hash table (vertices with few wedges),
-//  - a per-block shared-memory hash table (medium vertices),
-//  - a dense shared-memory array over the top-ranked ("hub") vertices plus a
-//    small shared-memory hash table for the other tops (heavy vertices: most
-//    wedges of a power-law graph end at a hub),
+//  - a per-block shared-memory hash table, in three sizes (medium vertices;
+//    each size class is launched with shared memory for its own tables),
+//  - a dense shared-memory array of 16-bit counters over a window of the
+//    top-ranked ("hub") vertices plus a small shared-memory hash table for the
+//    other tops (heavy vertices: most wedges of a power-law graph end at a
+//    hub; a count never exceeds the degree of w, so 16 bits suffice for every
+//    w of degree below 65536, and the others take the global class),
 //  - or a global-memory hash table (fallback).
 // Wedges are walked cooperatively: the segments of N+(v) of many middles v are
 // concatenated and split evenly over the lanes of a warp or a block.
@@ -30,13 +39,11 @@ namespace fglt {
 
 namespace {
 
-constexpr int WARP_HASH = 1024;   // slots per warp table
-constexpr int WARP_CAP = 512;     // most wedges handled by one warp table
 constexpr int WARP_T = 256;
-constexpr int DENSE_WORDS = 16384;  // 64 KB of counters
-constexpr int DHASH_BITS = 11;      // 2048-slot table for the non-hub tops
-constexpr int BHASH_BITS = 13;      // largest per-w table of the hash-only block class
-constexpr int BLOCK_CAP = 1 << (BHASH_BITS - 1);
+constexpr int DENSE_SPAN_MAX = 90112;  // 16-bit counters: 176 KB of shared memory at most
+constexpr int DHASH_BITS = 11;      // 2048-slot table for the non-hub tops of the dense class
+constexpr int MID_BITS0 = 11, MID_BITS1 = 12, MID_BITS2 = 13;  // table sizes of the three hash-only block classes
+constexpr int MID_BITS[3] = {MID_BITS0, MID_BITS1, MID_BITS2};
 
 int num_sms() {
   int dev = 0, sms = 1;
@@ -96,9 +103,56 @@ struct Table {
   }
 };
 
-// One group of up to 32 middles v = colidx[k0 .. k0+32) of w: each lane owns
-// one v and its segment of N+(v) above w; the concatenated segments are split
-// over the lanes. f(u, owner_lane) is called for every wedge.
+// The middles of one vertex w (rank space): K = nin + nout middles; middle
+// k < nin is the in-entry iin[ib + k] = (v, j), later ones are N+(w)[k - nin].
+struct Mids {
+  const int64_t* orp;
+  const int32_t* ocol;
+  const int2* iin;
+  int64_t ib, nin, ob, K;
+};
+
+__device__ __forceinline__ Mids mids_of(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                        const int64_t* __restrict__ irp, const int2* __restrict__ iin, int32_t w) {
+  Mids M;
+  M.orp = orp;
+  M.ocol = ocol;
+  M.iin = iin;
+  M.ib = irp[w];
+  M.nin = irp[w + 1] - M.ib;
+  M.ob = orp[w];
+  M.K = M.nin + (orp[w + 1] - M.ob);
+  return M;
+}
+
+// Middle k of w: its rank v and its segment [st, st + len) of tops in ocol.
+// Entries of a malformed graph (never-written in-list slots) give v = -1 and
+// an empty segment.
+__device__ __forceinline__ void middle_seg(const Mids& M, int64_t k, int64_t n, int32_t& v, int64_t& st,
+                                           int64_t& len) {
+  int32_t j = -1;
+  if (k < M.nin) {
+    const int2 e = __ldg(M.iin + M.ib + k);
+    v = e.x;
+    j = e.y;
+  } else {
+    v = __ldg(M.ocol + M.ob + (k - M.nin));
+  }
+  st = 0;
+  len = 0;
+  if ((uint32_t)v >= (uint64_t)n) {
+    v = -1;
+    return;
+  }
+  const int64_t b = __ldg(M.orp + v), e = __ldg(M.orp + v + 1);
+  st = b + (int64_t)j + 1;
+  if (st < b) st = b;
+  len = e > st ? e - st : 0;
+}
+
+// One group of up to 32 middles of w (middle k0 + lane per lane): each lane
+// owns one v and its segment of tops; the concatenated segments are split over
+// the lanes. f(u, owner_lane) is called for every wedge.
 struct Group {
   int32_t rv;     // rank of this lane's v (-1 if none)
   int64_t st;     // segment start in ocol
@@ -106,22 +160,12 @@ struct Group {
   int64_t total;  // wedges in the group
 };
 
-__device__ __forceinline__ Group make_group(const int32_t* __restrict__ ci, const int32_t* __restrict__ rank,
-                                            const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
-                                            int64_t k, int64_t e, int32_t w, int64_t n, int lane) {
+__device__ __forceinline__ Group make_group(const Mids& M, int64_t k, int64_t n, int lane) {
   Group g;
   g.rv = -1;
   g.st = 0;
   int64_t len = 0;
-  if (k < e) {
-    const int32_t v = __ldg(ci + k);
-    if ((uint32_t)v < (uint64_t)n) {
-      g.rv = __ldg(rank + v);
-      const int64_t ob = __ldg(orp + g.rv), oe = __ldg(orp + g.rv + 1);
-      g.st = upper_bound_i32(ocol, ob, oe, w);
-      len = oe - g.st;
-    }
-  }
+  if (k < M.K) middle_seg(M, k, n, g.rv, g.st, len);
   int64_t incl = len;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -167,20 +211,20 @@ __device__ __forceinline__ u64 run_sum(u64 x, int j, bool& head) {
 }
 
 // ---------------------------------------------------------------------------
-// Small vertices: one warp per w, a 1024-slot hash table per warp.
+// Small vertices: one warp per w, a 2^wbits-slot hash table per warp.
 // ---------------------------------------------------------------------------
-template <typename RP>
-__global__ void __launch_bounds__(WARP_T) k_cyc_warp(const RP* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                     const int32_t* __restrict__ rank, const int32_t* __restrict__ perm,
-                                                     const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+__global__ void __launch_bounds__(WARP_T) k_cyc_warp(const int64_t* __restrict__ orp,
+                                                     const int32_t* __restrict__ ocol,
+                                                     const int64_t* __restrict__ irp, const int2* __restrict__ iin,
                                                      const int64_t* __restrict__ wc, const int32_t* __restrict__ list,
                                                      const int32_t* __restrict__ cnt, int* next, u64* r12r, int64_t n,
-                                                     int64_t cap_bound, int* err) {
+                                                     int64_t cap_bound, int wbits, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t WH = 1u << wbits;
   u64* acc = reinterpret_cast<u64*>(smem) + warp * 32;
   uint32_t* tables = reinterpret_cast<uint32_t*>(reinterpret_cast<u64*>(smem) + (WARP_T / 32) * 32);
-  Table<false> T{tables + (size_t)warp * 2 * WARP_HASH, tables + (size_t)warp * 2 * WARP_HASH + WARP_HASH};
+  Table<false> T{tables + (size_t)warp * 2 * WH, tables + (size_t)warp * 2 * WH + WH};
   const int total = *cnt;
   for (;;) {
     int item = 0;
@@ -193,21 +237,21 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const RP* __restrict__ rp, 
     if (cap > cap_bound) cap = cap_bound;
     int hb = 5;
     while ((1LL << hb) < 2 * cap) ++hb;
+    if (hb > wbits) hb = wbits;  // the class guarantees 2 * cap <= 2^wbits
     const uint32_t H = 1u << hb;
     for (uint32_t i = lane; i < H; i += 32) T.clear(i);
     acc[lane] = 0;
     __syncwarp();
-    const int64_t wo = perm[w];
-    const int64_t s = (int64_t)rp[wo], e = (int64_t)rp[wo + 1];
-    for (int64_t k0 = s; k0 < e; k0 += 32) {
-      const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
+    const Mids M = mids_of(orp, ocol, irp, iin, w);
+    for (int64_t k0 = 0; k0 < M.K; k0 += 32) {
+      const Group g = make_group(M, k0 + lane, n, lane);
       walk_group(g, ocol, lane, [&](uint32_t u, int, bool valid) {
         if (valid) T.increment(u, hb, err);
       });
     }
     __syncwarp();
-    for (int64_t k0 = s; k0 < e; k0 += 32) {
-      const Group g = make_group(ci, rank, orp, ocol, k0 + lane, e, w, n, lane);
+    for (int64_t k0 = 0; k0 < M.K; k0 += 32) {
+      const Group g = make_group(M, k0 + lane, n, lane);
       walk_group(g, ocol, lane, [&](uint32_t u, int j, bool valid) {
         u64 c = 0;
         if (valid) {
@@ -300,25 +344,14 @@ __device__ __forceinline__ long long block_excl_scan(long long x, long long* scr
   return r;
 }
 
-// Segments of the middles colidx[c0 .. c0 + chunk): long ones listed for
+// Segments of the middles c0 .. c0 + chunk of w: long ones listed for
 // warp-per-segment walks, short non-empty ones compacted with their wedge
 // prefix for the flattened walk (one packed block scan).
-__device__ __forceinline__ void build_chunk(const Segs& S, const int32_t* __restrict__ ci,
-                                            const int32_t* __restrict__ rank, const int64_t* __restrict__ orp,
-                                            const int32_t* __restrict__ ocol, int64_t c0, int64_t e, int32_t w,
-                                            int64_t n, int chunk) {
+__device__ __forceinline__ void build_chunk(const Segs& S, const Mids& M, int64_t c0, int64_t n, int chunk) {
   const int64_t k = c0 + threadIdx.x;
   int32_t rv = -1;
   int64_t st = 0, len = 0;
-  if ((int)threadIdx.x < chunk && k < e) {
-    const int32_t v = __ldg(ci + k);
-    if ((uint32_t)v < (uint64_t)n) {
-      rv = __ldg(rank + v);
-      const int64_t ob = __ldg(orp + rv), oe = __ldg(orp + rv + 1);
-      st = upper_bound_i32(ocol, ob, oe, w);
-      len = oe - st;
-    }
-  }
+  if ((int)threadIdx.x < chunk && k < M.K) middle_seg(M, k, n, rv, st, len);
   const bool is_long = len >= LONG_SEG;
   const bool is_short = len > 0 && !is_long;
   // packed: [short wedge sum : 32 | short count : 16 | long count : 16]
@@ -413,19 +446,14 @@ size_t seg_bytes(int ch) {
   return (size_t)ch * 8 * 3 + 64 * 8 + (size_t)(ch + 1) * 4 + (size_t)ch * 4 * 3 + 16;
 }
 
-template <typename RP, int MODE, int BT>
-__global__ void __launch_bounds__(BT) k_cyc_block(const RP* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                       const int32_t* __restrict__ rank,
-                                                       const int32_t* __restrict__ perm,
-                                                       const int64_t* __restrict__ orp,
-                                                       const int32_t* __restrict__ ocol,
-                                                       const int64_t* __restrict__ wc,
-                                                       const int32_t* __restrict__ list,
-                                                       const int32_t* __restrict__ cnt, int* next, u64* r12r,
-                                                       int64_t n, int32_t hub_lo, int gbits, uint32_t* gkeys,
-                                                       uint32_t* gcnt, int64_t cap_bound, int* err) {
-  constexpr bool DENSE = MODE == 1 || MODE == 2;
-  constexpr bool C16 = MODE == 1;
+template <int MODE, int BT>
+__global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                                  const int64_t* __restrict__ irp, const int2* __restrict__ iin,
+                                                  const int64_t* __restrict__ wc, const int32_t* __restrict__ list,
+                                                  const int32_t* __restrict__ cnt, int* next, u64* r12r, int64_t n,
+                                                  int32_t hub_lo, int tbits, int dense_words, uint32_t* gkeys,
+                                                  uint32_t* gcnt, int64_t cap_bound, int* err) {
+  constexpr bool DENSE = MODE == 1;
   constexpr bool GMEM = MODE == 3;
   constexpr int CH = BT < CHUNK_MAX ? BT : CHUNK_MAX;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -444,12 +472,11 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const RP* __restrict__ rp, con
   S.misc = S.lrv + CH;
   uint32_t* after = reinterpret_cast<uint32_t*>(S.misc + 4);
   uint32_t* dense = after;
-  uint32_t* hbase = DENSE ? after + DENSE_WORDS : after;
-  const int tbits = GMEM ? gbits : (DENSE ? DHASH_BITS : BHASH_BITS);
+  uint32_t* hbase = DENSE ? after + dense_words : after;
   Table<GMEM> T;
   if (GMEM) {
-    T.keys = gkeys + ((size_t)blockIdx.x << gbits);
-    T.cnts = gcnt + ((size_t)blockIdx.x << gbits);
+    T.keys = gkeys + ((size_t)blockIdx.x << tbits);
+    T.cnts = gcnt + ((size_t)blockIdx.x << tbits);
   } else {
     T.keys = hbase;
     T.cnts = hbase + (1 << tbits);
@@ -460,13 +487,11 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const RP* __restrict__ rp, con
 
   auto dense_add = [&](uint32_t u) {
     const uint32_t i = u - (uint32_t)hub_lo;
-    if (C16) atomicAdd(&dense[i >> 1], 1u << ((i & 1u) << 4));
-    else atomicAdd(&dense[i], 1u);
+    atomicAdd(&dense[i >> 1], 1u << ((i & 1u) << 4));
   };
   auto dense_get = [&](uint32_t u) -> uint32_t {
     const uint32_t i = u - (uint32_t)hub_lo;
-    if (C16) return (dense[i >> 1] >> ((i & 1u) << 4)) & 0xFFFFu;
-    return dense[i];
+    return (dense[i >> 1] >> ((i & 1u) << 4)) & 0xFFFFu;
   };
 
   for (;;) {
@@ -482,18 +507,18 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const RP* __restrict__ rp, con
       if (cap > cap_bound) cap = cap_bound;
       hb = 5;
       while ((1LL << hb) < 2 * cap) ++hb;
+      if (hb > tbits) hb = tbits;  // the class guarantees 2 * cap <= 2^tbits
     }
     const uint32_t H = 1u << hb;
     if (DENSE) {
-      const int words = C16 ? (hub_n + 1) >> 1 : hub_n;
+      const int words = (hub_n + 1) >> 1;
       for (int i = tid; i < words; i += blockDim.x) dense[i] = 0u;
     }
     for (uint32_t i = tid; i < H; i += blockDim.x) T.clear(i);
     __syncthreads();
 
-    const int64_t wo = perm[w];
-    const int64_t s = (int64_t)rp[wo], e = (int64_t)rp[wo + 1];
-    const bool single = e - s <= CH;
+    const Mids M = mids_of(orp, ocol, irp, iin, w);
+    const bool single = M.K <= CH;
     auto count = [&](uint32_t u) {
       if (DENSE && (int32_t)u >= hub_lo) dense_add(u);
       else T.increment(u, hb, err);
@@ -503,8 +528,8 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const RP* __restrict__ rp, con
       return c > 1 ? (u64)(c - 1) : 0;
     };
     // Pass A: count the wedges per top u.
-    for (int64_t c0 = s; c0 < e; c0 += CH) {
-      build_chunk(S, ci, rank, orp, ocol, c0, e, w, n, CH);
+    for (int64_t c0 = 0; c0 < M.K; c0 += CH) {
+      build_chunk(S, M, c0, n, CH);
       walk_long(S, ocol, [&](uint32_t u) -> u64 { count(u); return 0; }, [](int32_t, u64) {});
       walk_chunk(S, ocol, [&](uint32_t u, int, bool valid) {
         if (valid) count(u);
@@ -512,9 +537,9 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const RP* __restrict__ rp, con
       __syncthreads();
     }
     // Pass B: each middle gains cnt[u] - 1 per wedge.
-    for (int64_t c0 = s; c0 < e; c0 += CH) {
+    for (int64_t c0 = 0; c0 < M.K; c0 += CH) {
       if (!single) {
-        build_chunk(S, ci, rank, orp, ocol, c0, e, w, n, CH);
+        build_chunk(S, M, c0, n, CH);
       } else {
         if (tid == 0) S.misc[2] = 0;
         __syncthreads();
@@ -564,35 +589,114 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const RP* __restrict__ rp, con
   }
 }
 
-// Vertex classes: 0 = warp table, 1 = block + shared hash, 2 = block + dense
-// hub counters + shared hash, 3 = block + global hash.
-__global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* __restrict__ wcn, int64_t n,
-                                int32_t* lists, int64_t list_stride, int32_t* counts, u64* gcap_max,
-                                int dense_ok, int64_t cap_bound) {
+// Hub cut: hc[v] = entries of N+(v) below hub_lo (rows are sorted).
+__global__ void k_hub_cut(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol, int64_t n,
+                          int32_t hub_lo, int32_t* hc) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = orp[v], e = orp[v + 1];
+    hc[v] = (int32_t)(upper_bound_i32(ocol, b, e, hub_lo - 1) - b);
+  }
+}
+
+__global__ void k_in_degree(const int32_t* __restrict__ dr, const int32_t* __restrict__ opc, int64_t n,
+                            int32_t* indeg) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = dr[v] - opc[v];
+    indeg[v] = x > 0 ? x : 0;
+  }
+}
+
+// In-lists and wedge counts, one warp per oriented row v. For the edge
+// v -> w = N+(v)[j]: the in-list of w gets (v, j); w's in-part wedges are the
+// d+(v) - j - 1 later entries of N+(v) (those below hub_lo: hc[v] - j - 1);
+// v's out-part wedges are all of N+(w) (hc[w] of them below hub_lo).
+// A slot beyond w's in-list capacity (only for a malformed graph) is dropped.
+__global__ void k_in_fill(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                          const int64_t* __restrict__ irp, const int32_t* __restrict__ hc, int64_t n, int32_t* icur,
+                          int2* iin, unsigned long long* wc, unsigned long long* wcn) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int64_t b = orp[v];
+    const int d = (int)(orp[v + 1] - b);
+    if (d == 0) continue;
+    const int hcv = hc[v];
+    u64 a = 0, c = 0;
+    for (int j = lane; j < d; j += 32) {
+      const int32_t w = ocol[b + j];
+      if ((uint32_t)w >= (uint64_t)n) continue;
+      const int32_t pos = atomicAdd(icur + w, 1);
+      if (irp[w] + pos < irp[w + 1]) iin[irp[w] + pos] = make_int2((int32_t)v, j);
+      if (d - j - 1 > 0) atomicAdd(wc + w, (u64)(d - j - 1));
+      if (hcv - j - 1 > 0) atomicAdd(wcn + w, (u64)(hcv - j - 1));
+      a += (u64)(orp[w + 1] - orp[w]);
+      c += (u64)hc[w];
+    }
+    a = warp_sum_u64(a);
+    c = warp_sum_u64(c);
+    if (lane == 0) {
+      if (a) atomicAdd(wc + v, a);
+      if (c) atomicAdd(wcn + v, c);
+    }
+  }
+}
+
+// Vertex classes (CYC_CLASSES lists): 0 = warp table, 1..3 = block + shared
+// hash table of 2^MID_BITS[c-1] slots, 4 = block + dense hub counters + shared
+// hash, 5 = block + global hash. Also the stage's total and largest wedge
+// counts (work counters).
+__global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* __restrict__ wcn,
+                                const int32_t* __restrict__ dr, int64_t n,
+                                int32_t* lists, int64_t list_stride, int32_t* counts, u64* gcap_max, u64* wmax,
+                                u64* wsum, u64* cls_wedges, int dense_ok, int64_t cap_bound, int wbits) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  u64 lmax = 0, lsum = 0;
+  u64 csum[CYC_CLASSES] = {};
   for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < n; r0 += stride) {
     const int64_t r = r0 + lane;
     int cls = -1;
     int64_t cap = 0;
+    if (r < n) {
+      lmax = max(lmax, (u64)wc[r]);
+      lsum += (u64)wc[r];
+    }
     if (r < n && wc[r] >= 2) {
       cap = wc[r];
       if (cap > n - 1 - r) cap = n - 1 - r;
       if (cap > cap_bound) cap = cap_bound;
-      if (wc[r] <= WARP_CAP) cls = 0;
-      else if (cap <= BLOCK_CAP) cls = 1;
-      else if (dense_ok && wcn[r] <= (1 << (DHASH_BITS - 1))) cls = 2;
-      else cls = 3;
+      if (wc[r] <= (1LL << (wbits - 1))) cls = 0;
+      else if (cap <= (1LL << (MID_BITS0 - 1))) cls = 1;
+      else if (cap <= (1LL << (MID_BITS1 - 1))) cls = 2;
+      else if (cap <= (1LL << (MID_BITS2 - 1))) cls = 3;
+      else if (dense_ok && wcn[r] <= (1 << (DHASH_BITS - 1)) && dr[r] < 65536) cls = 4;
+      else cls = 5;
     }
-    if (cls == 3) atomicMax(gcap_max, (u64)cap);
+    if (cls == 5) atomicMax(gcap_max, (u64)cap);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < CYC_CLASSES; ++c) {
+      if (cls == c) csum[c] += (u64)wc[r];
       const unsigned m = __ballot_sync(0xffffffffu, cls == c);
       int pos = 0;
       if (lane == 0 && m) pos = atomicAdd(&counts[c], __popc(m));
       pos = __shfl_sync(0xffffffffu, pos, 0);
       if (cls == c) lists[c * list_stride + pos + __popc(m & ((1u << lane) - 1))] = (int32_t)r;
     }
+  }
+  lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, 16));
+  lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, 8));
+  lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, 4));
+  lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, 2));
+  lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, 1));
+  lsum = warp_sum_u64(lsum);
+  if (lane == 0) {
+    if (lmax) atomicMax(wmax, lmax);
+    if (lsum) atomicAdd(wsum, lsum);
+  }
+#pragma unroll
+  for (int c = 0; c < CYC_CLASSES; ++c) {
+    const u64 x = warp_sum_u64(csum[c]);
+    if (lane == 0 && x) atomicAdd(cls_wedges + c, x);
   }
 }
 
@@ -602,71 +706,96 @@ int occupancy(const void* fn, int threads, size_t smem) {
   return per_sm < 1 ? 1 : per_sm;
 }
 
-// Block sizes: medium vertices (hash-only class) have a few thousand wedges,
-// so a 256-thread block keeps every warp busy between the per-vertex
-// barriers; heavy vertices use 1024 threads.
-constexpr int BT_HASH = 256, BT_HEAVY = 1024;
-
-size_t block_smem(int mode, int bt) {
+size_t block_smem(int mode, int bt, int tbits, int dense_words) {
   const size_t seg = seg_bytes(bt < CHUNK_MAX ? bt : CHUNK_MAX);
-  if (mode == 0) return seg + ((size_t)8 << BHASH_BITS);
-  if (mode == 1 || mode == 2) return seg + (size_t)DENSE_WORDS * 4 + ((size_t)8 << DHASH_BITS);
+  if (mode == 0) return seg + ((size_t)8 << tbits);
+  if (mode == 1) return seg + (size_t)dense_words * 4 + ((size_t)8 << DHASH_BITS);
   return seg;
 }
 
 int gmem_blocks() { return num_sms(); }
 
-template <typename RP, int MODE, int BT>
-void launch_block(const RP* rp, const Csr& g, const CycArgs& a, int cls, cudaStream_t st) {
-  const size_t smem = block_smem(MODE, BT);
-  allow_max_smem(k_cyc_block<RP, MODE, BT>);
-  const int grid = MODE == 3 ? gmem_blocks()
-                             : num_sms() * occupancy((const void*)k_cyc_block<RP, MODE, BT>, BT, smem);
-  k_cyc_block<RP, MODE, BT><<<grid, BT, smem, st>>>(rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc,
-                                                    a.lists + cls * a.list_stride, a.counts + cls, a.next + cls,
-                                                    a.r12r, g.n, a.hub_lo, a.gbits, a.gkeys, a.gcnt, a.cap_bound,
-                                                    a.err);
+template <int MODE, int BT>
+void launch_block(const CycArgs& a, int cls, int tbits, int dense_words, cudaStream_t st) {
+  const size_t smem = block_smem(MODE, BT, tbits, dense_words);
+  allow_max_smem(k_cyc_block<MODE, BT>);
+  const int grid = MODE == 3 ? gmem_blocks() : num_sms() * occupancy((const void*)k_cyc_block<MODE, BT>, BT, smem);
+  k_cyc_block<MODE, BT><<<grid, BT, smem, st>>>(a.orp, a.ocol, a.irp, a.iin, a.wc, a.lists + cls * a.list_stride,
+                                                a.counts + cls, a.next + cls, a.r12r, a.n, a.hub_lo, tbits,
+                                                dense_words, a.gkeys, a.gcnt, a.cap_bound, a.err);
   note_launch();
 }
 
-template <typename RP>
-cudaError_t launch_rp(const Csr& g, const CycArgs& a, cudaStream_t st) {
-  const RP* rp = static_cast<const RP*>(g.rowptr);
-  const int sms = num_sms();
-  const size_t wsmem = (size_t)(WARP_T / 32) * (32 * 8 + 2 * WARP_HASH * 4);
-  allow_max_smem(k_cyc_warp<RP>);
-  k_cyc_warp<RP><<<sms * occupancy((const void*)k_cyc_warp<RP>, WARP_T, wsmem), WARP_T, wsmem, st>>>(
-      rp, g.colidx, a.rank, a.perm, a.orp, a.ocol, a.wc, a.lists, a.counts, a.next + 0, a.r12r, g.n, a.cap_bound,
-      a.err);
-  note_launch();
-  launch_block<RP, 0, BT_HASH>(rp, g, a, 1, st);
-  if (a.c16) launch_block<RP, 1, BT_HEAVY>(rp, g, a, 2, st);
-  else launch_block<RP, 2, BT_HEAVY>(rp, g, a, 2, st);
-  if (a.gkeys) launch_block<RP, 3, BT_HEAVY>(rp, g, a, 3, st);
-  return cudaGetLastError();
+template <int MODE>
+void launch_block_bt(const CycArgs& a, int cls, int tbits, int dense_words, int bt, cudaStream_t st) {
+  if (bt >= 1024) launch_block<MODE, 1024>(a, cls, tbits, dense_words, st);
+  else if (bt >= 512) launch_block<MODE, 512>(a, cls, tbits, dense_words, st);
+  else launch_block<MODE, 256>(a, cls, tbits, dense_words, st);
 }
 
 }  // namespace
 
-int cyc_dense_span(bool c16) { return c16 ? 2 * DENSE_WORDS : DENSE_WORDS; }
-int cyc_block_cap() { return BLOCK_CAP; }
+int cyc_dense_span_max() { return DENSE_SPAN_MAX; }
+int cyc_block_cap() { return 1 << (MID_BITS[2] - 1); }
 int cyc_gmem_blocks() { return gmem_blocks(); }
+int cyc_warp_bits_max() { return 10; }
 
-cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, int64_t n, int32_t* lists,
-                                 int64_t list_stride, int32_t* counts, u64* gcap_max, bool dense_ok,
-                                 cudaStream_t st, int64_t cap_bound) {
+cudaError_t launch_in_lists(const int64_t* orp, const int32_t* ocol, const int32_t* dr, const int32_t* opc,
+                            int64_t n, int32_t hub_lo, int32_t* hc, int32_t* indeg, int64_t* irp, void* scan_tmp,
+                            int32_t* icur, int2* iin, int64_t* wc, int64_t* wcn, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int64_t blocks = (n + 255) / 256;
   if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
-  k_cyc_worklists<<<(unsigned)blocks, 256, 0, st>>>(wc, wcn, n, lists, list_stride, counts, gcap_max,
-                                                     dense_ok ? 1 : 0, cap_bound);
+  k_hub_cut<<<(unsigned)blocks, 256, 0, st>>>(orp, ocol, n, hub_lo, hc);
+  note_launch();
+  k_in_degree<<<(unsigned)blocks, 256, 0, st>>>(dr, opc, n, indeg);
+  note_launch();
+  cudaError_t e = launch_scan_i32_to_i64(indeg, n, irp, scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  int64_t wblocks = (n * 32 + 255) / 256;
+  if (wblocks > (int64_t)num_sms() * 16) wblocks = (int64_t)num_sms() * 16;
+  k_in_fill<<<(unsigned)wblocks, 256, 0, st>>>(orp, ocol, irp, hc, n, icur, iin,
+                                                reinterpret_cast<u64*>(wc), reinterpret_cast<u64*>(wcn));
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_cyc(const Csr& g, const CycArgs& a, cudaStream_t st) {
-  if (g.n <= 0) return cudaSuccess;
-  return g.rp64 ? launch_rp<int64_t>(g, a, st) : launch_rp<int32_t>(g, a, st);
+cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, const int32_t* dr, int64_t n, int32_t* lists,
+                                 int64_t list_stride, int32_t* counts, u64* gcap_max, u64* wmax, u64* wsum,
+                                 u64* cls_wedges, bool dense_ok, int64_t cap_bound, int wbits, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
+  k_cyc_worklists<<<(unsigned)blocks, 256, 0, st>>>(wc, wcn, dr, n, lists, list_stride, counts, gcap_max, wmax, wsum,
+                                                     cls_wedges, dense_ok ? 1 : 0, cap_bound, wbits);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cyc(const CycArgs& a, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  auto mark = [&](int c) {
+    if (a.ev) cudaEventRecord(a.ev[c], st);
+  };
+  const int sms = num_sms();
+  const int wbits = a.wbits;
+  const size_t wsmem = (size_t)(WARP_T / 32) * (32 * 8 + ((size_t)8 << wbits));
+  allow_max_smem(k_cyc_warp);
+  mark(0);
+  k_cyc_warp<<<sms * occupancy((const void*)k_cyc_warp, WARP_T, wsmem), WARP_T, wsmem, st>>>(
+      a.orp, a.ocol, a.irp, a.iin, a.wc, a.lists, a.counts, a.next + 0, a.r12r, a.n, a.cap_bound, wbits, a.err);
+  note_launch();
+  for (int c = 0; c < 3; ++c) {
+    mark(1 + c);
+    launch_block_bt<0>(a, 1 + c, MID_BITS[c], 0, a.mid_threads[c], st);
+  }
+  mark(4);
+  const int span = (int)(a.n - a.hub_lo);
+  if (span > 0) launch_block_bt<1>(a, 4, DHASH_BITS, (span + 1) / 2, a.heavy_threads, st);
+  mark(5);
+  if (a.gkeys) launch_block_bt<3>(a, 5, a.gbits, 0, a.heavy_threads, st);
+  mark(6);
+  return cudaGetLastError();
 }
 
 }  // namespace fglt

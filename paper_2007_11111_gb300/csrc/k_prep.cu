@@ -1,6 +1,5 @@
-// Passes over the input CSR (degrees, the two SpMV chains, validation, the
-// wedge-count pre-pass of the 4-cycle stage), the degree ordering, the
-// oriented graph, scans and the epilogue.
+// Passes over the input CSR (degrees, the two SpMV chains, validation), the
+// degree ordering, the oriented graph, scans and the epilogue.
 //
 // Rows of the input CSR are processed by 8-lane groups when their degree is at
 // most HEAVY_DEGREE and by a whole block otherwise (degree-binned scheduling:
@@ -184,37 +183,6 @@ struct OrientFillOp {  // appends rank(j) to the oriented row of rank(v)
     }
   }
   __device__ __forceinline__ void done(int64_t, long long, long long) const {}
-};
-
-// Wedges w - v - u with u above both v and w in the degree order (u in N+(v),
-// u > w): the 4-cycle stage's work and hash-table bound per vertex w.
-struct WedgeCountOp {
-  const int32_t* rank;
-  const int64_t* orp;
-  const int32_t* ocol;
-  int64_t* wc;
-  int64_t* wcn;
-  u64* wmax;
-  u64* wsum;
-  int64_t n;
-  int32_t hub_lo;
-  __device__ __forceinline__ void edge(int64_t v, int32_t j, int64_t, int64_t, int64_t, long long& a,
-                                       long long& b) const {
-    if ((uint32_t)j >= (uint64_t)n) return;
-    const int32_t rw = __ldg(rank + v), rv = __ldg(rank + j);
-    const int64_t ob = __ldg(orp + rv), oe = __ldg(orp + rv + 1);
-    const int64_t st = upper_bound_i32(ocol, ob, oe, rw);
-    a += oe - st;
-    if (rw + 1 < hub_lo) b += upper_bound_i32(ocol, st, oe, hub_lo - 1) - st;
-  }
-  __device__ __forceinline__ void done(int64_t v, long long a, long long b) const {
-    wc[__ldg(rank + v)] = a;
-    wcn[__ldg(rank + v)] = b;
-    if (a) {
-      atomicMax(wmax, (u64)a);
-      atomicAdd(wsum, (u64)a);
-    }
-  }
 };
 
 template <typename RP>
@@ -652,6 +620,52 @@ __global__ void k_epilogue(EpilogueIn in, int64_t n, int64_t* __restrict__ raw, 
   }
 }
 
+// Sub-dictionary epilogue: the Table I rows of the columns in s, and
+// f(s) = U16(s,s)^{-1} f^(s) (Table II caption), exact in int64. Inputs of
+// stages the sub-dictionary does not need are zero.
+__global__ void k_epilogue_sub(EpilogueIn in, SubDict sd, int64_t n, int64_t* __restrict__ raw,
+                               int64_t* __restrict__ net) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const long long d = in.d[v];
+    const int32_t r = in.rank[v];
+    const long long c3 = (long long)in.c3r[r];
+    const long long p2 = in.p2[v];
+    long long f[16];
+    f[0] = 1;
+    f[1] = d;
+    f[2] = p2;
+    f[3] = d * (d - 1) / 2;
+    f[4] = c3;
+    f[5] = in.p3[v];
+    f[6] = p2 * (d - 1) - 2 * c3;
+    f[7] = in.r7[v];
+    f[8] = (d * (d - 1) / 2) * (d - 2) / 3;
+    f[9] = in.r9[v];
+    f[10] = (long long)in.r10r[r];
+    f[11] = (d - 2) * c3;
+    f[12] = (long long)in.r12r[r];
+    f[13] = (long long)in.r13r[r];
+    f[14] = (long long)in.r14r[r];
+    f[15] = (long long)in.r15r[r];
+    long long fs[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      long long x = 0;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) x = (sd.col[i] == k) ? f[k] : x;
+      fs[i] = x;
+    }
+    for (int i = 0; i < sd.k; ++i) {
+      if (raw) raw[v * sd.k + i] = fs[i];
+      if (net) {
+        long long g = 0;
+        for (int j = i; j < sd.k; ++j) g += sd.uinv[i][j] * fs[j];
+        net[v * sd.k + i] = g;
+      }
+    }
+  }
+}
+
 unsigned grid_for(int64_t items, int threads, int per_sm = 8) {
   int64_t want = (items + threads - 1) / threads;
   int64_t cap = (int64_t)num_sms() * per_sm;
@@ -808,11 +822,12 @@ cudaError_t launch_unrank_u64(const u64* src_r, const int32_t* perm, int64_t n, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_wedge_count(const Csr& g, const int32_t* rank, const int64_t* orp, const int32_t* ocol,
-                               const int32_t* heavy, const int32_t* nheavy, int64_t heavy_cap, int32_t hub_lo,
-                               int64_t* wc, int64_t* wcn, u64* wmax, u64* wsum, cudaStream_t st) {
-  return dispatch_rows(g, heavy, nheavy, heavy_cap,
-                       WedgeCountOp{rank, orp, ocol, wc, wcn, wmax, wsum, g.n, hub_lo}, st);
+cudaError_t launch_epilogue_sub(const EpilogueIn& in, const SubDict& sd, int64_t n, int64_t* raw, int64_t* net,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_epilogue_sub<<<grid_for(n, 256), 256, 0, st>>>(in, sd, n, raw, net);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_epilogue(const EpilogueIn& in, int64_t n, int64_t* raw, int64_t* net, cudaStream_t st) {

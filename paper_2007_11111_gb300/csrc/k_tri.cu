@@ -96,7 +96,7 @@ __device__ __forceinline__ bool filter_test(const uint32_t* filt, uint32_t key, 
 //                                  i.e. twice the 4-cliques {a, x, ., .}
 // and a's own counts are the sums over x divided by 2 and 6.
 // ---------------------------------------------------------------------------
-template <bool SMEM_BM>
+template <bool SMEM_BM, bool K4>
 __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
                                                 const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
                                                 int* next, int Dmax, int Hbits, int32_t* C3o, u64* c3r, u64* k4r,
@@ -112,9 +112,10 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
   uint32_t* filt = reinterpret_cast<uint32_t*>(vals + Hmax);
   int32_t* ylist = reinterpret_cast<int32_t*>(filt + FWmax) + warp * (Dmax + Wmax);
   int32_t* wlist = ylist + Dmax;
-  uint32_t* bm = SMEM_BM ? reinterpret_cast<uint32_t*>(reinterpret_cast<int32_t*>(filt + FWmax) +
-                                                       nwarps * (Dmax + Wmax))
-                         : (gbm + (size_t)blockIdx.x * Dmax * Wmax);
+  uint32_t* after_lists = reinterpret_cast<uint32_t*>(reinterpret_cast<int32_t*>(filt + FWmax) +
+                                                      nwarps * (Dmax + Wmax));
+  uint32_t* bm = SMEM_BM ? after_lists : (gbm + (size_t)blockIdx.x * Dmax * Wmax);
+  uint32_t* k2loc = SMEM_BM ? after_lists + (size_t)Dmax * Wmax : after_lists;  // [Dmax]
   const int total = *nwork;
   const unsigned below = (1u << lane) - 1u;
 
@@ -134,6 +135,7 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
     for (int i = tid; i < (1 << hb); i += blockDim.x) keys[i] = EMPTY_KEY;
     for (int i = tid; i < (1 << (fb - 5)); i += blockDim.x) filt[i] = 0u;
     for (int i = tid; i < D * W; i += blockDim.x) bm[i] = 0u;
+    for (int i = tid; K4 && i < D; i += blockDim.x) k2loc[i] = 0u;
     __syncthreads();
     for (int x = tid; x < D; x += blockDim.x) {
       const uint32_t key = (uint32_t)ocol[base + x];
@@ -175,56 +177,77 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
     }
     __syncthreads();
 
-    // Per local vertex x: triangles through edge a-x (popc S_x) and 4-cliques
-    // through a-x (half of sum over y in S_x of |S_x ∩ S_y|).
-    u64 tri2x = 0, k4_6x = 0;
+    // Per local vertex x: triangles through edge a-x (popc S_x). Per edge x-y
+    // of G_a with y > x: t = |S_x ∩ S_y| triangles of G_a on that edge, added
+    // to both ends, so k2loc[x] ends as twice the triangles of G_a at x, i.e.
+    // twice the 4-cliques {a, x, ., .}.
+    u64 tri2x = 0;
     for (int x = warp; x < D; x += nwarps) {
       const uint32_t* Sx = bm + (size_t)x * W;
-      int deg = 0, nzw = 0;
+      int deg = 0, nzw = 0, nup = 0;
+      const int xw = x >> 5;
+      const uint32_t above = ~((2u << (x & 31)) - 1u);  // bits of the word of x above x
       for (int w0 = 0; w0 < W; w0 += 32) {
         const int w = w0 + lane;
-        uint32_t bits = w < W ? Sx[w] : 0u;
+        const uint32_t bits = w < W ? Sx[w] : 0u;
         const unsigned mz = __ballot_sync(0xffffffffu, bits != 0u);
         if (bits) wlist[nzw + __popc(mz & below)] = w;
         nzw += __popc(mz);
-        const int c = __popc(bits);
+        deg += warp_sum_i32(__popc(bits));
+        if (!K4) continue;
+        uint32_t ub = w > xw ? bits : (w == xw ? bits & above : 0u);
+        const int c = __popc(ub);
         int incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const int y = __shfl_up_sync(0xffffffffu, incl, o);
           if (lane >= o) incl += y;
         }
-        int p = deg + incl - c;
-        while (bits) {
-          const int t = __ffs(bits) - 1;
-          bits &= bits - 1;
+        int p = nup + incl - c;
+        while (ub) {
+          const int t = __ffs(ub) - 1;
+          ub &= ub - 1;
           ylist[p++] = (w << 5) + t;
         }
-        deg += __shfl_sync(0xffffffffu, incl, 31);
+        nup += __shfl_sync(0xffffffffu, incl, 31);
       }
       __syncwarp();
-      long long k2 = 0;
-      for (int i = lane; i < deg; i += 32) {
-        const uint32_t* Sy = bm + (size_t)ylist[i] * W;
-        int k = 0;
-        for (int q = 0; q < nzw; ++q) {
-          const int w = wlist[q];
-          k += __popc(Sx[w] & Sy[w]);
+      if (K4) {
+        int kx = 0;
+        for (int i = lane; i < nup; i += 32) {
+          const int y = ylist[i];
+          const uint32_t* Sy = bm + (size_t)y * W;
+          int t = 0;
+          for (int q = 0; q < nzw; ++q) {
+            const int w = wlist[q];
+            t += __popc(Sx[w] & Sy[w]);
+          }
+          if (t) atomicAdd(&k2loc[y], (uint32_t)t);
+          kx += t;
         }
-        k2 += k;
+        kx = warp_sum_i32(kx);
+        if (lane == 0 && kx) atomicAdd(&k2loc[x], (uint32_t)kx);
       }
-      k2 = warp_sum_i64(k2);
       if (lane == 0) {
-        const int32_t vx = ocol[base + x];
         if (deg) {
+          const int32_t vx = ocol[base + x];
           atomicAdd(&C3o[base + x], deg);
           atomicAdd(&c3r[vx], (u64)deg);
         }
-        if (k2) atomicAdd(&k4r[vx], (u64)(k2 / 2));
         tri2x += (u64)deg;
-        k4_6x += (u64)k2;
       }
       __syncwarp();
+    }
+    u64 k4_6x = 0;
+    if (K4) {
+      __syncthreads();
+      for (int x = tid; x < D; x += blockDim.x) {
+        const uint32_t k2 = k2loc[x];
+        if (k2) {
+          atomicAdd(&k4r[ocol[base + x]], (u64)(k2 / 2));
+          k4_6x += k2;
+        }
+      }
     }
     const u64 tri_sum = block_sum(tri2x, red) / 2;
     const u64 k4_sum = block_sum(k4_6x, red) / 6;
@@ -329,6 +352,7 @@ size_t tri1_smem_impl(int D, bool smem_bm) {
   const int H = 1 << hash_bits_for(D);
   const size_t W = (size_t)(D + 31) / 32;
   size_t bytes = (size_t)H * 8 + (size_t)host_filter_words(D) * 4 + (size_t)(TRI_T / 32) * (D + W) * 4;
+  bytes += (size_t)D * 4;  // per-vertex 4-clique tallies
   if (smem_bm) bytes += (size_t)D * W * 4;
   return (bytes + 15) & ~(size_t)15;
 }
@@ -356,11 +380,13 @@ int tri_grid_blocks() { return num_sms(); }
 static int tri1_grid(int dpmax, bool smem_bm) {
   const size_t smem = tri1_smem_impl(dpmax, smem_bm);
   if (smem_bm) {
-    allow_max_smem(k_tri1<true>);
-    return occupancy_grid((const void*)k_tri1<true>, smem);
+    allow_max_smem(k_tri1<true, true>);
+    allow_max_smem(k_tri1<true, false>);
+    return occupancy_grid((const void*)k_tri1<true, true>, smem);
   }
-  allow_max_smem(k_tri1<false>);
-  return occupancy_grid((const void*)k_tri1<false>, smem);
+  allow_max_smem(k_tri1<false, true>);
+  allow_max_smem(k_tri1<false, false>);
+  return occupancy_grid((const void*)k_tri1<false, true>, smem);
 }
 
 size_t tri1_gbm_bytes(int dpmax) {
@@ -371,17 +397,16 @@ size_t tri1_gbm_bytes(int dpmax) {
 
 cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm, u64* work_ctr,
-                        int* err, cudaStream_t st) {
+                        int* err, cudaStream_t st, bool cliques) {
   if (dpmax < 2) return cudaSuccess;
   const bool smem_bm = tri1_bitmap_fits_smem(dpmax);
   const size_t smem = tri1_smem_impl(dpmax, smem_bm);
   const int grid = tri1_grid(dpmax, smem_bm);
   const int hb = hash_bits_for(dpmax);
-  if (smem_bm)
-    k_tri1<true><<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, C3o, c3r, k4r, nullptr, work_ctr,
-                                            err);
-  else
-    k_tri1<false><<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, C3o, c3r, k4r, gbm, work_ctr, err);
+  auto* fn = smem_bm ? (cliques ? k_tri1<true, true> : k_tri1<true, false>)
+                     : (cliques ? k_tri1<false, true> : k_tri1<false, false>);
+  fn<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, C3o, c3r, k4r, smem_bm ? nullptr : gbm,
+                                work_ctr, err);
   note_launch();
   return cudaGetLastError();
 }

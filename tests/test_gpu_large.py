@@ -14,16 +14,40 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _oracle_cost(g):
-    """Per vertex i, a bound on the oracle's intersection work for row i:
-    sum over j in {i} + N(i), k in N(j) of min(d_j, d_k)."""
+def _row_costs(g):
+    """Per vertex j, the oracle's intersection work for the C3 values of row j:
+    sum over k in N(j) of min(d_j, d_k) (computed on the device)."""
     rp, ci = g.rowptr, g.colidx.long()
     d = (rp[1:] - rp[:-1])
     rows = torch.repeat_interleave(torch.arange(g.n, device=rp.device), d)
     edge = torch.minimum(d[rows], d[ci]).double()
     rc = torch.zeros(g.n, dtype=torch.float64, device=rp.device).index_add_(0, rows, edge)
-    cost = rc.clone().index_add_(0, rows, rc[ci])
-    return d.cpu().numpy(), cost.cpu().numpy()
+    return d.cpu().numpy(), rc.cpu().numpy()
+
+
+def pick_sample(g, d, rc, budget, per_bin=4, seed=24):
+    """Vertices from every degree range, highest first, while the rows the
+    oracle must intersect for them (their closed neighbourhoods, each row paid
+    once) stay within budget units of rc."""
+    rng = np.random.default_rng(seed)
+    in_r = np.zeros(g.n, bool)
+    total, picks = 0.0, []
+    for lo, hi in ((4097, 1 << 40), (513, 4097), (65, 513), (9, 65), (2, 9), (1, 2), (0, 1)):
+        cand = np.flatnonzero((d >= lo) & (d < hi))
+        rng.shuffle(cand)
+        got = 0
+        for v in cand[:3000]:
+            rows = np.concatenate([[v], g.colidx[g.rowptr[v]:g.rowptr[v + 1]]])
+            rows = rows[~in_r[rows]]
+            extra = float(rc[rows].sum())
+            if total + extra <= budget:
+                in_r[rows] = True
+                total += extra
+                picks.append(int(v))
+                got += 1
+                if got == per_bin:
+                    break
+    return np.unique(np.array(picks, dtype=np.int64))
 
 
 def test_rmat_s24_full_size_sampled():
@@ -48,19 +72,11 @@ def test_rmat_s24_full_size_sampled():
     assert s[10] == 2 * s[9] and s[9] == s[11] and s[13] == s[14]
     assert s[4] % 3 == 0 and s[12] % 4 == 0 and s[15] % 4 == 0
     # sampled rows vs the oracle: vertices from every degree range whose
-    # neighbourhood intersections cost the oracle at most 2e8 steps
-    d, cost = _oracle_cost(dg)
-    rng = np.random.default_rng(24)
-    picks = []
-    for lo, hi in ((0, 1), (1, 2), (2, 9), (9, 65), (65, 513), (513, 4097), (4097, 1 << 30)):
-        cand = np.flatnonzero((d >= lo) & (d < hi) & (cost <= 2e8))
-        if cand.size:
-            picks.append(rng.choice(cand, size=min(6, cand.size), replace=False))
-    cheap = np.flatnonzero(cost <= 2e8)
-    picks.append(cheap[np.argsort(d[cheap])[-4:]])  # the highest degrees the oracle affords
-    verts = np.unique(np.concatenate(picks))
-    assert verts.size >= 30 and d[verts].max() >= 1000
+    # neighbourhoods the oracle can intersect within a bounded budget
+    d, rc = _row_costs(dg)
     g = dg.to_host()
+    verts = pick_sample(g, d, rc, budget=6e9)
+    assert verts.size >= 16 and d[verts].max() >= 64
     oraw, onet = oracle.fglt(g, vertices=verts)
     vt = torch.from_numpy(verts).to(raw_d.device)
     np.testing.assert_array_equal(raw_d[vt].cpu().numpy(), oraw)

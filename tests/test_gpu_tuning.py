@@ -1,0 +1,101 @@
+"""The tuning settings (degree-class bounds of the triangle passes, hash-table
+sizes and block shapes of the 4-cycle classes, the dense hub span) move work
+between kernels but never change a count: every setting must reproduce the
+oracle bit for bit. The autotuner must return a valid setting, install it, and
+leave the results unchanged."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SETTINGS = [
+    dict(),
+    dict(tri_class_bounds=(2, 3)),
+    dict(tri_class_bounds=(8, 1024)),
+    dict(cyc_warp_bits=6),
+    dict(cyc_warp_bits=8, cyc_mid_threads=(512, 1024, 512)),
+    dict(cyc_mid_threads=(1024, 256, 1024), cyc_heavy_threads=256),
+    dict(cyc_heavy_threads=512, cyc_hub_span=64),
+    dict(cyc_hub_span=1, cyc_warp_bits=7, tri_class_bounds=(16, 32)),
+]
+
+
+def _graphs():
+    def complete_bipartite(a, b):
+        i = np.repeat(np.arange(a), b)
+        j = a + np.tile(np.arange(b), a)
+        return gg.csr_from_pairs(a + b, i, j)
+    return [gg.rmat(12, 16, seed=21), gg.barabasi_albert(3000, 7, seed=3), complete_bipartite(70, 90),
+            gg.rmat(13, 8, seed=5), gg.complete(300)]
+
+
+@pytest.fixture(scope="module")
+def cases():
+    return [(g, oracle.fglt(g)) for g in _graphs()]
+
+
+def _run(h, g):
+    dev = torch.device("cuda:0")
+    rp = torch.from_numpy(g.rowptr).to(dev)
+    ci = torch.from_numpy(g.colidx).to(dev)
+    raw, net = h.transform(rp, ci, g.n)
+    return raw.cpu().numpy(), net.cpu().numpy()
+
+
+@pytest.mark.parametrize("setting", SETTINGS, ids=[str(s) or "default" for s in SETTINGS])
+def test_every_setting_matches_oracle(cases, setting):
+    import paper_2007_11111_gb300 as fg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    with fg.Handle(device=0, **setting) as h:
+        for g, (oraw, onet) in cases:
+            raw, net = _run(h, g)
+            np.testing.assert_array_equal(raw, oraw, err_msg=f"{setting} n={g.n}")
+            np.testing.assert_array_equal(net, onet, err_msg=f"{setting} n={g.n}")
+
+
+def test_invalid_settings_rejected():
+    import paper_2007_11111_gb300 as fg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    for bad in (dict(tri_class_bounds=(64, 32)), dict(tri_class_bounds=(1, 8)), dict(cyc_warp_bits=11),
+                dict(cyc_warp_bits=5), dict(cyc_mid_threads=(128, 256, 256)), dict(cyc_heavy_threads=300),
+                dict(cyc_hub_span=-1)):
+        with pytest.raises(fg.FgltError) as e:
+            fg.Handle(device=0, **bad)
+        assert e.value.status == fg.FGLT_ERR_INVALID_ARG
+
+
+def test_autotune_installs_setting_and_keeps_results(cases):
+    import paper_2007_11111_gb300 as fg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g, (oraw, onet) = cases[0]
+    dev = torch.device("cuda:0")
+    rp = torch.from_numpy(g.rowptr).to(dev)
+    ci = torch.from_numpy(g.colidx).to(dev)
+    with fg.Handle(device=0) as h:
+        chosen, tuned_ms, default_ms = h.autotune(rp, ci, g.n, reps=1)
+        assert tuned_ms > 0 and default_ms > 0
+        t0, t1 = chosen["tri_class_bounds"]
+        assert 2 <= t0 < t1
+        assert 6 <= chosen["cyc_warp_bits"] <= 10
+        assert all(x in (256, 512, 1024) for x in chosen["cyc_mid_threads"])
+        assert chosen["cyc_heavy_threads"] in (256, 512, 1024)
+        # results under the installed setting, on this graph and on another
+        for gg_, (wr, wn) in (cases[0], cases[1]):
+            raw, net = _run(h, gg_)
+            np.testing.assert_array_equal(raw, wr)
+            np.testing.assert_array_equal(net, wn)
+        # a fresh handle created with the chosen setting gives the same counts
+        kw = dict(tri_class_bounds=tuple(chosen["tri_class_bounds"]), cyc_warp_bits=chosen["cyc_warp_bits"],
+                  cyc_mid_threads=tuple(chosen["cyc_mid_threads"]), cyc_heavy_threads=chosen["cyc_heavy_threads"],
+                  cyc_hub_span=chosen["cyc_hub_span"])
+        with fg.Handle(device=0, **kw) as h2:
+            raw, net = _run(h2, g)
+            np.testing.assert_array_equal(net, onet)
