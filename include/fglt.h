@@ -91,6 +91,11 @@ typedef struct {
      *   with shared memory sized for its largest d+ (default 64, 256;
      *   2 <= t0 < t1). */
     int tri_class_bounds[2];
+    /* tri_probe_loads: list entries each lane of the triangle passes keeps in
+     *   flight per scan step, 2 or 4 (default 2): more hides more memory
+     *   latency, at the cost of scanning up to 32 * loads entries past the end
+     *   of a scan. */
+    int tri_probe_loads;
     /* cyc_warp_bits: log2 of the per-warp hash-table slots of the 4-cycle
      *   stage's warp class, which takes vertices with at most 2^(bits-1)
      *   wedges (6..10, default 10). */
@@ -219,9 +224,9 @@ fglt_status fglt_csr_from_edges(fglt_t handle, const int32_t* src, const int32_t
  * fglt_options.profile_stages = 1. names[i] points to static strings.
  * *count receives the number of entries (at most max_stages are written):
  * the stages in order (degree, spmv1, rank, orient, sort, tri1, c3_edges,
- * spmv2, tri2, wedges, cyc, epilogue), then the six 4-cycle vertex classes
- * inside "cyc" (cyc.warp, cyc.hash11, cyc.hash12, cyc.hash13, cyc.dense,
- * cyc.global; 0 when the stage did not run). */
+ * spmv2, tri2, wedges, cyc, epilogue), then the seven 4-cycle vertex
+ * classes inside "cyc" (cyc.warp, cyc.hash11, cyc.hash12, cyc.hash13,
+ * cyc.dense, cyc.dense_spill, cyc.global; 0 when the stage did not run). */
 fglt_status fglt_stage_times(fglt_t handle, const char** names, float* ms,
                              int max_stages, int* count);
 
@@ -240,9 +245,9 @@ fglt_status fglt_stage_times(fglt_t handle, const char** names, float* ms,
  *   8 wedges enumerated by the 4-cycle stage
  *   9 largest wedge count of one vertex
  *  10 kernel launches the transform issued (memsets not included)
- *  11..16 vertices in each 4-cycle vertex class (the order of the cyc.*
+ *  11..17 vertices in each 4-cycle vertex class (the order of the cyc.*
  *         entries of fglt_stage_times)
- *  17..22 wedges of the vertices in each class
+ *  18..24 wedges of the vertices in each class
  * FGLT_ERR_NOT_FOUND if no transform has completed on the handle. */
 fglt_status fglt_work_counters(fglt_t handle, int64_t* counters, int max_counters, int* count);
 

@@ -349,7 +349,7 @@ int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i
 #pragma omp atomic write
             failed = 1;
         } else {
-#pragma omp for schedule(dynamic, 16)
+#pragma omp for schedule(dynamic, 1)
             for (i64 r = 0; r < rows; r++) {
                 i64 i = verts ? verts[r] : r;
                 i64 d = p1[i];

@@ -63,6 +63,7 @@ class fglt_options(ctypes.Structure):
         ("profile_stages", ctypes.c_int),
         ("cyc_hub_span", ctypes.c_int),
         ("tri_class_bounds", ctypes.c_int * 2),
+        ("tri_probe_loads", ctypes.c_int),
         ("cyc_warp_bits", ctypes.c_int),
         ("cyc_mid_threads", ctypes.c_int * 3),
         ("cyc_heavy_threads", ctypes.c_int),
@@ -72,6 +73,7 @@ class fglt_options(ctypes.Structure):
     def tuning(self) -> dict:
         """The tuning fields (0 = default)."""
         return {"cyc_hub_span": self.cyc_hub_span, "tri_class_bounds": list(self.tri_class_bounds),
+                "tri_probe_loads": self.tri_probe_loads,
                 "cyc_warp_bits": self.cyc_warp_bits, "cyc_mid_threads": list(self.cyc_mid_threads),
                 "cyc_heavy_threads": self.cyc_heavy_threads}
 
@@ -264,7 +266,7 @@ def fglt_stage_times(h) -> dict:
     return {names[i].decode(): float(ms[i]) for i in range(min(cnt.value, 32))}
 
 
-CYC_CLASSES = ["warp", "hash11", "hash12", "hash13", "dense", "global"]
+CYC_CLASSES = ["warp", "hash11", "hash12", "hash13", "dense", "dense_spill", "global"]
 WORK_COUNTER_NAMES = (["n", "nnz", "m", "max_degree", "max_out_degree", "tri_scanned", "triangles",
                        "k4", "wedges", "max_wedges", "launches"] + [f"cls_vertices.{c}" for c in CYC_CLASSES]
                       + [f"cls_wedges.{c}" for c in CYC_CLASSES])
@@ -316,7 +318,8 @@ class Handle:
     def __init__(self, device: int = 0, validate: bool = False, profile_stages: bool = False,
                  serve_memory_budget: int = 0, serve_max_batch: int = 0, serve_max_queue: int = 0,
                  cyc_hub_span: int = 0, tri_class_bounds=(0, 0), cyc_warp_bits: int = 0,
-                 cyc_mid_threads=(0, 0, 0), cyc_heavy_threads: int = 0, dictionary: int = 0):
+                 cyc_mid_threads=(0, 0, 0), cyc_heavy_threads: int = 0, dictionary: int = 0,
+                 tri_probe_loads: int = 0):
         """dictionary: sub-dictionary bit mask (0 = Sigma16; DICT_SIGMA5 = Sigma5)."""
         opt = fglt_options_default()
         opt.dictionary_mask = int(dictionary)
@@ -327,6 +330,7 @@ class Handle:
         for i, x in enumerate(cyc_mid_threads):
             opt.cyc_mid_threads[i] = int(x)
         opt.cyc_heavy_threads = int(cyc_heavy_threads)
+        opt.tri_probe_loads = int(tri_probe_loads)
         opt.validate = int(validate)
         opt.profile_stages = int(profile_stages)
         opt.serve_memory_budget = int(serve_memory_budget)

@@ -228,7 +228,8 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
     if ((s = time_once(h, g, st, start, 1, &base)) != FGLT_OK) return s;  // warm-up (sizes the workspace)
     if ((s = time_once(h, g, st, start, reps, &base)) != FGLT_OK) return s;
     // Candidate values per parameter, tried one parameter at a time.
-    const int t_bounds[][2] = {{32, 128}, {64, 256}, {128, 512}, {32, 256}, {64, 1024}};
+    const int t_bounds[][3] = {{32, 128, 2}, {64, 256, 4}, {128, 512, 2}, {32, 256, 4}, {64, 1024, 2},
+                               {64, 256, 2}};
     const int wbits[] = {8, 9, 10};
     const int spans[] = {0, 16384, 32768, 65536, 90112};
     const int threads[] = {256, 512, 1024};
@@ -237,7 +238,8 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
       Tuning t = best;
       t.tri_t0 = tb[0];
       t.tri_t1 = tb[1];
-      if (t.tri_t0 != start.tri_t0 || t.tri_t1 != start.tri_t1) tri_c.push_back(t);
+      t.tri_loads = tb[2];
+      if (t.tri_t0 != start.tri_t0 || t.tri_t1 != start.tri_t1 || t.tri_loads != start.tri_loads) tri_c.push_back(t);
     }
     TuneScore cur = base;
     // The 4-cycle parameters interact through the class split: search them in
@@ -252,6 +254,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
         if (with_tri) {
           run.tri_t0 = tri_c.back().tri_t0;
           run.tri_t1 = tri_c.back().tri_t1;
+          run.tri_loads = tri_c.back().tri_loads;
         }
         TuneScore sc;
         fglt_status e = time_once(h, g, st, run, reps, &sc);
@@ -260,15 +263,17 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
           if (sc.tri < cur.tri) {
             best.tri_t0 = run.tri_t0;
             best.tri_t1 = run.tri_t1;
+            best.tri_loads = run.tri_loads;
             cur.tri = sc.tri;
           }
           tri_c.pop_back();
         }
         if (sc.cyc < cur.cyc) {
-          const int t0 = best.tri_t0, t1 = best.tri_t1;
+          const int t0 = best.tri_t0, t1 = best.tri_t1, tl = best.tri_loads;
           best = t;
           best.tri_t0 = t0;
           best.tri_t1 = t1;
+          best.tri_loads = tl;
           cur.cyc = sc.cyc;
         }
       }
@@ -291,12 +296,14 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
       Tuning run = best;
       run.tri_t0 = tri_c.back().tri_t0;
       run.tri_t1 = tri_c.back().tri_t1;
+      run.tri_loads = tri_c.back().tri_loads;
       tri_c.pop_back();
       TuneScore sc;
       if ((s = time_once(h, g, st, run, reps, &sc)) != FGLT_OK) return s;
       if (sc.tri < cur.tri) {
         best.tri_t0 = run.tri_t0;
         best.tri_t1 = run.tri_t1;
+        best.tri_loads = run.tri_loads;
         cur.tri = sc.tri;
       }
     }

@@ -62,10 +62,10 @@ cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int32
 // Vertices (rank labels) with at least `min_out` out-neighbours.
 cudaError_t launch_worklist_outdeg(const int32_t* opc, int64_t n, int min_out, int32_t* list,
                                    int32_t* count, cudaStream_t st);
-// The same split into three lists by out-degree: [min_out, t0], (t0, t1],
-// (t1, ...) at lists + c * stride, sizes in counts[0..2].
-cudaError_t launch_worklist_outdeg3(const int32_t* opc, int64_t n, int min_out, int t0, int t1, int32_t* lists,
-                                    int64_t stride, int32_t* counts, cudaStream_t st);
+// The same split into four lists by out-degree: [min_out, t0], (t0, t1],
+// (t1, t2], (t2, ...) at lists + c * stride, sizes in counts[0..3].
+cudaError_t launch_worklist_outdeg4(const int32_t* opc, int64_t n, int min_out, int t0, int t1, int t2,
+                                    int32_t* lists, int64_t stride, int32_t* counts, cudaStream_t st);
 
 // --- scans -----------------------------------------------------------------
 // out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
@@ -77,17 +77,21 @@ cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t n, int64_t* out, v
 size_t tri1_smem_bytes(int dpmax, bool bitmap_in_smem);
 size_t tri2_smem_bytes(int dpmax);
 bool tri1_bitmap_fits_smem(int dpmax);
+// Largest out-degree whose adjacency bitmap fits in shared memory.
+int tri1_smem_bitmap_max();
 int tri_grid_blocks();
 // C3 per oriented edge, c3 per vertex, 4-clique count per vertex (only with
-// cliques = true). work_ctr[0..2] += (scanned out-list entries, triangles,
+// cliques = true). loads: list entries each lane has in flight per scan step
+// (2 or 4). work_ctr[0..2] += (scanned out-list entries, triangles,
 // 4-cliques).
 cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm,
-                        u64* work_ctr, int* err, cudaStream_t st, bool cliques = true);
+                        u64* work_ctr, int* err, cudaStream_t st, bool cliques = true, int loads = 2);
 size_t tri1_gbm_bytes(int dpmax);
 // d^13 (diamond, off-cord) per vertex from the final C3.
 cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
-                        int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st);
+                        int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st,
+                        int loads = 2);
 // d^10 = C3 (p1 - 2) and d^14 = D4,3 e / 2 from the final C3 (rank space).
 cudaError_t launch_c3_edge_terms(const int64_t* orp, const int32_t* ocol, const int32_t* C3o,
                                  const int32_t* dr, int64_t n, u64* r10r, u64* r14r, cudaStream_t st);
@@ -96,7 +100,7 @@ cudaError_t launch_unrank_u64(const u64* src_r, const int32_t* perm, int64_t n, 
                               cudaStream_t st);
 
 // --- 4-cycles (rank space) ---------------------------------------------------
-constexpr int CYC_CLASSES = 6;
+constexpr int CYC_CLASSES = 7;
 // Largest window of top ranks the dense class can hold (16-bit counters in
 // shared memory).
 int cyc_dense_span_max();
@@ -115,12 +119,12 @@ cudaError_t launch_in_lists(const int64_t* orp, const int32_t* ocol, const int32
                             int32_t* icur, int2* iin, int64_t* wc, int64_t* wcn, cudaStream_t st);
 // Splits the vertices with at least two wedges into CYC_CLASSES classes (lists
 // at lists + c * list_stride, counts[c]): warp table (wc <= 2^(wbits-1)),
-// three block hash-table sizes, dense hub counters (only if dense_ok, for
-// vertices of degree dr < 65536), global hash table; *gcap_max = largest table need of the last class; *wmax, *wsum =
-// largest and total wedge count. cap_bound caps the distinct tops of one
-// vertex (e.g. the largest graph of a block-diagonal batch minus one); pass n
-// when unknown.
-// cls_wedges[c] += wedges of the vertices in class c.
+// three block hash-table sizes, dense hub counters with a shared spill table
+// and with a global spill table (only if dense_ok, for vertices of degree
+// dr < 65536), global hash table; *gcap_max = largest global table need;
+// *wmax, *wsum = largest and total wedge count; cls_wedges[c] += wedges of the
+// vertices in class c. cap_bound caps the distinct tops of one vertex (e.g.
+// the largest graph of a block-diagonal batch minus one); pass n when unknown.
 cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, const int32_t* dr, int64_t n, int32_t* lists,
                                  int64_t list_stride, int32_t* counts, u64* gcap_max, u64* wmax, u64* wsum,
                                  u64* cls_wedges, bool dense_ok, int64_t cap_bound, int wbits, cudaStream_t st);
@@ -131,6 +135,7 @@ struct CycArgs {
   const int64_t* irp;
   const int2* iin;
   const int64_t* wc;
+  const int64_t* wcn;
   const int32_t* lists;
   int64_t list_stride;
   const int32_t* counts;  // CYC_CLASSES class sizes
@@ -139,8 +144,8 @@ struct CycArgs {
   int wbits;              // warp-class table slots (log2, at most cyc_warp_bits_max())
   int mid_threads[3];     // block sizes of the three hash-table classes (256, 512 or 1024)
   int heavy_threads;      // block size of the dense and global classes
-  int gbits;              // global class: cyc_gmem_blocks() << gbits slots each array
-  uint32_t* gkeys;        // NULL when the global class is empty
+  int gbits;              // global tables: cyc_gmem_blocks() << gbits slots each array
+  uint32_t* gkeys;        // NULL when both global-table classes are empty
   uint32_t* gcnt;
   u64* r12r;
   int* err;

@@ -23,17 +23,18 @@ namespace fglt {
 
 const char* const STAGE_NAMES[NUM_STAGES] = {"degree", "spmv1", "rank", "orient", "sort", "tri1", "c3_edges",
                                              "spmv2", "tri2", "wedges", "cyc", "epilogue"};
-const char* const CYC_CLASS_NAMES[CYC_CLASSES] = {"cyc.warp", "cyc.hash11", "cyc.hash12", "cyc.hash13", "cyc.dense",
-                                                  "cyc.global"};
+const char* const CYC_CLASS_NAMES[CYC_CLASSES] = {"cyc.warp",  "cyc.hash11",      "cyc.hash12", "cyc.hash13",
+                                                  "cyc.dense", "cyc.dense_spill", "cyc.global"};
 
 namespace {
 
 constexpr int64_t MAX_DEGREE_EXACT = 2097151;  // binom(d,3) products stay inside int64
+constexpr int TRI_CLASSES = 4;
 
 // Small device counters, one int slot each.
 enum CounterId {
-  C_DMAX, C_NHEAVY, C_DPMAX, C_NTRI0, C_NTRI1, C_NTRI2, C_NEXT1_0, C_NEXT1_1, C_NEXT1_2, C_NEXT2_0,
-  C_NEXT2_1, C_NEXT2_2, C_NCYC0, C_NEXTC0 = C_NCYC0 + CYC_CLASSES, C_ERR = C_NEXTC0 + CYC_CLASSES, C_NUM
+  C_DMAX, C_NHEAVY, C_DPMAX, C_NTRI0, C_NEXT1_0 = C_NTRI0 + TRI_CLASSES, C_NEXT2_0 = C_NEXT1_0 + TRI_CLASSES,
+  C_NCYC0 = C_NEXT2_0 + TRI_CLASSES, C_NEXTC0 = C_NCYC0 + CYC_CLASSES, C_ERR = C_NEXTC0 + CYC_CLASSES, C_NUM
 };
 // 64-bit work counters: triangle-pass scanned entries, triangles, 4-cliques,
 // max and total wedges of the 4-cycle stage, largest global table need.
@@ -106,6 +107,8 @@ fglt_status tuning_from_options(const fglt_options& o, Tuning* t) {
   if (o.tri_class_bounds[0]) x.tri_t0 = o.tri_class_bounds[0];
   if (o.tri_class_bounds[1]) x.tri_t1 = o.tri_class_bounds[1];
   if (x.tri_t0 < 2 || x.tri_t1 <= x.tri_t0) return FGLT_ERR_INVALID_ARG;
+  if (o.tri_probe_loads) x.tri_loads = o.tri_probe_loads;
+  if (x.tri_loads != 2 && x.tri_loads != 4) return FGLT_ERR_INVALID_ARG;
   if (o.cyc_warp_bits) x.cyc_warp_bits = o.cyc_warp_bits;
   if (x.cyc_warp_bits < 6 || x.cyc_warp_bits > cyc_warp_bits_max()) return FGLT_ERR_INVALID_ARG;
   for (int c = 0; c < 3; ++c) {
@@ -122,6 +125,7 @@ void tuning_to_options(const Tuning& t, fglt_options* o) {
   o->cyc_hub_span = t.cyc_hub_span;
   o->tri_class_bounds[0] = t.tri_t0;
   o->tri_class_bounds[1] = t.tri_t1;
+  o->tri_probe_loads = t.tri_loads;
   o->cyc_warp_bits = t.cyc_warp_bits;
   for (int c = 0; c < 3; ++c) o->cyc_mid_threads[c] = t.cyc_mid_threads[c];
   o->cyc_heavy_threads = t.cyc_heavy_threads;
@@ -286,11 +290,14 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   // Triangle-pass work lists by out-degree; each class is launched with shared
   // memory sized for its largest out-degree.
   const int T0 = tu.tri_t0, T1 = tu.tri_t1;
+  // The last class holds the vertices whose adjacency bitmap of the first
+  // pass only fits in global memory.
+  const int T2 = std::max(T1, tri1_smem_bitmap_max());
   int32_t* twork;
-  NEED(B_TWORK, 3 * n, twork);
-  CK(launch_worklist_outdeg3(opc, n, 2, T0, T1, twork, n, cnt + C_NTRI0, st));
-  const int tri_cap[3] = {std::min(dpmax, T0), std::min(dpmax, T1), dpmax};
-  const bool tri_on[3] = {dpmax >= 2, dpmax > T0, dpmax > T1};
+  NEED(B_TWORK, (int64_t)TRI_CLASSES * n, twork);
+  CK(launch_worklist_outdeg4(opc, n, 2, T0, T1, T2, twork, n, cnt + C_NTRI0, st));
+  const int tri_cap[TRI_CLASSES] = {std::min(dpmax, T0), std::min(dpmax, T1), std::min(dpmax, T2), dpmax};
+  const bool tri_on[TRI_CLASSES] = {dpmax >= 2, dpmax > T0, dpmax > T1, dpmax > T2};
 
   // Triangle pass 1: C3, c3, 4-cliques.
   mark(5);
@@ -303,16 +310,20 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   CK(cudaMemsetAsync(c3r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
   CK(cudaMemsetAsync(k4r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
   uint32_t* gbm = nullptr;
-  if (size_t gb = tri1_gbm_bytes(dpmax)) {
+  size_t gbm_need = 0;  // classes whose bitmap does not fit in shared memory share one buffer
+  for (int c = 0; c < TRI_CLASSES; ++c)
+    if (tri_on[c]) gbm_need = std::max(gbm_need, tri1_gbm_bytes(tri_cap[c]));
+  if (size_t gb = gbm_need) {
     unsigned char* p = nullptr;
     NEED(B_GBM, (int64_t)gb, p);
     gbm = reinterpret_cast<uint32_t*>(p);
   }
   if (dpmax >= 2 && tri2_smem_bytes(dpmax) > 227 * 1024) return FGLT_ERR_UNSUPPORTED;
-  for (int c = 0; c < 3; ++c)
+  for (int c = 0; c < TRI_CLASSES; ++c)
     if (tri_on[c] && need_tri1)
       CK(launch_tri1(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT1_0 + c, tri_cap[c], C3o, c3r, k4r,
-                     c == 2 ? gbm : nullptr, ctr + W_PROBES, err, st, need_k4));
+                     tri1_gbm_bytes(tri_cap[c]) ? gbm : nullptr, ctr + W_PROBES, err, st, need_k4,
+                     tu.tri_loads));
 
   // Edge terms of the final C3, then SpMV chain 2.
   mark(6);
@@ -341,10 +352,10 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   u64* r13r;
   NEED(B_R13R, n, r13r);
   CK(cudaMemsetAsync(r13r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
-  for (int c = 0; c < 3; ++c)
+  for (int c = 0; c < TRI_CLASSES; ++c)
     if (tri_on[c] && need_tri2)
       CK(launch_tri2(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT2_0 + c, tri_cap[c], C3o, r13r, err,
-                     st));
+                     st, tu.tri_loads));
 
   // 4-cycles: in-lists and wedge counts, vertex classes, then the class kernels.
   mark(9);
@@ -386,7 +397,12 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
         gcap = (u64)cap_bound;
       }
     } else {
-      READ(cnt + C_NCYC0 + (CYC_CLASSES - 1), &n_gmem);
+      int32_t ng[2];
+      {
+        fglt_status s2 = ws.read(ng, cnt + C_NCYC0 + (CYC_CLASSES - 2), sizeof ng, st);
+        if (s2 != FGLT_OK) return s2;
+      }
+      n_gmem = ng[0] + ng[1];
       READ(ctr + W_GCAP, &gcap);
     }
     mark(10);
@@ -398,6 +414,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
       ca.irp = irp;
       ca.iin = iin;
       ca.wc = wc;
+      ca.wcn = wcn;
       ca.lists = lists;
       ca.list_stride = n;
       ca.counts = cnt + C_NCYC0;

@@ -42,6 +42,7 @@ extern const char* const CYC_CLASS_NAMES[CYC_CLASSES];
 // Tunables; the counts never depend on them (fglt_options documents each).
 struct Tuning {
   int tri_t0 = 64, tri_t1 = 256;
+  int tri_loads = 2;
   int cyc_warp_bits = 10;
   int cyc_mid_threads[3] = {256, 256, 256};
   int cyc_heavy_threads = 1024;

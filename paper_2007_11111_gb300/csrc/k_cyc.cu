@@ -29,7 +29,9 @@
 //    other tops (heavy vertices: most wedges of a power-law graph end at a
 //    hub; a count never exceeds the degree of w, so 16 bits suffice for every
 //    w of degree below 65536, and the others take the global class),
-//  - or a global-memory hash table (fallback).
+//  - the dense window with the other tops in a per-block global-memory hash
+//    table (heavy vertices with many tops outside the window),
+//  - or a global-memory hash table alone (fallback).
 // Wedges are walked cooperatively: the segments of N+(v) of many middles v are
 // concatenated and split evenly over the lanes of a warp or a block.
 #include "fglt_device.cuh"
@@ -451,10 +453,11 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
                                                   const int64_t* __restrict__ irp, const int2* __restrict__ iin,
                                                   const int64_t* __restrict__ wc, const int32_t* __restrict__ list,
                                                   const int32_t* __restrict__ cnt, int* next, u64* r12r, int64_t n,
-                                                  int32_t hub_lo, int tbits, int dense_words, uint32_t* gkeys,
+                                                  const int64_t* __restrict__ wcn, int32_t hub_lo, int tbits,
+                                                  int dense_words, uint32_t* gkeys,
                                                   uint32_t* gcnt, int64_t cap_bound, int* err) {
-  constexpr bool DENSE = MODE == 1;
-  constexpr bool GMEM = MODE == 3;
+  constexpr bool DENSE = MODE == 1 || MODE == 4;
+  constexpr bool GMEM = MODE == 3 || MODE == 4;
   constexpr int CH = BT < CHUNK_MAX ? BT : CHUNK_MAX;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
@@ -501,13 +504,15 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
     if (item >= total) break;
     const int32_t w = list[item];
     int hb = tbits;
-    if (!DENSE) {
-      int64_t cap = wc[w];
+    if (!DENSE || GMEM) {
+      // distinct tops the table must hold: all of them, or (dense window)
+      // those below the window, at most the wedges that reach them
+      int64_t cap = GMEM && DENSE ? wcn[w] : wc[w];
       if (cap > n - 1 - w) cap = n - 1 - w;
       if (cap > cap_bound) cap = cap_bound;
       hb = 5;
       while ((1LL << hb) < 2 * cap) ++hb;
-      if (hb > tbits) hb = tbits;  // the class guarantees 2 * cap <= 2^tbits
+      if (hb > tbits) hb = tbits;  // the class (or the table sizing) guarantees 2 * cap <= 2^tbits
     }
     const uint32_t H = 1u << hb;
     if (DENSE) {
@@ -643,7 +648,7 @@ __global__ void k_in_fill(const int64_t* __restrict__ orp, const int32_t* __rest
 
 // Vertex classes (CYC_CLASSES lists): 0 = warp table, 1..3 = block + shared
 // hash table of 2^MID_BITS[c-1] slots, 4 = block + dense hub counters + shared
-// hash, 5 = block + global hash. Also the stage's total and largest wedge
+// hash, 5 = block + dense hub counters + global hash, 6 = block + global hash. Also the stage's total and largest wedge
 // counts (work counters).
 __global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* __restrict__ wcn,
                                 const int32_t* __restrict__ dr, int64_t n,
@@ -670,9 +675,11 @@ __global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* _
       else if (cap <= (1LL << (MID_BITS1 - 1))) cls = 2;
       else if (cap <= (1LL << (MID_BITS2 - 1))) cls = 3;
       else if (dense_ok && wcn[r] <= (1 << (DHASH_BITS - 1)) && dr[r] < 65536) cls = 4;
-      else cls = 5;
+      else if (dense_ok && dr[r] < 65536) cls = 5;
+      else cls = 6;
     }
-    if (cls == 5) atomicMax(gcap_max, (u64)cap);
+    if (cls == 5) atomicMax(gcap_max, (u64)min(cap, (int64_t)wcn[r]));
+    if (cls == 6) atomicMax(gcap_max, (u64)cap);
 #pragma unroll
     for (int c = 0; c < CYC_CLASSES; ++c) {
       if (cls == c) csum[c] += (u64)wc[r];
@@ -710,6 +717,7 @@ size_t block_smem(int mode, int bt, int tbits, int dense_words) {
   const size_t seg = seg_bytes(bt < CHUNK_MAX ? bt : CHUNK_MAX);
   if (mode == 0) return seg + ((size_t)8 << tbits);
   if (mode == 1) return seg + (size_t)dense_words * 4 + ((size_t)8 << DHASH_BITS);
+  if (mode == 4) return seg + (size_t)dense_words * 4;
   return seg;
 }
 
@@ -719,9 +727,10 @@ template <int MODE, int BT>
 void launch_block(const CycArgs& a, int cls, int tbits, int dense_words, cudaStream_t st) {
   const size_t smem = block_smem(MODE, BT, tbits, dense_words);
   allow_max_smem(k_cyc_block<MODE, BT>);
-  const int grid = MODE == 3 ? gmem_blocks() : num_sms() * occupancy((const void*)k_cyc_block<MODE, BT>, BT, smem);
+  // global-table modes: one table per block, cyc_gmem_blocks() tables
+  const int grid = MODE >= 3 ? gmem_blocks() : num_sms() * occupancy((const void*)k_cyc_block<MODE, BT>, BT, smem);
   k_cyc_block<MODE, BT><<<grid, BT, smem, st>>>(a.orp, a.ocol, a.irp, a.iin, a.wc, a.lists + cls * a.list_stride,
-                                                a.counts + cls, a.next + cls, a.r12r, a.n, a.hub_lo, tbits,
+                                                a.counts + cls, a.next + cls, a.r12r, a.n, a.wcn, a.hub_lo, tbits,
                                                 dense_words, a.gkeys, a.gcnt, a.cap_bound, a.err);
   note_launch();
 }
@@ -793,8 +802,10 @@ cudaError_t launch_cyc(const CycArgs& a, cudaStream_t st) {
   const int span = (int)(a.n - a.hub_lo);
   if (span > 0) launch_block_bt<1>(a, 4, DHASH_BITS, (span + 1) / 2, a.heavy_threads, st);
   mark(5);
-  if (a.gkeys) launch_block_bt<3>(a, 5, a.gbits, 0, a.heavy_threads, st);
+  if (a.gkeys && span > 0) launch_block_bt<4>(a, 5, a.gbits, (span + 1) / 2, a.heavy_threads, st);
   mark(6);
+  if (a.gkeys) launch_block_bt<3>(a, 6, a.gbits, 0, a.heavy_threads, st);
+  mark(7);
   return cudaGetLastError();
 }
 

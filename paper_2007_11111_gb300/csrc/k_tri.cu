@@ -86,6 +86,25 @@ __device__ __forceinline__ bool filter_test(const uint32_t* filt, uint32_t key, 
   return (filt[b >> 5] >> (b & 31)) & 1u;
 }
 
+// Warp scan of the sorted list ocol[bb, be) up to the first entry above
+// last: PL loads per lane in flight per step (32 * PL entries), probe(c, k)
+// for each entry c = ocol[k] (entries past the end read as INT_MAX).
+template <int PL, typename P>
+__device__ __forceinline__ void scan_sorted(const int32_t* __restrict__ ocol, int64_t bb, int64_t be, int32_t last,
+                                            int lane, P probe) {
+  for (int64_t k0 = bb; k0 < be; k0 += 32 * PL) {
+    int32_t c[PL];
+#pragma unroll
+    for (int t = 0; t < PL; ++t) {
+      const int64_t k = k0 + lane + 32 * t;
+      c[t] = k < be ? ocol[k] : 0x7fffffff;
+    }
+#pragma unroll
+    for (int t = 0; t < PL; ++t) probe(c[t], k0 + lane + 32 * t);
+    if (__shfl_sync(0xffffffffu, c[PL - 1], 31) > last) break;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Pass 1
 //
@@ -96,7 +115,7 @@ __device__ __forceinline__ bool filter_test(const uint32_t* filt, uint32_t key, 
 //                                  i.e. twice the 4-cliques {a, x, ., .}
 // and a's own counts are the sums over x divided by 2 and 6.
 // ---------------------------------------------------------------------------
-template <bool SMEM_BM, bool K4>
+template <bool SMEM_BM, bool K4, int PL>
 __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
                                                 const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
                                                 int* next, int Dmax, int Hbits, int32_t* C3o, u64* c3r, u64* k4r,
@@ -165,15 +184,7 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
           }
         }
       };
-      // two steps per iteration so that both loads are in flight together
-      for (int64_t k0 = bb; k0 < be; k0 += 64) {
-        const int64_t k1 = k0 + lane, k2 = k1 + 32;
-        const int32_t c1 = k1 < be ? ocol[k1] : 0x7fffffff;
-        const int32_t c2 = k2 < be ? ocol[k2] : 0x7fffffff;
-        probe(c1, k1);
-        probe(c2, k2);
-        if (__shfl_sync(0xffffffffu, c2, 31) > lastA) break;
-      }
+      scan_sorted<PL>(ocol, bb, be, lastA, lane, probe);
     }
     __syncthreads();
 
@@ -266,6 +277,7 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
 // ---------------------------------------------------------------------------
 // Pass 2
 // ---------------------------------------------------------------------------
+template <int PL>
 __global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
                                                 const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
                                                 int* next, int Dmax, int Hbits, const int32_t* __restrict__ C3o,
@@ -322,14 +334,7 @@ __global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp,
           }
         }
       };
-      for (int64_t k0 = bb; k0 < be; k0 += 64) {
-        const int64_t k1 = k0 + lane, k2 = k1 + 32;
-        const int32_t c1 = k1 < be ? ocol[k1] : 0x7fffffff;
-        const int32_t c2 = k2 < be ? ocol[k2] : 0x7fffffff;
-        probe(c1, k1);
-        probe(c2, k2);
-        if (__shfl_sync(0xffffffffu, c2, 31) > lastA) break;
-      }
+      scan_sorted<PL>(ocol, bb, be, lastA, lane, probe);
       accb = warp_sum_i64(accb);
       if (lane == 0 && accb) atomicAdd(&acc[ib], (u64)accb);
     }
@@ -368,6 +373,15 @@ int occupancy_grid(const void* fn, size_t smem) {
 
 bool tri1_bitmap_fits_smem(int dpmax) { return tri1_smem_impl(dpmax, true) <= SMEM_LIMIT - 1024; }
 
+int tri1_smem_bitmap_max() {
+  int lo = 2, hi = 1 << 14;  // fits(lo), !fits(hi)
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if (tri1_bitmap_fits_smem(mid)) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 size_t tri1_smem_bytes(int dpmax, bool bitmap_in_smem) { return tri1_smem_impl(dpmax, bitmap_in_smem); }
 
 size_t tri2_smem_bytes(int dpmax) {
@@ -377,16 +391,22 @@ size_t tri2_smem_bytes(int dpmax) {
 
 int tri_grid_blocks() { return num_sms(); }
 
+template <bool SMEM_BM>
+void allow_tri1() {
+  allow_max_smem(k_tri1<SMEM_BM, true, 2>);
+  allow_max_smem(k_tri1<SMEM_BM, false, 2>);
+  allow_max_smem(k_tri1<SMEM_BM, true, 4>);
+  allow_max_smem(k_tri1<SMEM_BM, false, 4>);
+}
+
 static int tri1_grid(int dpmax, bool smem_bm) {
   const size_t smem = tri1_smem_impl(dpmax, smem_bm);
   if (smem_bm) {
-    allow_max_smem(k_tri1<true, true>);
-    allow_max_smem(k_tri1<true, false>);
-    return occupancy_grid((const void*)k_tri1<true, true>, smem);
+    allow_tri1<true>();
+    return occupancy_grid((const void*)k_tri1<true, true, 2>, smem);
   }
-  allow_max_smem(k_tri1<false, true>);
-  allow_max_smem(k_tri1<false, false>);
-  return occupancy_grid((const void*)k_tri1<false, true>, smem);
+  allow_tri1<false>();
+  return occupancy_grid((const void*)k_tri1<false, true, 2>, smem);
 }
 
 size_t tri1_gbm_bytes(int dpmax) {
@@ -397,14 +417,16 @@ size_t tri1_gbm_bytes(int dpmax) {
 
 cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm, u64* work_ctr,
-                        int* err, cudaStream_t st, bool cliques) {
+                        int* err, cudaStream_t st, bool cliques, int loads) {
   if (dpmax < 2) return cudaSuccess;
   const bool smem_bm = tri1_bitmap_fits_smem(dpmax);
   const size_t smem = tri1_smem_impl(dpmax, smem_bm);
   const int grid = tri1_grid(dpmax, smem_bm);
   const int hb = hash_bits_for(dpmax);
-  auto* fn = smem_bm ? (cliques ? k_tri1<true, true> : k_tri1<true, false>)
-                     : (cliques ? k_tri1<false, true> : k_tri1<false, false>);
+  auto* fn = loads >= 4 ? (smem_bm ? (cliques ? k_tri1<true, true, 4> : k_tri1<true, false, 4>)
+                                   : (cliques ? k_tri1<false, true, 4> : k_tri1<false, false, 4>))
+                        : (smem_bm ? (cliques ? k_tri1<true, true, 2> : k_tri1<true, false, 2>)
+                                   : (cliques ? k_tri1<false, true, 2> : k_tri1<false, false, 2>));
   fn<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, C3o, c3r, k4r, smem_bm ? nullptr : gbm,
                                 work_ctr, err);
   note_launch();
@@ -412,13 +434,15 @@ cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* 
 }
 
 cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
-                        int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st) {
+                        int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st, int loads) {
   if (dpmax < 2) return cudaSuccess;
   const size_t smem = tri2_smem_bytes(dpmax);
   if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
-  allow_max_smem(k_tri2);
-  const int grid = occupancy_grid((const void*)k_tri2, smem);
-  k_tri2<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hash_bits_for(dpmax), C3o, r13r, err);
+  auto* fn = loads >= 4 ? k_tri2<4> : k_tri2<2>;
+  allow_max_smem(k_tri2<2>);
+  allow_max_smem(k_tri2<4>);
+  const int grid = occupancy_grid((const void*)fn, smem);
+  fn<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hash_bits_for(dpmax), C3o, r13r, err);
   note_launch();
   return cudaGetLastError();
 }

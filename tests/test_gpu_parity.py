@@ -234,8 +234,9 @@ def test_cycle_paths_with_small_hub_span(span):
 def test_rmat_s20_full_size_sampled(handle):
     """R-MAT scale 20, edge factor 16, seed 0 (the benchmark workload), in the
     benchmark's launch configuration: every row checked against the invariants
-    that hold at any size, and a vertex sample (top-degree hubs, low-degree and
-    isolated vertices, uniform picks) element by element against the oracle."""
+    that hold at any size, and a vertex sample (high-degree, dense-class,
+    low-degree and isolated vertices, uniform picks) element by element
+    against the oracle."""
     g = gg.rmat(20, 16, seed=0)
     raw, net = gpu(handle, g)
     deg = np.diff(g.rowptr)
@@ -251,8 +252,11 @@ def test_rmat_s20_full_size_sampled(handle):
     # sampled rows vs the oracle
     rng = np.random.default_rng(2024)
     order = np.argsort(deg)
-    verts = np.unique(np.concatenate([order[-8:], order[:4], order[len(order) // 2: len(order) // 2 + 4],
-                                      rng.integers(0, g.n, 40)]))
+    # a high-degree vertex (rank 300 from the top, degree ~4000), vertices of
+    # the dense 4-cycle classes (ranks 1500 and 3000), the lowest, median and
+    # random ones; the largest hubs cost the oracle minutes per row
+    verts = np.unique(np.concatenate([order[[-300, -1500, -3000]], order[:4],
+                                      order[len(order) // 2: len(order) // 2 + 4], rng.integers(0, g.n, 40)]))
     oraw, onet = oracle.fglt(g, vertices=verts)
     assert_same(raw[verts], oraw, "sampled raw")
     assert_same(net[verts], onet, "sampled net")

@@ -16,7 +16,8 @@ torch = pytest.importorskip("torch")
 SETTINGS = [
     dict(),
     dict(tri_class_bounds=(2, 3)),
-    dict(tri_class_bounds=(8, 1024)),
+    dict(tri_class_bounds=(8, 1024), tri_probe_loads=4),
+    dict(tri_class_bounds=(3, 2000), tri_probe_loads=4),
     dict(cyc_warp_bits=6),
     dict(cyc_warp_bits=8, cyc_mid_threads=(512, 1024, 512)),
     dict(cyc_mid_threads=(1024, 256, 1024), cyc_heavy_threads=256),
@@ -65,7 +66,7 @@ def test_invalid_settings_rejected():
         pytest.skip("no CUDA device")
     for bad in (dict(tri_class_bounds=(64, 32)), dict(tri_class_bounds=(1, 8)), dict(cyc_warp_bits=11),
                 dict(cyc_warp_bits=5), dict(cyc_mid_threads=(128, 256, 256)), dict(cyc_heavy_threads=300),
-                dict(cyc_hub_span=-1)):
+                dict(cyc_hub_span=-1), dict(cyc_hub_span=90113), dict(tri_probe_loads=3)):
         with pytest.raises(fg.FgltError) as e:
             fg.Handle(device=0, **bad)
         assert e.value.status == fg.FGLT_ERR_INVALID_ARG
@@ -94,8 +95,27 @@ def test_autotune_installs_setting_and_keeps_results(cases):
             np.testing.assert_array_equal(net, wn)
         # a fresh handle created with the chosen setting gives the same counts
         kw = dict(tri_class_bounds=tuple(chosen["tri_class_bounds"]), cyc_warp_bits=chosen["cyc_warp_bits"],
+                  tri_probe_loads=chosen["tri_probe_loads"],
                   cyc_mid_threads=tuple(chosen["cyc_mid_threads"]), cyc_heavy_threads=chosen["cyc_heavy_threads"],
                   cyc_hub_span=chosen["cyc_hub_span"])
         with fg.Handle(device=0, **kw) as h2:
             raw, net = _run(h2, g)
             np.testing.assert_array_equal(net, onet)
+
+
+@pytest.mark.parametrize("bounds", [(3, 2000), (64, 256)])
+def test_global_bitmap_in_any_class_closed_form(bounds):
+    """K_1200: every out-degree in the degree order is above the shared-memory
+    bitmap limit, so with class bounds (3, 2000) a middle class runs on the
+    global-memory bitmap. Net counts have the closed form of a clique."""
+    import paper_2007_11111_gb300 as fg
+    from math import comb
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    n = 1200
+    g = gg.complete(n)
+    with fg.Handle(device=0, tri_class_bounds=bounds) as h:
+        _, net = _run(h, g)
+    want = np.zeros(16, np.int64)
+    want[0], want[1], want[4], want[15] = 1, n - 1, comb(n - 1, 2), comb(n - 1, 3)
+    np.testing.assert_array_equal(net, np.tile(want, (n, 1)))
