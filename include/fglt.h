@@ -224,9 +224,11 @@ fglt_status fglt_csr_from_edges(fglt_t handle, const int32_t* src, const int32_t
  * fglt_options.profile_stages = 1. names[i] points to static strings.
  * *count receives the number of entries (at most max_stages are written):
  * the stages in order (degree, spmv1, rank, orient, sort, tri1, c3_edges,
- * spmv2, tri2, wedges, cyc, epilogue), then the seven 4-cycle vertex
- * classes inside "cyc" (cyc.warp, cyc.hash11, cyc.hash12, cyc.hash13,
- * cyc.dense, cyc.dense_spill, cyc.global; 0 when the stage did not run). */
+ * spmv2, tri2, wedges, cyc, epilogue), then their parts: the seven 4-cycle
+ * vertex classes inside "cyc" (cyc.warp, cyc.hash11, cyc.hash12, cyc.hash13,
+ * cyc.dense, cyc.dense_spill, cyc.global) and the four out-degree classes of
+ * each triangle pass (tri1.c0 .. tri1.c3, tri2.c0 .. tri2.c3); a part that
+ * did not run reads 0. */
 fglt_status fglt_stage_times(fglt_t handle, const char** names, float* ms,
                              int max_stages, int* count);
 

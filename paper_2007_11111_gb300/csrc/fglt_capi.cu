@@ -42,9 +42,9 @@ struct fglt_handle {
   int64_t* pinned = nullptr;  // small host staging for read-backs
   std::string cuda_err;
   cudaEvent_t ev[NUM_STAGES + 1] = {};
-  cudaEvent_t cyc_ev[CYC_CLASSES + 1] = {};
-  float stage_ms[NUM_STAGES + CYC_CLASSES] = {};
-  bool cyc_valid = false;
+  cudaEvent_t sub_ev[2 * NUM_SUB] = {};
+  bool sub_rec[NUM_SUB] = {};
+  float stage_ms[NUM_STAGES + NUM_SUB] = {};
   bool stages_valid = false;
   int64_t work[O_NUM] = {};
   bool work_valid = false;
@@ -140,7 +140,8 @@ fglt_status run_on_handle(fglt_t h, const Csr& g, int64_t* out_raw, int64_t* out
   ro.capturing = capturing;
   const bool prof = (h->opt.profile_stages != 0 || force_profile) && !capturing;
   ro.stage_events = prof ? h->ev : nullptr;
-  ro.cyc_events = prof ? h->cyc_ev : nullptr;
+  ro.sub_events = prof ? h->sub_ev : nullptr;
+  ro.sub_recorded = prof ? h->sub_rec : nullptr;
   int64_t work[O_NUM];
   ro.work = capturing ? nullptr : work;
   h->stages_valid = false;
@@ -151,11 +152,9 @@ fglt_status run_on_handle(fglt_t h, const Csr& g, int64_t* out_raw, int64_t* out
   h->work_valid = true;
   if (prof) {
     for (int i = 0; i < NUM_STAGES; ++i) cudaEventElapsedTime(&h->stage_ms[i], h->ev[i], h->ev[i + 1]);
-    // class timers exist only when the 4-cycle stage ran
-    h->cyc_valid = cudaEventQuery(h->cyc_ev[CYC_CLASSES]) == cudaSuccess && work[O_WEDGES] > 0;
-    for (int c = 0; c < CYC_CLASSES; ++c) {
+    for (int c = 0; c < NUM_SUB; ++c) {  // sub-stages that did not run read 0
       float t = 0;
-      if (h->cyc_valid && cudaEventElapsedTime(&t, h->cyc_ev[c], h->cyc_ev[c + 1]) != cudaSuccess) t = 0;
+      if (h->sub_rec[c] && cudaEventElapsedTime(&t, h->sub_ev[2 * c], h->sub_ev[2 * c + 1]) != cudaSuccess) t = 0;
       h->stage_ms[NUM_STAGES + c] = t;
     }
     cudaGetLastError();
@@ -378,7 +377,7 @@ fglt_status fglt_create(fglt_t* out, const fglt_options* opt, int device) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMallocHost(&h->pinned, 256);
   for (int i = 0; e == cudaSuccess && i <= NUM_STAGES; ++i) e = cudaEventCreate(&h->ev[i]);
-  for (int i = 0; e == cudaSuccess && i <= CYC_CLASSES; ++i) e = cudaEventCreate(&h->cyc_ev[i]);
+  for (int i = 0; e == cudaSuccess && i < 2 * NUM_SUB; ++i) e = cudaEventCreate(&h->sub_ev[i]);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -405,8 +404,8 @@ fglt_status fglt_destroy(fglt_t h) {
     if (b.p) cudaFree(b.p);
   for (int i = 0; i <= NUM_STAGES; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
-  for (int i = 0; i <= CYC_CLASSES; ++i)
-    if (h->cyc_ev[i]) cudaEventDestroy(h->cyc_ev[i]);
+  for (int i = 0; i < 2 * NUM_SUB; ++i)
+    if (h->sub_ev[i]) cudaEventDestroy(h->sub_ev[i]);
   if (h->pinned) cudaFreeHost(h->pinned);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -624,10 +623,10 @@ fglt_status fglt_stage_times(fglt_t h, const char** names, float* ms, int max_st
     *count = 0;
     return FGLT_ERR_NOT_FOUND;
   }
-  const int total = NUM_STAGES + CYC_CLASSES;
+  const int total = NUM_STAGES + NUM_SUB;
   const int k = std::min(max_stages, total);
   for (int i = 0; i < k; ++i) {
-    if (names) names[i] = i < NUM_STAGES ? STAGE_NAMES[i] : CYC_CLASS_NAMES[i - NUM_STAGES];
+    if (names) names[i] = i < NUM_STAGES ? STAGE_NAMES[i] : SUB_NAMES[i - NUM_STAGES];
     if (ms) ms[i] = h->stage_ms[i];
   }
   *count = total;

@@ -101,6 +101,7 @@ cudaError_t launch_unrank_u64(const u64* src_r, const int32_t* perm, int64_t n, 
 
 // --- 4-cycles (rank space) ---------------------------------------------------
 constexpr int CYC_CLASSES = 7;
+constexpr int TRI_CLASSES = 4;  // out-degree classes of the triangle passes
 // Largest window of top ranks the dense class can hold (16-bit counters in
 // shared memory).
 int cyc_dense_span_max();
@@ -150,7 +151,8 @@ struct CycArgs {
   u64* r12r;
   int* err;
   int64_t cap_bound;      // bound on distinct tops of one vertex (n when unknown)
-  cudaEvent_t* ev;        // CYC_CLASSES + 1 events around the class launches, or NULL
+  cudaEvent_t* ev;        // 2 * CYC_CLASSES events (start, stop of each class launch), or NULL
+  bool* ev_rec;           // CYC_CLASSES flags: the class's pair was recorded
 };
 cudaError_t launch_cyc(const CycArgs& a, cudaStream_t st);
 

@@ -23,13 +23,13 @@ namespace fglt {
 
 const char* const STAGE_NAMES[NUM_STAGES] = {"degree", "spmv1", "rank", "orient", "sort", "tri1", "c3_edges",
                                              "spmv2", "tri2", "wedges", "cyc", "epilogue"};
-const char* const CYC_CLASS_NAMES[CYC_CLASSES] = {"cyc.warp",  "cyc.hash11",      "cyc.hash12", "cyc.hash13",
-                                                  "cyc.dense", "cyc.dense_spill", "cyc.global"};
+const char* const SUB_NAMES[NUM_SUB] = {"cyc.warp",    "cyc.hash11",      "cyc.hash12", "cyc.hash13", "cyc.dense",
+                                        "cyc.dense_spill", "cyc.global",   "tri1.c0",    "tri1.c1",    "tri1.c2",
+                                        "tri1.c3",     "tri2.c0",         "tri2.c1",    "tri2.c2",    "tri2.c3"};
 
 namespace {
 
 constexpr int64_t MAX_DEGREE_EXACT = 2097151;  // binom(d,3) products stay inside int64
-constexpr int TRI_CLASSES = 4;
 
 // Small device counters, one int slot each.
 enum CounterId {
@@ -162,6 +162,13 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   auto mark = [&](int i) {
     if (ro.stage_events && !capturing) cudaEventRecord(ro.stage_events[i], st);
   };
+  auto sub = [&](int i, int edge) {  // sub-stage i: edge 0 = start, 1 = stop
+    if (!ro.sub_events || capturing) return;
+    cudaEventRecord(ro.sub_events[2 * i + edge], st);
+    if (edge) ro.sub_recorded[i] = true;
+  };
+  if (ro.sub_recorded)
+    for (int i = 0; i < NUM_SUB; ++i) ro.sub_recorded[i] = false;
 #define CK(call)                            \
   do {                                      \
     cudaError_t e__ = (call);               \
@@ -320,10 +327,13 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   }
   if (dpmax >= 2 && tri2_smem_bytes(dpmax) > 227 * 1024) return FGLT_ERR_UNSUPPORTED;
   for (int c = 0; c < TRI_CLASSES; ++c)
-    if (tri_on[c] && need_tri1)
+    if (tri_on[c] && need_tri1) {
+      sub(CYC_CLASSES + c, 0);
       CK(launch_tri1(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT1_0 + c, tri_cap[c], C3o, c3r, k4r,
                      tri1_gbm_bytes(tri_cap[c]) ? gbm : nullptr, ctr + W_PROBES, err, st, need_k4,
                      tu.tri_loads));
+      sub(CYC_CLASSES + c, 1);
+    }
 
   // Edge terms of the final C3, then SpMV chain 2.
   mark(6);
@@ -353,9 +363,12 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   NEED(B_R13R, n, r13r);
   CK(cudaMemsetAsync(r13r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
   for (int c = 0; c < TRI_CLASSES; ++c)
-    if (tri_on[c] && need_tri2)
+    if (tri_on[c] && need_tri2) {
+      sub(CYC_CLASSES + TRI_CLASSES + c, 0);
       CK(launch_tri2(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT2_0 + c, tri_cap[c], C3o, r13r, err,
                      st, tu.tri_loads));
+      sub(CYC_CLASSES + TRI_CLASSES + c, 1);
+    }
 
   // 4-cycles: in-lists and wedge counts, vertex classes, then the class kernels.
   mark(9);
@@ -426,7 +439,8 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
       ca.r12r = r12r;
       ca.err = err;
       ca.cap_bound = cap_bound;
-      ca.ev = capturing ? nullptr : ro.cyc_events;
+      ca.ev = capturing ? nullptr : ro.sub_events;
+      ca.ev_rec = ro.sub_recorded;
       if (n_gmem > 0) {
         ca.gbits = bits_for((int64_t)gcap);
         const int64_t slots = (int64_t)cyc_gmem_blocks() << ca.gbits;

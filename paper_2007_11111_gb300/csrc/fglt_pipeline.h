@@ -36,8 +36,10 @@ enum WorkOut {
 
 constexpr int NUM_STAGES = 12;
 extern const char* const STAGE_NAMES[NUM_STAGES];
-// Sub-stages of "cyc": one per 4-cycle vertex class.
-extern const char* const CYC_CLASS_NAMES[CYC_CLASSES];
+// Sub-stages: the 4-cycle vertex classes inside "cyc", then the out-degree
+// classes of "tri1" and of "tri2".
+constexpr int NUM_SUB = CYC_CLASSES + 2 * TRI_CLASSES;
+extern const char* const SUB_NAMES[NUM_SUB];
 
 // Tunables; the counts never depend on them (fglt_options documents each).
 struct Tuning {
@@ -80,7 +82,8 @@ struct RunOptions {
   const Bounds* bounds = nullptr;   // replaces every read-back (see Bounds)
   bool capturing = false;           // stream capture in progress: no read-back, no allocation
   cudaEvent_t* stage_events = nullptr;  // NUM_STAGES + 1 events, or NULL
-  cudaEvent_t* cyc_events = nullptr;    // CYC_CLASSES + 1 events, or NULL
+  cudaEvent_t* sub_events = nullptr;    // 2 * NUM_SUB events (start, stop per sub-stage), or NULL
+  bool* sub_recorded = nullptr;         // NUM_SUB flags set for the sub-stages that ran
   int64_t* work = nullptr;              // O_NUM counters out, or NULL
 };
 

@@ -783,29 +783,41 @@ cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, const in
 
 cudaError_t launch_cyc(const CycArgs& a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
-  auto mark = [&](int c) {
-    if (a.ev) cudaEventRecord(a.ev[c], st);
+  auto mark = [&](int c, int edge) {
+    if (!a.ev) return;
+    cudaEventRecord(a.ev[2 * c + edge], st);
+    if (edge) a.ev_rec[c] = true;
   };
   const int sms = num_sms();
   const int wbits = a.wbits;
   const size_t wsmem = (size_t)(WARP_T / 32) * (32 * 8 + ((size_t)8 << wbits));
   allow_max_smem(k_cyc_warp);
-  mark(0);
+  mark(0, 0);
   k_cyc_warp<<<sms * occupancy((const void*)k_cyc_warp, WARP_T, wsmem), WARP_T, wsmem, st>>>(
       a.orp, a.ocol, a.irp, a.iin, a.wc, a.lists, a.counts, a.next + 0, a.r12r, a.n, a.cap_bound, wbits, a.err);
   note_launch();
+  mark(0, 1);
   for (int c = 0; c < 3; ++c) {
-    mark(1 + c);
+    mark(1 + c, 0);
     launch_block_bt<0>(a, 1 + c, MID_BITS[c], 0, a.mid_threads[c], st);
+    mark(1 + c, 1);
   }
-  mark(4);
   const int span = (int)(a.n - a.hub_lo);
-  if (span > 0) launch_block_bt<1>(a, 4, DHASH_BITS, (span + 1) / 2, a.heavy_threads, st);
-  mark(5);
-  if (a.gkeys && span > 0) launch_block_bt<4>(a, 5, a.gbits, (span + 1) / 2, a.heavy_threads, st);
-  mark(6);
-  if (a.gkeys) launch_block_bt<3>(a, 6, a.gbits, 0, a.heavy_threads, st);
-  mark(7);
+  if (span > 0) {
+    mark(4, 0);
+    launch_block_bt<1>(a, 4, DHASH_BITS, (span + 1) / 2, a.heavy_threads, st);
+    mark(4, 1);
+  }
+  if (a.gkeys && span > 0) {
+    mark(5, 0);
+    launch_block_bt<4>(a, 5, a.gbits, (span + 1) / 2, a.heavy_threads, st);
+    mark(5, 1);
+  }
+  if (a.gkeys) {
+    mark(6, 0);
+    launch_block_bt<3>(a, 6, a.gbits, 0, a.heavy_threads, st);
+    mark(6, 1);
+  }
   return cudaGetLastError();
 }
 
