@@ -96,16 +96,20 @@ typedef struct {
      *   latency, at the cost of scanning up to 32 * loads entries past the end
      *   of a scan. */
     int tri_probe_loads;
+    /* tri_hash_factor: slots per element of the shared-memory hash table of
+     *   N+(a) in the triangle passes, 2 or 4 (default 2): 4 shortens the probe
+     *   runs that every lane of a warp waits for, at twice the table memory. */
+    int tri_hash_factor;
     /* cyc_warp_bits: log2 of the per-warp hash-table slots of the 4-cycle
      *   stage's warp class, which takes vertices with at most 2^(bits-1)
      *   wedges (6..10, default 10). */
     int cyc_warp_bits;
-    /* cyc_mid_threads: thread-block size (256, 512 or 1024; default 256) of
+    /* cyc_mid_threads: thread-block size (128, 256, 512 or 1024; default 256) of
      *   the three block hash-table classes of the 4-cycle stage (tables of
      *   2^11, 2^12, 2^13 slots). */
     int cyc_mid_threads[3];
     /* cyc_heavy_threads: block size of the dense-counter and global-table
-     *   classes of the 4-cycle stage (256, 512 or 1024; default 1024). */
+     *   classes of the 4-cycle stage (128, 256, 512 or 1024; default 1024). */
     int cyc_heavy_threads;
     /* Sub-dictionary s of Sigma16 (Table II caption): bit k set = sigma_k in
      * s; 0 (or 0xFFFF) selects Sigma16. Bits 0 and 1 must be set and no bit

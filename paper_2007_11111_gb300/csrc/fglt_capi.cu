@@ -227,18 +227,22 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
     if ((s = time_once(h, g, st, start, 1, &base)) != FGLT_OK) return s;  // warm-up (sizes the workspace)
     if ((s = time_once(h, g, st, start, reps, &base)) != FGLT_OK) return s;
     // Candidate values per parameter, tried one parameter at a time.
-    const int t_bounds[][3] = {{32, 128, 2}, {64, 256, 4}, {128, 512, 2}, {32, 256, 4}, {64, 1024, 2},
-                               {64, 256, 2}};
+    // triangle candidates: class bounds t0, t1, loads in flight, hash slots per element
+    const int t_bounds[][4] = {{32, 128, 2, 2}, {64, 256, 4, 2}, {128, 512, 2, 2}, {32, 256, 4, 4},
+                               {64, 1024, 2, 2}, {64, 256, 2, 4}, {64, 256, 4, 4}, {128, 512, 4, 4}};
     const int wbits[] = {8, 9, 10};
     const int spans[] = {0, 16384, 32768, 65536, 90112};
-    const int threads[] = {256, 512, 1024};
+    const int threads[] = {128, 256, 512, 1024};
     std::vector<Tuning> tri_c, cyc_c;
     for (auto& tb : t_bounds) {
       Tuning t = best;
       t.tri_t0 = tb[0];
       t.tri_t1 = tb[1];
       t.tri_loads = tb[2];
-      if (t.tri_t0 != start.tri_t0 || t.tri_t1 != start.tri_t1 || t.tri_loads != start.tri_loads) tri_c.push_back(t);
+      t.tri_hash_factor = tb[3];
+      if (t.tri_t0 != start.tri_t0 || t.tri_t1 != start.tri_t1 || t.tri_loads != start.tri_loads ||
+          t.tri_hash_factor != start.tri_hash_factor)
+        tri_c.push_back(t);
     }
     TuneScore cur = base;
     // The 4-cycle parameters interact through the class split: search them in
@@ -254,6 +258,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
           run.tri_t0 = tri_c.back().tri_t0;
           run.tri_t1 = tri_c.back().tri_t1;
           run.tri_loads = tri_c.back().tri_loads;
+          run.tri_hash_factor = tri_c.back().tri_hash_factor;
         }
         TuneScore sc;
         fglt_status e = time_once(h, g, st, run, reps, &sc);
@@ -263,16 +268,18 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
             best.tri_t0 = run.tri_t0;
             best.tri_t1 = run.tri_t1;
             best.tri_loads = run.tri_loads;
+            best.tri_hash_factor = run.tri_hash_factor;
             cur.tri = sc.tri;
           }
           tri_c.pop_back();
         }
         if (sc.cyc < cur.cyc) {
-          const int t0 = best.tri_t0, t1 = best.tri_t1, tl = best.tri_loads;
+          const int t0 = best.tri_t0, t1 = best.tri_t1, tl = best.tri_loads, thf = best.tri_hash_factor;
           best = t;
           best.tri_t0 = t0;
           best.tri_t1 = t1;
           best.tri_loads = tl;
+          best.tri_hash_factor = thf;
           cur.cyc = sc.cyc;
         }
       }
@@ -285,9 +292,9 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
              if (t.cyc_mid_threads[c] == v) return false;
              t.cyc_mid_threads[c] = v;
              return true;
-           }, threads, 3)) != FGLT_OK) return s;
+           }, threads, 4)) != FGLT_OK) return s;
     if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_heavy_threads == v) return false; t.cyc_heavy_threads = v; return true; },
-                     threads + 1, 2)) != FGLT_OK) return s;
+                     threads + 2, 2)) != FGLT_OK) return s;
     if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_hub_span == v) return false; t.cyc_hub_span = v; return true; },
                      spans, 5)) != FGLT_OK) return s;
     // triangle candidates left over
@@ -296,6 +303,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
       run.tri_t0 = tri_c.back().tri_t0;
       run.tri_t1 = tri_c.back().tri_t1;
       run.tri_loads = tri_c.back().tri_loads;
+      run.tri_hash_factor = tri_c.back().tri_hash_factor;
       tri_c.pop_back();
       TuneScore sc;
       if ((s = time_once(h, g, st, run, reps, &sc)) != FGLT_OK) return s;
@@ -303,6 +311,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
         best.tri_t0 = run.tri_t0;
         best.tri_t1 = run.tri_t1;
         best.tri_loads = run.tri_loads;
+        best.tri_hash_factor = run.tri_hash_factor;
         cur.tri = sc.tri;
       }
     }

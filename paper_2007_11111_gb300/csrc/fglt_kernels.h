@@ -73,12 +73,13 @@ size_t scan_temp_bytes(int64_t n);
 cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t n, int64_t* out, void* temp, cudaStream_t st);
 
 // --- triangle passes (oriented, rank space) ---------------------------------
-// Per-block shared memory the triangle kernels need for a max out-degree.
-size_t tri1_smem_bytes(int dpmax, bool bitmap_in_smem);
-size_t tri2_smem_bytes(int dpmax);
-bool tri1_bitmap_fits_smem(int dpmax);
+// Per-block shared memory the triangle kernels need for a max out-degree (hf:
+// hash-table slots per element of N+(a), 2 or 4).
+size_t tri1_smem_bytes(int dpmax, bool bitmap_in_smem, int hf = 2);
+size_t tri2_smem_bytes(int dpmax, int hf = 2);
+bool tri1_bitmap_fits_smem(int dpmax, int hf = 2);
 // Largest out-degree whose adjacency bitmap fits in shared memory.
-int tri1_smem_bitmap_max();
+int tri1_smem_bitmap_max(int hf = 2);
 int tri_grid_blocks();
 // C3 per oriented edge, c3 per vertex, 4-clique count per vertex (only with
 // cliques = true). loads: list entries each lane has in flight per scan step
@@ -86,12 +87,12 @@ int tri_grid_blocks();
 // 4-cliques).
 cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm,
-                        u64* work_ctr, int* err, cudaStream_t st, bool cliques = true, int loads = 2);
-size_t tri1_gbm_bytes(int dpmax);
+                        u64* work_ctr, int* err, cudaStream_t st, bool cliques = true, int loads = 2, int hf = 2);
+size_t tri1_gbm_bytes(int dpmax, int hf = 2);
 // d^13 (diamond, off-cord) per vertex from the final C3.
 cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st,
-                        int loads = 2);
+                        int loads = 2, int hf = 2);
 // d^10 = C3 (p1 - 2) and d^14 = D4,3 e / 2 from the final C3 (rank space).
 cudaError_t launch_c3_edge_terms(const int64_t* orp, const int32_t* ocol, const int32_t* C3o,
                                  const int32_t* dr, int64_t n, u64* r10r, u64* r14r, cudaStream_t st);
@@ -143,7 +144,7 @@ struct CycArgs {
   int* next;              // CYC_CLASSES scheduling counters (zeroed)
   int32_t hub_lo;
   int wbits;              // warp-class table slots (log2, at most cyc_warp_bits_max())
-  int mid_threads[3];     // block sizes of the three hash-table classes (256, 512 or 1024)
+  int mid_threads[3];     // block sizes of the three hash-table classes (128 .. 1024)
   int heavy_threads;      // block size of the dense and global classes
   int gbits;              // global tables: cyc_gmem_blocks() << gbits slots each array
   uint32_t* gkeys;        // NULL when both global-table classes are empty

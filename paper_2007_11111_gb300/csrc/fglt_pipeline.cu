@@ -46,7 +46,7 @@ int bits_for(int64_t cap) {
   return hb;
 }
 
-bool pow2_threads(int t) { return t == 256 || t == 512 || t == 1024; }
+bool pow2_threads(int t) { return t == 128 || t == 256 || t == 512 || t == 1024; }
 
 }  // namespace
 
@@ -109,6 +109,8 @@ fglt_status tuning_from_options(const fglt_options& o, Tuning* t) {
   if (x.tri_t0 < 2 || x.tri_t1 <= x.tri_t0) return FGLT_ERR_INVALID_ARG;
   if (o.tri_probe_loads) x.tri_loads = o.tri_probe_loads;
   if (x.tri_loads != 2 && x.tri_loads != 4) return FGLT_ERR_INVALID_ARG;
+  if (o.tri_hash_factor) x.tri_hash_factor = o.tri_hash_factor;
+  if (x.tri_hash_factor != 2 && x.tri_hash_factor != 4) return FGLT_ERR_INVALID_ARG;
   if (o.cyc_warp_bits) x.cyc_warp_bits = o.cyc_warp_bits;
   if (x.cyc_warp_bits < 6 || x.cyc_warp_bits > cyc_warp_bits_max()) return FGLT_ERR_INVALID_ARG;
   for (int c = 0; c < 3; ++c) {
@@ -126,6 +128,7 @@ void tuning_to_options(const Tuning& t, fglt_options* o) {
   o->tri_class_bounds[0] = t.tri_t0;
   o->tri_class_bounds[1] = t.tri_t1;
   o->tri_probe_loads = t.tri_loads;
+  o->tri_hash_factor = t.tri_hash_factor;
   o->cyc_warp_bits = t.cyc_warp_bits;
   for (int c = 0; c < 3; ++c) o->cyc_mid_threads[c] = t.cyc_mid_threads[c];
   o->cyc_heavy_threads = t.cyc_heavy_threads;
@@ -299,7 +302,8 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   const int T0 = tu.tri_t0, T1 = tu.tri_t1;
   // The last class holds the vertices whose adjacency bitmap of the first
   // pass only fits in global memory.
-  const int T2 = std::max(T1, tri1_smem_bitmap_max());
+  const int HF = tu.tri_hash_factor;
+  const int T2 = std::max(T1, tri1_smem_bitmap_max(HF));
   int32_t* twork;
   NEED(B_TWORK, (int64_t)TRI_CLASSES * n, twork);
   CK(launch_worklist_outdeg4(opc, n, 2, T0, T1, T2, twork, n, cnt + C_NTRI0, st));
@@ -319,19 +323,19 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   uint32_t* gbm = nullptr;
   size_t gbm_need = 0;  // classes whose bitmap does not fit in shared memory share one buffer
   for (int c = 0; c < TRI_CLASSES; ++c)
-    if (tri_on[c]) gbm_need = std::max(gbm_need, tri1_gbm_bytes(tri_cap[c]));
+    if (tri_on[c]) gbm_need = std::max(gbm_need, tri1_gbm_bytes(tri_cap[c], HF));
   if (size_t gb = gbm_need) {
     unsigned char* p = nullptr;
     NEED(B_GBM, (int64_t)gb, p);
     gbm = reinterpret_cast<uint32_t*>(p);
   }
-  if (dpmax >= 2 && tri2_smem_bytes(dpmax) > 227 * 1024) return FGLT_ERR_UNSUPPORTED;
+  if (dpmax >= 2 && tri2_smem_bytes(dpmax, HF) > 227 * 1024) return FGLT_ERR_UNSUPPORTED;
   for (int c = 0; c < TRI_CLASSES; ++c)
     if (tri_on[c] && need_tri1) {
       sub(CYC_CLASSES + c, 0);
       CK(launch_tri1(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT1_0 + c, tri_cap[c], C3o, c3r, k4r,
-                     tri1_gbm_bytes(tri_cap[c]) ? gbm : nullptr, ctr + W_PROBES, err, st, need_k4,
-                     tu.tri_loads));
+                     tri1_gbm_bytes(tri_cap[c], HF) ? gbm : nullptr, ctr + W_PROBES, err, st, need_k4,
+                     tu.tri_loads, HF));
       sub(CYC_CLASSES + c, 1);
     }
 
@@ -366,7 +370,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
     if (tri_on[c] && need_tri2) {
       sub(CYC_CLASSES + TRI_CLASSES + c, 0);
       CK(launch_tri2(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT2_0 + c, tri_cap[c], C3o, r13r, err,
-                     st, tu.tri_loads));
+                     st, tu.tri_loads, HF));
       sub(CYC_CLASSES + TRI_CLASSES + c, 1);
     }
 

@@ -739,7 +739,8 @@ template <int MODE>
 void launch_block_bt(const CycArgs& a, int cls, int tbits, int dense_words, int bt, cudaStream_t st) {
   if (bt >= 1024) launch_block<MODE, 1024>(a, cls, tbits, dense_words, st);
   else if (bt >= 512) launch_block<MODE, 512>(a, cls, tbits, dense_words, st);
-  else launch_block<MODE, 256>(a, cls, tbits, dense_words, st);
+  else if (bt >= 256) launch_block<MODE, 256>(a, cls, tbits, dense_words, st);
+  else launch_block<MODE, 128>(a, cls, tbits, dense_words, st);
 }
 
 }  // namespace

@@ -26,9 +26,10 @@ namespace {
 constexpr int TRI_T = 256;
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
-int hash_bits_for(int D) {
+// Hash table of N+(a): hf slots per element (2 or 4), a power of two.
+int hash_bits_for(int D, int hf) {
   int hb = 5;
-  while ((1 << hb) < 2 * D) ++hb;
+  while ((1 << hb) < hf * D) ++hb;
   return hb;
 }
 
@@ -118,7 +119,8 @@ __device__ __forceinline__ void scan_sorted(const int32_t* __restrict__ ocol, in
 template <bool SMEM_BM, bool K4, int PL>
 __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
                                                 const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
-                                                int* next, int Dmax, int Hbits, int32_t* C3o, u64* c3r, u64* k4r,
+                                                int* next, int Dmax, int Hbits, int hf, int32_t* C3o, u64* c3r,
+                                                u64* k4r,
                                                 uint32_t* gbm, u64* work_ctr, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
     const int64_t base = orp[a];
     const int D = (int)(orp[a + 1] - base);
     int hb = 5;
-    while ((1 << hb) < 2 * D) ++hb;
+    while ((1 << hb) < hf * D) ++hb;
     const int fb = filter_bits_for(D);
     const int W = (D + 31) >> 5;
 
@@ -280,7 +282,8 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
 template <int PL>
 __global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
                                                 const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
-                                                int* next, int Dmax, int Hbits, const int32_t* __restrict__ C3o,
+                                                int* next, int Dmax, int Hbits, int hf,
+                                                const int32_t* __restrict__ C3o,
                                                 u64* r13r, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
@@ -303,7 +306,7 @@ __global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp,
     const int64_t base = orp[a];
     const int D = (int)(orp[a + 1] - base);
     int hb = 5;
-    while ((1 << hb) < 2 * D) ++hb;
+    while ((1 << hb) < hf * D) ++hb;
     const int fb = filter_bits_for(D);
 
     for (int i = tid; i < (1 << hb); i += blockDim.x) keys[i] = EMPTY_KEY;
@@ -353,8 +356,8 @@ int host_filter_words(int D) {
   return (1 << fb) >> 5;
 }
 
-size_t tri1_smem_impl(int D, bool smem_bm) {
-  const int H = 1 << hash_bits_for(D);
+size_t tri1_smem_impl(int D, bool smem_bm, int hf) {
+  const int H = 1 << hash_bits_for(D, hf);
   const size_t W = (size_t)(D + 31) / 32;
   size_t bytes = (size_t)H * 8 + (size_t)host_filter_words(D) * 4 + (size_t)(TRI_T / 32) * (D + W) * 4;
   bytes += (size_t)D * 4;  // per-vertex 4-clique tallies
@@ -371,21 +374,21 @@ int occupancy_grid(const void* fn, size_t smem) {
 
 }  // namespace
 
-bool tri1_bitmap_fits_smem(int dpmax) { return tri1_smem_impl(dpmax, true) <= SMEM_LIMIT - 1024; }
+bool tri1_bitmap_fits_smem(int dpmax, int hf) { return tri1_smem_impl(dpmax, true, hf) <= SMEM_LIMIT - 1024; }
 
-int tri1_smem_bitmap_max() {
+int tri1_smem_bitmap_max(int hf) {
   int lo = 2, hi = 1 << 14;  // fits(lo), !fits(hi)
   while (hi - lo > 1) {
     const int mid = (lo + hi) / 2;
-    if (tri1_bitmap_fits_smem(mid)) lo = mid; else hi = mid;
+    if (tri1_bitmap_fits_smem(mid, hf)) lo = mid; else hi = mid;
   }
   return lo;
 }
 
-size_t tri1_smem_bytes(int dpmax, bool bitmap_in_smem) { return tri1_smem_impl(dpmax, bitmap_in_smem); }
+size_t tri1_smem_bytes(int dpmax, bool bitmap_in_smem, int hf) { return tri1_smem_impl(dpmax, bitmap_in_smem, hf); }
 
-size_t tri2_smem_bytes(int dpmax) {
-  const int H = 1 << hash_bits_for(dpmax);
+size_t tri2_smem_bytes(int dpmax, int hf) {
+  const int H = 1 << hash_bits_for(dpmax, hf);
   return (((size_t)dpmax * 12 + (size_t)H * 8 + (size_t)host_filter_words(dpmax) * 4) + 15) & ~(size_t)15;
 }
 
@@ -399,8 +402,8 @@ void allow_tri1() {
   allow_max_smem(k_tri1<SMEM_BM, false, 4>);
 }
 
-static int tri1_grid(int dpmax, bool smem_bm) {
-  const size_t smem = tri1_smem_impl(dpmax, smem_bm);
+static int tri1_grid(int dpmax, bool smem_bm, int hf) {
+  const size_t smem = tri1_smem_impl(dpmax, smem_bm, hf);
   if (smem_bm) {
     allow_tri1<true>();
     return occupancy_grid((const void*)k_tri1<true, true, 2>, smem);
@@ -409,40 +412,41 @@ static int tri1_grid(int dpmax, bool smem_bm) {
   return occupancy_grid((const void*)k_tri1<false, true, 2>, smem);
 }
 
-size_t tri1_gbm_bytes(int dpmax) {
-  if (dpmax < 2 || tri1_bitmap_fits_smem(dpmax)) return 0;
+size_t tri1_gbm_bytes(int dpmax, int hf) {
+  if (dpmax < 2 || tri1_bitmap_fits_smem(dpmax, hf)) return 0;
   const size_t W = (size_t)(dpmax + 31) / 32;
-  return (size_t)tri1_grid(dpmax, false) * (size_t)dpmax * W * 4;
+  return (size_t)tri1_grid(dpmax, false, hf) * (size_t)dpmax * W * 4;
 }
 
 cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm, u64* work_ctr,
-                        int* err, cudaStream_t st, bool cliques, int loads) {
+                        int* err, cudaStream_t st, bool cliques, int loads, int hf) {
   if (dpmax < 2) return cudaSuccess;
-  const bool smem_bm = tri1_bitmap_fits_smem(dpmax);
-  const size_t smem = tri1_smem_impl(dpmax, smem_bm);
-  const int grid = tri1_grid(dpmax, smem_bm);
-  const int hb = hash_bits_for(dpmax);
+  const bool smem_bm = tri1_bitmap_fits_smem(dpmax, hf);
+  const size_t smem = tri1_smem_impl(dpmax, smem_bm, hf);
+  const int grid = tri1_grid(dpmax, smem_bm, hf);
+  const int hb = hash_bits_for(dpmax, hf);
   auto* fn = loads >= 4 ? (smem_bm ? (cliques ? k_tri1<true, true, 4> : k_tri1<true, false, 4>)
                                    : (cliques ? k_tri1<false, true, 4> : k_tri1<false, false, 4>))
                         : (smem_bm ? (cliques ? k_tri1<true, true, 2> : k_tri1<true, false, 2>)
                                    : (cliques ? k_tri1<false, true, 2> : k_tri1<false, false, 2>));
-  fn<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, C3o, c3r, k4r, smem_bm ? nullptr : gbm,
+  fn<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, hf, C3o, c3r, k4r, smem_bm ? nullptr : gbm,
                                 work_ctr, err);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
-                        int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st, int loads) {
+                        int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st, int loads,
+                        int hf) {
   if (dpmax < 2) return cudaSuccess;
-  const size_t smem = tri2_smem_bytes(dpmax);
+  const size_t smem = tri2_smem_bytes(dpmax, hf);
   if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
   auto* fn = loads >= 4 ? k_tri2<4> : k_tri2<2>;
   allow_max_smem(k_tri2<2>);
   allow_max_smem(k_tri2<4>);
   const int grid = occupancy_grid((const void*)fn, smem);
-  fn<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hash_bits_for(dpmax), C3o, r13r, err);
+  fn<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hash_bits_for(dpmax, hf), hf, C3o, r13r, err);
   note_launch();
   return cudaGetLastError();
 }

@@ -16,11 +16,11 @@ torch = pytest.importorskip("torch")
 SETTINGS = [
     dict(),
     dict(tri_class_bounds=(2, 3)),
-    dict(tri_class_bounds=(8, 1024), tri_probe_loads=4),
+    dict(tri_class_bounds=(8, 1024), tri_probe_loads=4, tri_hash_factor=4),
     dict(tri_class_bounds=(3, 2000), tri_probe_loads=4),
     dict(cyc_warp_bits=6),
     dict(cyc_warp_bits=8, cyc_mid_threads=(512, 1024, 512)),
-    dict(cyc_mid_threads=(1024, 256, 1024), cyc_heavy_threads=256),
+    dict(cyc_mid_threads=(1024, 128, 1024), cyc_heavy_threads=256, tri_hash_factor=4),
     dict(cyc_heavy_threads=512, cyc_hub_span=64),
     dict(cyc_hub_span=1, cyc_warp_bits=7, tri_class_bounds=(16, 32)),
 ]
@@ -66,7 +66,8 @@ def test_invalid_settings_rejected():
         pytest.skip("no CUDA device")
     for bad in (dict(tri_class_bounds=(64, 32)), dict(tri_class_bounds=(1, 8)), dict(cyc_warp_bits=11),
                 dict(cyc_warp_bits=5), dict(cyc_mid_threads=(128, 256, 256)), dict(cyc_heavy_threads=300),
-                dict(cyc_hub_span=-1), dict(cyc_hub_span=90113), dict(tri_probe_loads=3)):
+                dict(cyc_hub_span=-1), dict(cyc_hub_span=90113), dict(tri_probe_loads=3),
+                dict(tri_hash_factor=3), dict(cyc_mid_threads=(64, 256, 256))):
         with pytest.raises(fg.FgltError) as e:
             fg.Handle(device=0, **bad)
         assert e.value.status == fg.FGLT_ERR_INVALID_ARG
@@ -86,7 +87,8 @@ def test_autotune_installs_setting_and_keeps_results(cases):
         t0, t1 = chosen["tri_class_bounds"]
         assert 2 <= t0 < t1
         assert 6 <= chosen["cyc_warp_bits"] <= 10
-        assert all(x in (256, 512, 1024) for x in chosen["cyc_mid_threads"])
+        assert all(x in (128, 256, 512, 1024) for x in chosen["cyc_mid_threads"])
+        assert chosen["tri_hash_factor"] in (2, 4) and chosen["tri_probe_loads"] in (2, 4)
         assert chosen["cyc_heavy_threads"] in (256, 512, 1024)
         # results under the installed setting, on this graph and on another
         for gg_, (wr, wn) in (cases[0], cases[1]):
@@ -95,7 +97,7 @@ def test_autotune_installs_setting_and_keeps_results(cases):
             np.testing.assert_array_equal(net, wn)
         # a fresh handle created with the chosen setting gives the same counts
         kw = dict(tri_class_bounds=tuple(chosen["tri_class_bounds"]), cyc_warp_bits=chosen["cyc_warp_bits"],
-                  tri_probe_loads=chosen["tri_probe_loads"],
+                  tri_probe_loads=chosen["tri_probe_loads"], tri_hash_factor=chosen["tri_hash_factor"],
                   cyc_mid_threads=tuple(chosen["cyc_mid_threads"]), cyc_heavy_threads=chosen["cyc_heavy_threads"],
                   cyc_hub_span=chosen["cyc_hub_span"])
         with fg.Handle(device=0, **kw) as h2:

@@ -44,7 +44,8 @@ def test_noalloc_matches_transform_on_consecutive_calls():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     graphs = [gg.rmat(13, 16, seed=31), gg.erdos_renyi(2000, 10, seed=0), gg.rmat(13, 16, seed=31),
-              gg.barabasi_albert(3000, 5, seed=2)]
+              gg.barabasi_albert(3000, 5, seed=2),
+              gg.rmat(15, 16, seed=5)]  # 32768 vertices, ~880K stored entries: near both limits
     with fg.Handle(device=0) as h:
         for k, g in enumerate(graphs):
             want_raw, want_net = _reference(h, g)
