@@ -65,7 +65,7 @@ def test_invalid_settings_rejected():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     for bad in (dict(tri_class_bounds=(64, 32)), dict(tri_class_bounds=(1, 8)), dict(cyc_warp_bits=11),
-                dict(cyc_warp_bits=5), dict(cyc_mid_threads=(128, 256, 256)), dict(cyc_heavy_threads=300),
+                dict(cyc_warp_bits=5), dict(cyc_mid_threads=(96, 256, 256)), dict(cyc_heavy_threads=300),
                 dict(cyc_hub_span=-1), dict(cyc_hub_span=90113), dict(tri_probe_loads=3),
                 dict(tri_hash_factor=3), dict(cyc_mid_threads=(64, 256, 256))):
         with pytest.raises(fg.FgltError) as e:
