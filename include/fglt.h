@@ -88,16 +88,16 @@ typedef struct {
     int cyc_hub_span;
     /* tri_class_bounds: the triangle passes split the vertices by out-degree
      *   d+ in the degree order into (2, t0], (t0, t1], (t1, ...), each launched
-     *   with shared memory sized for its largest d+ (default 64, 256;
+     *   with shared memory sized for its largest d+ (default 128, 512;
      *   2 <= t0 < t1). */
     int tri_class_bounds[2];
     /* tri_probe_loads: list entries each lane of the triangle passes keeps in
-     *   flight per scan step, 2 or 4 (default 2): more hides more memory
+     *   flight per scan step, 2 or 4 (default 4): more hides more memory
      *   latency, at the cost of scanning up to 32 * loads entries past the end
      *   of a scan. */
     int tri_probe_loads;
     /* tri_hash_factor: slots per element of the shared-memory hash table of
-     *   N+(a) in the triangle passes, 2 or 4 (default 2): 4 shortens the probe
+     *   N+(a) in the triangle passes, 2 or 4 (default 4): 4 shortens the probe
      *   runs that every lane of a warp waits for, at twice the table memory. */
     int tri_hash_factor;
     /* cyc_warp_bits: log2 of the per-warp hash-table slots of the 4-cycle
@@ -270,7 +270,7 @@ fglt_status fglt_work_counters(fglt_t handle, int64_t* counters, int max_counter
  *   Scratch: one file-scope device array of FGLT_NOALLOC_SCRATCH_BYTES held by
  *   every device that loads the library until exit. Limits: n <=
  *   FGLT_NOALLOC_MAX_VERTICES, rowptr[n] <= FGLT_NOALLOC_MAX_ENTRIES, and a
- *   largest out-degree in the degree order of about 1100 (the triangle pass's
+ *   largest out-degree in the degree order of about 1000 (the triangle pass's
  *   shared-memory bitmap); larger inputs return FGLT_ERR_UNSUPPORTED.
  *   The first call on each device looks up the array's address; make it before
  *   any stream capture. All calls share the array and each leaves its data

@@ -228,8 +228,8 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
     if ((s = time_once(h, g, st, start, reps, &base)) != FGLT_OK) return s;
     // Candidate values per parameter, tried one parameter at a time.
     // triangle candidates: class bounds t0, t1, loads in flight, hash slots per element
-    const int t_bounds[][4] = {{32, 128, 2, 2}, {64, 256, 4, 2}, {128, 512, 2, 2}, {32, 256, 4, 4},
-                               {64, 1024, 2, 2}, {64, 256, 2, 4}, {64, 256, 4, 4}, {128, 512, 4, 4}};
+    const int t_bounds[][4] = {{32, 128, 4, 4}, {64, 256, 4, 4}, {128, 512, 2, 4}, {128, 512, 4, 2},
+                               {64, 1024, 4, 4}, {256, 768, 4, 4}, {128, 384, 4, 4}, {64, 256, 2, 2}};
     const int wbits[] = {8, 9, 10};
     const int spans[] = {0, 16384, 32768, 65536, 90112};
     const int threads[] = {128, 256, 512, 1024};

@@ -14,7 +14,7 @@
 // FGLT_NOALLOC_MAX_VERTICES and rowptr[n] <= FGLT_NOALLOC_MAX_ENTRIES, checked
 // before any device work; every buffer of the stage sequence must fit in the
 // array, checked as the sequence carves them (a largest out-degree in the
-// degree order above about 1100 needs a global-memory bitmap that does not).
+// degree order above about 1000 needs a global-memory bitmap that does not).
 // Every device that loads the library holds the array until the process
 // exits.
 //

@@ -43,9 +43,9 @@ extern const char* const SUB_NAMES[NUM_SUB];
 
 // Tunables; the counts never depend on them (fglt_options documents each).
 struct Tuning {
-  int tri_t0 = 64, tri_t1 = 256;
-  int tri_loads = 2;
-  int tri_hash_factor = 2;
+  int tri_t0 = 128, tri_t1 = 512;
+  int tri_loads = 4;
+  int tri_hash_factor = 4;
   int cyc_warp_bits = 10;
   int cyc_mid_threads[3] = {256, 256, 256};
   int cyc_heavy_threads = 1024;

@@ -199,15 +199,19 @@ __device__ __forceinline__ void walk_group(const Group& g, const int32_t* __rest
 
 // Sum of x over the lanes of each run of equal owners j (owners are
 // non-decreasing over the lanes); the first lane of a run gets the run total.
-__device__ __forceinline__ u64 run_sum(u64 x, int j, bool& head) {
+// 32 bits suffice: one credit is below the degree limit of the library
+// (2^21) and a run spans at most 32 lanes.
+__device__ __forceinline__ uint32_t run_sum(uint32_t x, int j, bool& head) {
   const int lane = threadIdx.x & 31;
   const int jp = __shfl_up_sync(0xffffffffu, j, 1);
   head = lane == 0 || jp != j;
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const unsigned after = lane == 31 ? 0u : (heads >> (lane + 1));  // run heads after this lane
+  const int end = after ? lane + __ffs(after) - 1 : 31;            // last lane of this run
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const u64 y = __shfl_down_sync(0xffffffffu, x, o);
-    const int jy = __shfl_down_sync(0xffffffffu, j, o);
-    if (lane + o < 32 && jy == j) x += y;
+    const uint32_t y = __shfl_down_sync(0xffffffffu, x, o);
+    if (lane + o <= end) x += y;
   }
   return x;
 }
@@ -261,8 +265,8 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const int64_t* __restrict__
           c = c > 1 ? c - 1 : 0;
         }
         bool head;
-        const u64 sum = run_sum(c, valid ? j : -1, head);
-        if (head && valid && sum) atomicAdd(&acc[j], sum);
+        const uint32_t sum = run_sum((uint32_t)c, valid ? j : -1, head);
+        if (head && valid && sum) atomicAdd(&acc[j], (u64)sum);
       });
       __syncwarp();
       if (acc[lane]) {
@@ -556,8 +560,8 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
       walk_chunk(S, ocol, [&](uint32_t u, int j, bool valid) {
         const u64 c = valid ? credit(u) : 0;
         bool head;
-        const u64 sum = run_sum(c, valid ? j : -1, head);
-        if (head && valid && sum) atomicAdd(&S.acc[j], sum);
+        const uint32_t sum = run_sum((uint32_t)c, valid ? j : -1, head);
+        if (head && valid && sum) atomicAdd(&S.acc[j], (u64)sum);
       });
       __syncthreads();
       const int ns = S.misc[0];

@@ -329,9 +329,10 @@ __global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp,
       long long accb = 0;
       auto probe = [&](int32_t c, int64_t k) {
         if (c <= lastA && filter_test(filt, (uint32_t)c, fb)) {
+          const int32_t c3bc = C3o[k];  // issued before the table probe so that the two overlap
           const int ic = table_find(keys, vals, (uint32_t)c, hb);
           if (ic >= 0) {
-            acc_a += (long long)C3o[k] - 1;  // a: opposite edge b-c
+            acc_a += (long long)c3bc - 1;  // a: opposite edge b-c
             accb += (long long)tv[ic] - 1;   // b: opposite edge a-c
             if (tab > 1) atomicAdd(&acc[ic], (u64)(tab - 1));  // c: opposite edge a-b
           }
