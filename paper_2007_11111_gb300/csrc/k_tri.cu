@@ -23,7 +23,8 @@ namespace fglt {
 
 namespace {
 
-constexpr int TRI_T = 256;
+constexpr int TRI_T = 256;       // block size of the classes whose bitmap fits in shared memory
+constexpr int TRI_T_BIG = 1024;  // block size of the class with the global-memory bitmap
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 // Hash table of N+(a): hf slots per element (2 or 4), a power of two.
@@ -117,7 +118,7 @@ __device__ __forceinline__ void scan_sorted(const int32_t* __restrict__ ocol, in
 // and a's own counts are the sums over x divided by 2 and 6.
 // ---------------------------------------------------------------------------
 template <bool SMEM_BM, bool K4, int PL>
-__global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+__global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
                                                 const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
                                                 int* next, int Dmax, int Hbits, int hf, int32_t* C3o, u64* c3r,
                                                 u64* k4r,
@@ -131,12 +132,24 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
   uint32_t* keys = reinterpret_cast<uint32_t*>(smem);
   int32_t* vals = reinterpret_cast<int32_t*>(keys + Hmax);
   uint32_t* filt = reinterpret_cast<uint32_t*>(vals + Hmax);
-  int32_t* ylist = reinterpret_cast<int32_t*>(filt + FWmax) + warp * (Dmax + Wmax);
+  // Shared-memory bitmap: [per-warp lists][bitmap][tallies] in shared memory.
+  // Otherwise the bitmap and the per-warp lists live in this block's slot of
+  // gbm and the tallies in shared memory.
+  int32_t* lists_base;
+  uint32_t* bm;
+  uint32_t* k2loc;  // [Dmax] per-vertex 4-clique tallies
+  if (SMEM_BM) {
+    lists_base = reinterpret_cast<int32_t*>(filt + FWmax);
+    bm = reinterpret_cast<uint32_t*>(lists_base + nwarps * (Dmax + Wmax));
+    k2loc = bm + (size_t)Dmax * Wmax;
+  } else {
+    uint32_t* slot = gbm + (size_t)blockIdx.x * ((size_t)Dmax * Wmax + (size_t)nwarps * (Dmax + Wmax));
+    bm = slot;
+    lists_base = reinterpret_cast<int32_t*>(slot + (size_t)Dmax * Wmax);
+    k2loc = filt + FWmax;
+  }
+  int32_t* ylist = lists_base + warp * (Dmax + Wmax);
   int32_t* wlist = ylist + Dmax;
-  uint32_t* after_lists = reinterpret_cast<uint32_t*>(reinterpret_cast<int32_t*>(filt + FWmax) +
-                                                      nwarps * (Dmax + Wmax));
-  uint32_t* bm = SMEM_BM ? after_lists : (gbm + (size_t)blockIdx.x * Dmax * Wmax);
-  uint32_t* k2loc = SMEM_BM ? after_lists + (size_t)Dmax * Wmax : after_lists;  // [Dmax]
   const int total = *nwork;
   const unsigned below = (1u << lane) - 1u;
 
@@ -279,8 +292,8 @@ __global__ void __launch_bounds__(TRI_T) k_tri1(const int64_t* __restrict__ orp,
 // ---------------------------------------------------------------------------
 // Pass 2
 // ---------------------------------------------------------------------------
-template <int PL>
-__global__ void __launch_bounds__(TRI_T) k_tri2(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+template <int PL, int BT>
+__global__ void __launch_bounds__(BT) k_tri2(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
                                                 const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
                                                 int* next, int Dmax, int Hbits, int hf,
                                                 const int32_t* __restrict__ C3o,
@@ -360,15 +373,15 @@ int host_filter_words(int D) {
 size_t tri1_smem_impl(int D, bool smem_bm, int hf) {
   const int H = 1 << hash_bits_for(D, hf);
   const size_t W = (size_t)(D + 31) / 32;
-  size_t bytes = (size_t)H * 8 + (size_t)host_filter_words(D) * 4 + (size_t)(TRI_T / 32) * (D + W) * 4;
+  size_t bytes = (size_t)H * 8 + (size_t)host_filter_words(D) * 4;
   bytes += (size_t)D * 4;  // per-vertex 4-clique tallies
-  if (smem_bm) bytes += (size_t)D * W * 4;
+  if (smem_bm) bytes += (size_t)(TRI_T / 32) * (D + W) * 4 + (size_t)D * W * 4;  // lists and bitmap
   return (bytes + 15) & ~(size_t)15;
 }
 
-int occupancy_grid(const void* fn, size_t smem) {
+int occupancy_grid(const void* fn, size_t smem, int threads = TRI_T) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TRI_T, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
   if (per_sm < 1) per_sm = 1;
   return per_sm * num_sms();
 }
@@ -410,13 +423,14 @@ static int tri1_grid(int dpmax, bool smem_bm, int hf) {
     return occupancy_grid((const void*)k_tri1<true, true, 2>, smem);
   }
   allow_tri1<false>();
-  return occupancy_grid((const void*)k_tri1<false, true, 2>, smem);
+  return occupancy_grid((const void*)k_tri1<false, true, 2>, smem, TRI_T_BIG);
 }
 
 size_t tri1_gbm_bytes(int dpmax, int hf) {
   if (dpmax < 2 || tri1_bitmap_fits_smem(dpmax, hf)) return 0;
   const size_t W = (size_t)(dpmax + 31) / 32;
-  return (size_t)tri1_grid(dpmax, false, hf) * (size_t)dpmax * W * 4;
+  const size_t per_block = (size_t)dpmax * W + (size_t)(TRI_T_BIG / 32) * ((size_t)dpmax + W);  // bitmap + lists
+  return (size_t)tri1_grid(dpmax, false, hf) * per_block * 4;
 }
 
 cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
@@ -431,8 +445,8 @@ cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* 
                                    : (cliques ? k_tri1<false, true, 4> : k_tri1<false, false, 4>))
                         : (smem_bm ? (cliques ? k_tri1<true, true, 2> : k_tri1<true, false, 2>)
                                    : (cliques ? k_tri1<false, true, 2> : k_tri1<false, false, 2>));
-  fn<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, hf, C3o, c3r, k4r, smem_bm ? nullptr : gbm,
-                                work_ctr, err);
+  fn<<<grid, smem_bm ? TRI_T : TRI_T_BIG, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, hf, C3o, c3r, k4r,
+                                                     smem_bm ? nullptr : gbm, work_ctr, err);
   note_launch();
   return cudaGetLastError();
 }
@@ -443,11 +457,15 @@ cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* 
   if (dpmax < 2) return cudaSuccess;
   const size_t smem = tri2_smem_bytes(dpmax, hf);
   if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
-  auto* fn = loads >= 4 ? k_tri2<4> : k_tri2<2>;
-  allow_max_smem(k_tri2<2>);
-  allow_max_smem(k_tri2<4>);
-  const int grid = occupancy_grid((const void*)fn, smem);
-  fn<<<grid, TRI_T, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hash_bits_for(dpmax, hf), hf, C3o, r13r, err);
+  // the out-degree class beyond the shared-memory bitmap of pass 1 runs with
+  // 1024-thread blocks (its tables allow one block per SM)
+  const bool big = !tri1_bitmap_fits_smem(dpmax, hf);
+  auto* fn = big ? (loads >= 4 ? k_tri2<4, TRI_T_BIG> : k_tri2<2, TRI_T_BIG>)
+                 : (loads >= 4 ? k_tri2<4, TRI_T> : k_tri2<2, TRI_T>);
+  allow_max_smem(fn);
+  const int threads = big ? TRI_T_BIG : TRI_T;
+  const int grid = occupancy_grid((const void*)fn, smem, threads);
+  fn<<<grid, threads, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hash_bits_for(dpmax, hf), hf, C3o, r13r, err);
   note_launch();
   return cudaGetLastError();
 }
