@@ -30,6 +30,7 @@ const char* const SUB_NAMES[NUM_SUB] = {"cyc.warp",    "cyc.hash11",      "cyc.h
 namespace {
 
 constexpr int64_t MAX_DEGREE_EXACT = 2097151;  // binom(d,3) products stay inside int64
+constexpr size_t TRI_SMEM_LIMIT = 225 * 1024;  // dynamic shared memory a triangle-pass block may ask for
 
 // Small device counters, one int slot each.
 enum CounterId {
@@ -320,22 +321,35 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   CK(cudaMemsetAsync(C3o, 0, (size_t)std::max<int64_t>(m_or, 1) * sizeof(int32_t), st));
   CK(cudaMemsetAsync(c3r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
   CK(cudaMemsetAsync(k4r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
+  // Hash-table slots per element, per class: the tuned value where both
+  // passes' shared memory fits, else 2; a class that fits with neither is
+  // outside what this build supports.
+  int tri_hf[TRI_CLASSES];
+  for (int c = 0; c < TRI_CLASSES; ++c) {
+    tri_hf[c] = HF;
+    if (!tri_on[c]) continue;
+    auto fits = [&](int hf) {
+      return tri1_smem_bytes(tri_cap[c], tri1_bitmap_fits_smem(tri_cap[c], hf), hf) <= TRI_SMEM_LIMIT &&
+             tri2_smem_bytes(tri_cap[c], hf) <= TRI_SMEM_LIMIT;
+    };
+    if (!fits(tri_hf[c])) tri_hf[c] = 2;
+    if (!fits(tri_hf[c])) return FGLT_ERR_UNSUPPORTED;
+  }
   uint32_t* gbm = nullptr;
   size_t gbm_need = 0;  // classes whose bitmap does not fit in shared memory share one buffer
   for (int c = 0; c < TRI_CLASSES; ++c)
-    if (tri_on[c]) gbm_need = std::max(gbm_need, tri1_gbm_bytes(tri_cap[c], HF));
+    if (tri_on[c]) gbm_need = std::max(gbm_need, tri1_gbm_bytes(tri_cap[c], tri_hf[c]));
   if (size_t gb = gbm_need) {
     unsigned char* p = nullptr;
     NEED(B_GBM, (int64_t)gb, p);
     gbm = reinterpret_cast<uint32_t*>(p);
   }
-  if (dpmax >= 2 && tri2_smem_bytes(dpmax, HF) > 227 * 1024) return FGLT_ERR_UNSUPPORTED;
   for (int c = 0; c < TRI_CLASSES; ++c)
     if (tri_on[c] && need_tri1) {
       sub(CYC_CLASSES + c, 0);
       CK(launch_tri1(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT1_0 + c, tri_cap[c], C3o, c3r, k4r,
-                     tri1_gbm_bytes(tri_cap[c], HF) ? gbm : nullptr, ctr + W_PROBES, err, st, need_k4,
-                     tu.tri_loads, HF));
+                     tri1_gbm_bytes(tri_cap[c], tri_hf[c]) ? gbm : nullptr, ctr + W_PROBES, err, st, need_k4,
+                     tu.tri_loads, tri_hf[c]));
       sub(CYC_CLASSES + c, 1);
     }
 
@@ -370,7 +384,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
     if (tri_on[c] && need_tri2) {
       sub(CYC_CLASSES + TRI_CLASSES + c, 0);
       CK(launch_tri2(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT2_0 + c, tri_cap[c], C3o, r13r, err,
-                     st, tu.tri_loads, HF));
+                     st, tu.tri_loads, tri_hf[c]));
       sub(CYC_CLASSES + TRI_CLASSES + c, 1);
     }
 

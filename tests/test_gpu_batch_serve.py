@@ -150,3 +150,21 @@ def test_served_budget_and_cancel(fg):
             assert fg.fglt_stream_poll(h.h, ids[-1], 0)[0] == fg.FGLT_ERR_NOT_FOUND
         else:
             assert fg.fglt_stream_poll(h.h, ids[-1], 60000)[0] == fg.FGLT_OK
+
+
+@pytest.mark.parametrize("hash_factor", [2, 4])
+def test_batched_with_a_4096_vertex_member(fg, hash_factor):
+    """A batch whose largest graph has 4096 vertices: the host-side bounds put
+    the degree and out-degree bounds at 4095, so every triangle class up to
+    the global-bitmap one is sized for that bound (both hash-table sizes)."""
+    graphs = [gg.rmat(12, 8, seed=3), gg.barabasi_albert(300, 3, seed=1), gg.complete(40), gg.cycle(9)]
+    batch = gg.pack_block_diagonal(graphs)
+    oraw, onet = oracle.fglt(batch.graph)
+    dev = torch.device("cuda:0")
+    rp = torch.from_numpy(batch.graph.rowptr).to(dev)
+    ci = torch.from_numpy(batch.graph.colidx).to(dev)
+    with fg.Handle(device=0, tri_hash_factor=hash_factor) as h:
+        for _ in range(2):  # captured run, then replay
+            raw, net = h.transform_batched(rp, ci, batch.offsets)
+            np.testing.assert_array_equal(raw.cpu().numpy(), oraw)
+            np.testing.assert_array_equal(net.cpu().numpy(), onet)
