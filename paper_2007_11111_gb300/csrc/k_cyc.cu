@@ -232,6 +232,10 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const int64_t* __restrict__
   uint32_t* tables = reinterpret_cast<uint32_t*>(reinterpret_cast<u64*>(smem) + (WARP_T / 32) * 32);
   Table<false> T{tables + (size_t)warp * 2 * WH, tables + (size_t)warp * 2 * WH + WH};
   const int total = *cnt;
+  // The table starts empty; pass C empties every slot it reads, so each
+  // vertex finds it empty again.
+  for (uint32_t i = lane; i < WH; i += 32) T.clear(i);
+  __syncwarp();
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(next, 1);
@@ -245,7 +249,6 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const int64_t* __restrict__
     while ((1LL << hb) < 2 * cap) ++hb;
     if (hb > wbits) hb = wbits;  // the class guarantees 2 * cap <= 2^wbits
     const uint32_t H = 1u << hb;
-    for (uint32_t i = lane; i < H; i += 32) T.clear(i);
     acc[lane] = 0;
     __syncwarp();
     const Mids M = mids_of(orp, ocol, irp, iin, w);
@@ -285,6 +288,7 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const int64_t* __restrict__
           atomicAdd(&r12r[key], v);
           accw += v;
         }
+        T.clear(i);
       }
     }
     accw = warp_sum_u64(accw);
@@ -501,6 +505,13 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
     return (dense[i >> 1] >> ((i & 1u) << 4)) & 0xFFFFu;
   };
 
+  // Shared-memory tables and the dense window start empty; pass C empties
+  // what it reads, so each vertex finds them empty again. Global tables are
+  // cleared per vertex (only the part the vertex uses).
+  if (!GMEM)
+    for (uint32_t i = tid; i < (1u << tbits); i += blockDim.x) T.clear(i);
+  if (DENSE)
+    for (int i = tid; i < (hub_n + 1) >> 1; i += blockDim.x) dense[i] = 0u;
   for (;;) {
     if (tid == 0) s_item = atomicAdd(next, 1);
     __syncthreads();
@@ -519,12 +530,10 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
       if (hb > tbits) hb = tbits;  // the class (or the table sizing) guarantees 2 * cap <= 2^tbits
     }
     const uint32_t H = 1u << hb;
-    if (DENSE) {
-      const int words = (hub_n + 1) >> 1;
-      for (int i = tid; i < words; i += blockDim.x) dense[i] = 0u;
+    if (GMEM) {
+      for (uint32_t i = tid; i < H; i += blockDim.x) T.clear(i);
+      __syncthreads();
     }
-    for (uint32_t i = tid; i < H; i += blockDim.x) T.clear(i);
-    __syncthreads();
 
     const Mids M = mids_of(orp, ocol, irp, iin, w);
     const bool single = M.K <= CH;
@@ -572,12 +581,19 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
     // Pass C: top u and bottom w gain binom(cnt[u], 2).
     u64 accw = 0;
     if (DENSE) {
-      for (int i = tid; i < hub_n; i += blockDim.x) {
-        const u64 c = dense_get((uint32_t)(hub_lo + i));
-        if (c >= 2) {
-          const u64 v = c * (c - 1) / 2;
-          atomicAdd(&r12r[hub_lo + i], v);
-          accw += v;
+      for (int i = tid; i < (hub_n + 1) >> 1; i += blockDim.x) {
+        const uint32_t x = dense[i];  // counters of tops hub_lo + 2i and hub_lo + 2i + 1
+        if (x) {
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const u64 c = (x >> (16 * half)) & 0xFFFFu;
+            if (c >= 2) {
+              const u64 v = c * (c - 1) / 2;
+              atomicAdd(&r12r[hub_lo + 2 * i + half], v);
+              accw += v;
+            }
+          }
+          dense[i] = 0u;
         }
       }
     }
@@ -590,6 +606,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
           atomicAdd(&r12r[key], v);
           accw += v;
         }
+        if (!GMEM) T.clear(i);
       }
     }
     accw = block_sum(accw, red);
