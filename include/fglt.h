@@ -111,6 +111,10 @@ typedef struct {
     /* cyc_heavy_threads: block size of the dense-counter and global-table
      *   classes of the 4-cycle stage (128, 256, 512 or 1024; default 1024). */
     int cyc_heavy_threads;
+    /* cyc_dense_min: vertices with more possible 4-cycle tops than this
+     *   (and few tops outside the dense window) use the dense-window class
+     *   instead of a hash-table class (1 .. 4096; default 4096). */
+    int cyc_dense_min;
     /* Sub-dictionary s of Sigma16 (Table II caption): bit k set = sigma_k in
      * s; 0 (or 0xFFFF) selects Sigma16. Bits 0 and 1 must be set and no bit
      * above 15. Outputs then hold C = popcount(s) columns, sigma indices in

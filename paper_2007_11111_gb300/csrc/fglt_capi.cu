@@ -297,6 +297,9 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
                      threads + 2, 2)) != FGLT_OK) return s;
     if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_hub_span == v) return false; t.cyc_hub_span = v; return true; },
                      spans, 5)) != FGLT_OK) return s;
+    const int dmins[] = {1024, 2048, 4096};
+    if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_dense_min == v) return false; t.cyc_dense_min = v; return true; },
+                     dmins, 3)) != FGLT_OK) return s;
     // triangle candidates left over
     while (!tri_c.empty()) {
       Tuning run = best;

@@ -78,6 +78,8 @@ cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t n, int64_t* out, v
 size_t tri1_smem_bytes(int dpmax, bool bitmap_in_smem, int hf = 2);
 size_t tri2_smem_bytes(int dpmax, int hf = 2);
 bool tri1_bitmap_fits_smem(int dpmax, int hf = 2);
+// Dynamic shared memory a triangle-pass block may ask for.
+size_t tri_smem_limit();
 // Largest out-degree whose adjacency bitmap fits in shared memory.
 int tri1_smem_bitmap_max(int hf = 2);
 int tri_grid_blocks();
@@ -127,9 +129,12 @@ cudaError_t launch_in_lists(const int64_t* orp, const int32_t* ocol, const int32
 // *wmax, *wsum = largest and total wedge count; cls_wedges[c] += wedges of the
 // vertices in class c. cap_bound caps the distinct tops of one vertex (e.g.
 // the largest graph of a block-diagonal batch minus one); pass n when unknown.
+// Vertices with more than dense_min possible tops go to the dense class when
+// they qualify for it, before the hash-table classes are considered.
 cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, const int32_t* dr, int64_t n, int32_t* lists,
                                  int64_t list_stride, int32_t* counts, u64* gcap_max, u64* wmax, u64* wsum,
-                                 u64* cls_wedges, bool dense_ok, int64_t cap_bound, int wbits, cudaStream_t st);
+                                 u64* cls_wedges, bool dense_ok, int64_t cap_bound, int wbits, int64_t dense_min,
+                                 cudaStream_t st);
 struct CycArgs {
   int64_t n;
   const int64_t* orp;

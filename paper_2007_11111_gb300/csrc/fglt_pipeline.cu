@@ -30,7 +30,6 @@ const char* const SUB_NAMES[NUM_SUB] = {"cyc.warp",    "cyc.hash11",      "cyc.h
 namespace {
 
 constexpr int64_t MAX_DEGREE_EXACT = 2097151;  // binom(d,3) products stay inside int64
-constexpr size_t TRI_SMEM_LIMIT = 225 * 1024;  // dynamic shared memory a triangle-pass block may ask for
 
 // Small device counters, one int slot each.
 enum CounterId {
@@ -118,6 +117,8 @@ fglt_status tuning_from_options(const fglt_options& o, Tuning* t) {
     if (o.cyc_mid_threads[c]) x.cyc_mid_threads[c] = o.cyc_mid_threads[c];
     if (!pow2_threads(x.cyc_mid_threads[c])) return FGLT_ERR_INVALID_ARG;
   }
+  if (o.cyc_dense_min) x.cyc_dense_min = o.cyc_dense_min;
+  if (x.cyc_dense_min < 0 || x.cyc_dense_min > 4096) return FGLT_ERR_INVALID_ARG;
   if (o.cyc_heavy_threads) x.cyc_heavy_threads = o.cyc_heavy_threads;
   if (!pow2_threads(x.cyc_heavy_threads)) return FGLT_ERR_INVALID_ARG;
   *t = x;
@@ -133,6 +134,7 @@ void tuning_to_options(const Tuning& t, fglt_options* o) {
   o->cyc_warp_bits = t.cyc_warp_bits;
   for (int c = 0; c < 3; ++c) o->cyc_mid_threads[c] = t.cyc_mid_threads[c];
   o->cyc_heavy_threads = t.cyc_heavy_threads;
+  o->cyc_dense_min = t.cyc_dense_min;
 }
 
 fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t* out_net, cudaStream_t st,
@@ -329,8 +331,8 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
     tri_hf[c] = HF;
     if (!tri_on[c]) continue;
     auto fits = [&](int hf) {
-      return tri1_smem_bytes(tri_cap[c], tri1_bitmap_fits_smem(tri_cap[c], hf), hf) <= TRI_SMEM_LIMIT &&
-             tri2_smem_bytes(tri_cap[c], hf) <= TRI_SMEM_LIMIT;
+      return tri1_smem_bytes(tri_cap[c], tri1_bitmap_fits_smem(tri_cap[c], hf), hf) <= tri_smem_limit() &&
+             tri2_smem_bytes(tri_cap[c], hf) <= tri_smem_limit();
     };
     if (!fits(tri_hf[c])) tri_hf[c] = 2;
     if (!fits(tri_hf[c])) return FGLT_ERR_UNSUPPORTED;
@@ -419,7 +421,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
     const int64_t cap_bound = b ? std::min<int64_t>(b->cap, n) : n;
     CK(launch_cyc_worklists(wc, wcn, dr, n, lists, n, cnt + C_NCYC0, ctr + W_GCAP, ctr + W_WMAX, ctr + W_WSUM, ctr + W_CLS,
                             hub_lo < n,
-                            cap_bound, tu.cyc_warp_bits, st));
+                            cap_bound, tu.cyc_warp_bits, tu.cyc_dense_min, st));
     int32_t n_gmem = 0;
     u64 gcap = 0;
     if (b) {

@@ -50,6 +50,7 @@ struct Tuning {
   int cyc_mid_threads[3] = {256, 256, 256};
   int cyc_heavy_threads = 1024;
   int cyc_hub_span = 0;
+  int cyc_dense_min = 4096;
 };
 
 // Fills t from the options (0 fields keep the defaults) and checks ranges.

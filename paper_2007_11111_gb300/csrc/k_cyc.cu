@@ -674,7 +674,8 @@ __global__ void k_in_fill(const int64_t* __restrict__ orp, const int32_t* __rest
 __global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* __restrict__ wcn,
                                 const int32_t* __restrict__ dr, int64_t n,
                                 int32_t* lists, int64_t list_stride, int32_t* counts, u64* gcap_max, u64* wmax,
-                                u64* wsum, u64* cls_wedges, int dense_ok, int64_t cap_bound, int wbits) {
+                                u64* wsum, u64* cls_wedges, int dense_ok, int64_t cap_bound, int wbits,
+                                int64_t dense_min) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   u64 lmax = 0, lsum = 0;
@@ -691,12 +692,13 @@ __global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* _
       cap = wc[r];
       if (cap > n - 1 - r) cap = n - 1 - r;
       if (cap > cap_bound) cap = cap_bound;
+      const bool dense_fit = dense_ok && dr[r] < 65536;
       if (wc[r] <= (1LL << (wbits - 1))) cls = 0;
+      else if (cap > dense_min && dense_fit && wcn[r] <= (1 << (DHASH_BITS - 1))) cls = 4;
       else if (cap <= (1LL << (MID_BITS0 - 1))) cls = 1;
       else if (cap <= (1LL << (MID_BITS1 - 1))) cls = 2;
       else if (cap <= (1LL << (MID_BITS2 - 1))) cls = 3;
-      else if (dense_ok && wcn[r] <= (1 << (DHASH_BITS - 1)) && dr[r] < 65536) cls = 4;
-      else if (dense_ok && dr[r] < 65536) cls = 5;
+      else if (dense_fit) cls = 5;
       else cls = 6;
     }
     if (cls == 5) atomicMax(gcap_max, (u64)min(cap, (int64_t)wcn[r]));
@@ -793,12 +795,13 @@ cudaError_t launch_in_lists(const int64_t* orp, const int32_t* ocol, const int32
 
 cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, const int32_t* dr, int64_t n, int32_t* lists,
                                  int64_t list_stride, int32_t* counts, u64* gcap_max, u64* wmax, u64* wsum,
-                                 u64* cls_wedges, bool dense_ok, int64_t cap_bound, int wbits, cudaStream_t st) {
+                                 u64* cls_wedges, bool dense_ok, int64_t cap_bound, int wbits, int64_t dense_min,
+                                 cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int64_t blocks = (n + 255) / 256;
   if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
   k_cyc_worklists<<<(unsigned)blocks, 256, 0, st>>>(wc, wcn, dr, n, lists, list_stride, counts, gcap_max, wmax, wsum,
-                                                     cls_wedges, dense_ok ? 1 : 0, cap_bound, wbits);
+                                                     cls_wedges, dense_ok ? 1 : 0, cap_bound, wbits, dense_min);
   note_launch();
   return cudaGetLastError();
 }

@@ -388,7 +388,9 @@ int occupancy_grid(const void* fn, size_t smem, int threads = TRI_T) {
 
 }  // namespace
 
-bool tri1_bitmap_fits_smem(int dpmax, int hf) { return tri1_smem_impl(dpmax, true, hf) <= SMEM_LIMIT - 1024; }
+size_t tri_smem_limit() { return SMEM_LIMIT - 1024; }  // room for the kernels' static shared memory
+
+bool tri1_bitmap_fits_smem(int dpmax, int hf) { return tri1_smem_impl(dpmax, true, hf) <= tri_smem_limit(); }
 
 int tri1_smem_bitmap_max(int hf) {
   int lo = 2, hi = 1 << 14;  // fits(lo), !fits(hi)
