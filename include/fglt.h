@@ -100,6 +100,10 @@ typedef struct {
      *   N+(a) in the triangle passes, 2 or 4 (default 4): 4 shortens the probe
      *   runs that every lane of a warp waits for, at twice the table memory. */
     int tri_hash_factor;
+    /* tri_group_lanes: lanes that scan one out-list N+(b) together in the
+     *   triangle passes, 8, 16 or 32 (default 32): short out-lists leave most
+     *   lanes of a 32-lane group idle. */
+    int tri_group_lanes;
     /* cyc_warp_bits: log2 of the per-warp hash-table slots of the 4-cycle
      *   stage's warp class, which takes vertices with at most 2^(bits-1)
      *   wedges (6..10, default 10). */

@@ -227,9 +227,10 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
     if ((s = time_once(h, g, st, start, 1, &base)) != FGLT_OK) return s;  // warm-up (sizes the workspace)
     if ((s = time_once(h, g, st, start, reps, &base)) != FGLT_OK) return s;
     // Candidate values per parameter, tried one parameter at a time.
-    // triangle candidates: class bounds t0, t1, loads in flight, hash slots per element
-    const int t_bounds[][4] = {{32, 128, 4, 4}, {64, 256, 4, 4}, {128, 512, 2, 4}, {128, 512, 4, 2},
-                               {64, 1024, 4, 4}, {256, 768, 4, 4}, {128, 384, 4, 4}, {64, 256, 2, 2}};
+    // triangle candidates: class bounds t0, t1, loads in flight, hash slots per element, group lanes
+    const int t_bounds[][5] = {{128, 512, 4, 4, 8},  {128, 512, 4, 4, 16}, {64, 256, 4, 4, 8},  {128, 512, 2, 4, 8},
+                               {256, 768, 4, 4, 8},  {32, 128, 4, 4, 16},  {128, 512, 4, 2, 8}, {64, 256, 4, 4, 32},
+                               {128, 384, 4, 4, 16}};
     const int wbits[] = {8, 9, 10};
     const int spans[] = {0, 16384, 32768, 65536, 90112};
     const int threads[] = {128, 256, 512, 1024};
@@ -240,8 +241,9 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
       t.tri_t1 = tb[1];
       t.tri_loads = tb[2];
       t.tri_hash_factor = tb[3];
+      t.tri_group = tb[4];
       if (t.tri_t0 != start.tri_t0 || t.tri_t1 != start.tri_t1 || t.tri_loads != start.tri_loads ||
-          t.tri_hash_factor != start.tri_hash_factor)
+          t.tri_hash_factor != start.tri_hash_factor || t.tri_group != start.tri_group)
         tri_c.push_back(t);
     }
     TuneScore cur = base;
@@ -259,6 +261,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
           run.tri_t1 = tri_c.back().tri_t1;
           run.tri_loads = tri_c.back().tri_loads;
           run.tri_hash_factor = tri_c.back().tri_hash_factor;
+          run.tri_group = tri_c.back().tri_group;
         }
         TuneScore sc;
         fglt_status e = time_once(h, g, st, run, reps, &sc);
@@ -269,17 +272,20 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
             best.tri_t1 = run.tri_t1;
             best.tri_loads = run.tri_loads;
             best.tri_hash_factor = run.tri_hash_factor;
+            best.tri_group = run.tri_group;
             cur.tri = sc.tri;
           }
           tri_c.pop_back();
         }
         if (sc.cyc < cur.cyc) {
-          const int t0 = best.tri_t0, t1 = best.tri_t1, tl = best.tri_loads, thf = best.tri_hash_factor;
+          const int t0 = best.tri_t0, t1 = best.tri_t1, tl = best.tri_loads, thf = best.tri_hash_factor,
+                    tg = best.tri_group;
           best = t;
           best.tri_t0 = t0;
           best.tri_t1 = t1;
           best.tri_loads = tl;
           best.tri_hash_factor = thf;
+          best.tri_group = tg;
           cur.cyc = sc.cyc;
         }
       }
@@ -307,6 +313,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
       run.tri_t1 = tri_c.back().tri_t1;
       run.tri_loads = tri_c.back().tri_loads;
       run.tri_hash_factor = tri_c.back().tri_hash_factor;
+      run.tri_group = tri_c.back().tri_group;
       tri_c.pop_back();
       TuneScore sc;
       if ((s = time_once(h, g, st, run, reps, &sc)) != FGLT_OK) return s;
@@ -315,6 +322,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
         best.tri_t1 = run.tri_t1;
         best.tri_loads = run.tri_loads;
         best.tri_hash_factor = run.tri_hash_factor;
+        best.tri_group = run.tri_group;
         cur.tri = sc.tri;
       }
     }

@@ -85,16 +85,17 @@ int tri1_smem_bitmap_max(int hf = 2);
 int tri_grid_blocks();
 // C3 per oriented edge, c3 per vertex, 4-clique count per vertex (only with
 // cliques = true). loads: list entries each lane has in flight per scan step
-// (2 or 4). work_ctr[0..2] += (scanned out-list entries, triangles,
+// (2 or 4); group: lanes that scan one out-list N+(b) together (8, 16, 32). work_ctr[0..2] += (scanned out-list entries, triangles,
 // 4-cliques).
 cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm,
-                        u64* work_ctr, int* err, cudaStream_t st, bool cliques = true, int loads = 2, int hf = 2);
+                        u64* work_ctr, int* err, cudaStream_t st, bool cliques = true, int loads = 2, int hf = 2,
+                        int group = 32);
 size_t tri1_gbm_bytes(int dpmax, int hf = 2);
 // d^13 (diamond, off-cord) per vertex from the final C3.
 cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st,
-                        int loads = 2, int hf = 2);
+                        int loads = 2, int hf = 2, int group = 32);
 // d^10 = C3 (p1 - 2) and d^14 = D4,3 e / 2 from the final C3 (rank space).
 cudaError_t launch_c3_edge_terms(const int64_t* orp, const int32_t* ocol, const int32_t* C3o,
                                  const int32_t* dr, int64_t n, u64* r10r, u64* r14r, cudaStream_t st);

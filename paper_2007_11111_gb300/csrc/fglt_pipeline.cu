@@ -111,6 +111,8 @@ fglt_status tuning_from_options(const fglt_options& o, Tuning* t) {
   if (x.tri_loads != 2 && x.tri_loads != 4) return FGLT_ERR_INVALID_ARG;
   if (o.tri_hash_factor) x.tri_hash_factor = o.tri_hash_factor;
   if (x.tri_hash_factor != 2 && x.tri_hash_factor != 4) return FGLT_ERR_INVALID_ARG;
+  if (o.tri_group_lanes) x.tri_group = o.tri_group_lanes;
+  if (x.tri_group != 8 && x.tri_group != 16 && x.tri_group != 32) return FGLT_ERR_INVALID_ARG;
   if (o.cyc_warp_bits) x.cyc_warp_bits = o.cyc_warp_bits;
   if (x.cyc_warp_bits < 6 || x.cyc_warp_bits > cyc_warp_bits_max()) return FGLT_ERR_INVALID_ARG;
   for (int c = 0; c < 3; ++c) {
@@ -131,6 +133,7 @@ void tuning_to_options(const Tuning& t, fglt_options* o) {
   o->tri_class_bounds[1] = t.tri_t1;
   o->tri_probe_loads = t.tri_loads;
   o->tri_hash_factor = t.tri_hash_factor;
+  o->tri_group_lanes = t.tri_group;
   o->cyc_warp_bits = t.cyc_warp_bits;
   for (int c = 0; c < 3; ++c) o->cyc_mid_threads[c] = t.cyc_mid_threads[c];
   o->cyc_heavy_threads = t.cyc_heavy_threads;
@@ -351,7 +354,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
       sub(CYC_CLASSES + c, 0);
       CK(launch_tri1(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT1_0 + c, tri_cap[c], C3o, c3r, k4r,
                      tri1_gbm_bytes(tri_cap[c], tri_hf[c]) ? gbm : nullptr, ctr + W_PROBES, err, st, need_k4,
-                     tu.tri_loads, tri_hf[c]));
+                     tu.tri_loads, tri_hf[c], tu.tri_group));
       sub(CYC_CLASSES + c, 1);
     }
 
@@ -386,7 +389,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
     if (tri_on[c] && need_tri2) {
       sub(CYC_CLASSES + TRI_CLASSES + c, 0);
       CK(launch_tri2(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT2_0 + c, tri_cap[c], C3o, r13r, err,
-                     st, tu.tri_loads, tri_hf[c]));
+                     st, tu.tri_loads, tri_hf[c], tu.tri_group));
       sub(CYC_CLASSES + TRI_CLASSES + c, 1);
     }
 

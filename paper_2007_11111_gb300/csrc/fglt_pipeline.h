@@ -46,6 +46,7 @@ struct Tuning {
   int tri_t0 = 128, tri_t1 = 512;
   int tri_loads = 4;
   int tri_hash_factor = 4;
+  int tri_group = 32;
   int cyc_warp_bits = 10;
   int cyc_mid_threads[3] = {256, 256, 256};
   int cyc_heavy_threads = 1024;

@@ -88,24 +88,38 @@ __device__ __forceinline__ bool filter_test(const uint32_t* filt, uint32_t key, 
   return (filt[b >> 5] >> (b & 31)) & 1u;
 }
 
-// Warp scan of the sorted list ocol[bb, be) up to the first entry above
-// last: PL loads per lane in flight per step (32 * PL entries), probe(c, k)
-// for each entry c = ocol[k] (entries past the end read as INT_MAX).
-template <int PL, typename P>
+// Scan of the sorted list ocol[bb, be) by a group of G lanes (gl = lane in
+// the group, gmask = the group's lanes) up to the first entry above last: PL
+// loads per lane in flight per step (G * PL entries), probe(c, k) for each
+// entry c = ocol[k] (entries past the end read as INT_MAX).
+template <int PL, int G, typename P>
 __device__ __forceinline__ void scan_sorted(const int32_t* __restrict__ ocol, int64_t bb, int64_t be, int32_t last,
-                                            int lane, P probe) {
-  for (int64_t k0 = bb; k0 < be; k0 += 32 * PL) {
+                                            int gl, unsigned gmask, P probe) {
+  for (int64_t k0 = bb; k0 < be; k0 += G * PL) {
     int32_t c[PL];
 #pragma unroll
     for (int t = 0; t < PL; ++t) {
-      const int64_t k = k0 + lane + 32 * t;
+      const int64_t k = k0 + gl + G * t;
       c[t] = k < be ? ocol[k] : 0x7fffffff;
     }
 #pragma unroll
-    for (int t = 0; t < PL; ++t) probe(c[t], k0 + lane + 32 * t);
-    if (__shfl_sync(0xffffffffu, c[PL - 1], 31) > last) break;
+    for (int t = 0; t < PL; ++t) probe(c[t], k0 + gl + G * t);
+    if (__shfl_sync(gmask, c[PL - 1], G - 1, G) > last) break;
   }
 }
+
+// Lane groups of G lanes, one out-neighbour b of a per group.
+template <int G>
+struct Groups {
+  int first, stride, gl;
+  unsigned mask;
+  __device__ __forceinline__ Groups(int warp, int nwarps, int lane) {
+    first = warp * (32 / G) + lane / G;
+    stride = nwarps * (32 / G);
+    gl = lane % G;
+    mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Pass 1
@@ -117,7 +131,7 @@ __device__ __forceinline__ void scan_sorted(const int32_t* __restrict__ ocol, in
 //                                  i.e. twice the 4-cliques {a, x, ., .}
 // and a's own counts are the sums over x divided by 2 and 6.
 // ---------------------------------------------------------------------------
-template <bool SMEM_BM, bool K4, int PL>
+template <bool SMEM_BM, bool K4, int PL, int G>
 __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
                                                 const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
                                                 int* next, int Dmax, int Hbits, int hf, int32_t* C3o, u64* c3r,
@@ -182,7 +196,8 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int6
     // stops at the first step beyond the largest element of N+(a).
     const int32_t lastA = ocol[base + D - 1];
     u64 probes = 0;
-    for (int ib = warp; ib < D; ib += nwarps) {
+    const Groups<G> grp(warp, nwarps, lane);
+    for (int ib = grp.first; ib < D; ib += grp.stride) {
       const int32_t b = ocol[base + ib];
       const int64_t bb = orp[b], be = orp[b + 1];
       uint32_t* row = bm + (size_t)ib * W;
@@ -199,7 +214,7 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int6
           }
         }
       };
-      scan_sorted<PL>(ocol, bb, be, lastA, lane, probe);
+      scan_sorted<PL, G>(ocol, bb, be, lastA, grp.gl, grp.mask, probe);
     }
     __syncthreads();
 
@@ -292,7 +307,7 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int6
 // ---------------------------------------------------------------------------
 // Pass 2
 // ---------------------------------------------------------------------------
-template <int PL, int BT>
+template <int PL, int BT, int G>
 __global__ void __launch_bounds__(BT) k_tri2(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
                                                 const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
                                                 int* next, int Dmax, int Hbits, int hf,
@@ -335,7 +350,8 @@ __global__ void __launch_bounds__(BT) k_tri2(const int64_t* __restrict__ orp, co
 
     const int32_t lastA = ocol[base + D - 1];
     long long acc_a = 0;
-    for (int ib = warp; ib < D; ib += nwarps) {
+    const Groups<G> grp(warp, nwarps, lane);
+    for (int ib = grp.first; ib < D; ib += grp.stride) {
       const int32_t b = ocol[base + ib];
       const int64_t bb = orp[b], be = orp[b + 1];
       const long long tab = tv[ib];
@@ -351,9 +367,10 @@ __global__ void __launch_bounds__(BT) k_tri2(const int64_t* __restrict__ orp, co
           }
         }
       };
-      scan_sorted<PL>(ocol, bb, be, lastA, lane, probe);
-      accb = warp_sum_i64(accb);
-      if (lane == 0 && accb) atomicAdd(&acc[ib], (u64)accb);
+      scan_sorted<PL, G>(ocol, bb, be, lastA, grp.gl, grp.mask, probe);
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) accb += __shfl_xor_sync(grp.mask, accb, o, G);
+      if (grp.gl == 0 && accb) atomicAdd(&acc[ib], (u64)accb);
     }
     __syncthreads();
     for (int x = tid; x < D; x += blockDim.x)
@@ -410,22 +427,30 @@ size_t tri2_smem_bytes(int dpmax, int hf) {
 
 int tri_grid_blocks() { return num_sms(); }
 
+// Kernel instance for (bitmap in shared memory, cliques, loads, group lanes).
+template <bool SMEM_BM, bool K4>
+auto tri1_fn(int loads, int g) {
+  if (loads >= 4) return g >= 32 ? k_tri1<SMEM_BM, K4, 4, 32> : (g >= 16 ? k_tri1<SMEM_BM, K4, 4, 16> : k_tri1<SMEM_BM, K4, 4, 8>);
+  return g >= 32 ? k_tri1<SMEM_BM, K4, 2, 32> : (g >= 16 ? k_tri1<SMEM_BM, K4, 2, 16> : k_tri1<SMEM_BM, K4, 2, 8>);
+}
+
 template <bool SMEM_BM>
 void allow_tri1() {
-  allow_max_smem(k_tri1<SMEM_BM, true, 2>);
-  allow_max_smem(k_tri1<SMEM_BM, false, 2>);
-  allow_max_smem(k_tri1<SMEM_BM, true, 4>);
-  allow_max_smem(k_tri1<SMEM_BM, false, 4>);
+  for (int loads : {2, 4})
+    for (int g : {8, 16, 32}) {
+      allow_max_smem(tri1_fn<SMEM_BM, true>(loads, g));
+      allow_max_smem(tri1_fn<SMEM_BM, false>(loads, g));
+    }
 }
 
 static int tri1_grid(int dpmax, bool smem_bm, int hf) {
   const size_t smem = tri1_smem_impl(dpmax, smem_bm, hf);
   if (smem_bm) {
     allow_tri1<true>();
-    return occupancy_grid((const void*)k_tri1<true, true, 2>, smem);
+    return occupancy_grid((const void*)k_tri1<true, true, 2, 32>, smem);
   }
   allow_tri1<false>();
-  return occupancy_grid((const void*)k_tri1<false, true, 2>, smem, TRI_T_BIG);
+  return occupancy_grid((const void*)k_tri1<false, true, 2, 32>, smem, TRI_T_BIG);
 }
 
 size_t tri1_gbm_bytes(int dpmax, int hf) {
@@ -437,16 +462,14 @@ size_t tri1_gbm_bytes(int dpmax, int hf) {
 
 cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm, u64* work_ctr,
-                        int* err, cudaStream_t st, bool cliques, int loads, int hf) {
+                        int* err, cudaStream_t st, bool cliques, int loads, int hf, int group) {
   if (dpmax < 2) return cudaSuccess;
   const bool smem_bm = tri1_bitmap_fits_smem(dpmax, hf);
   const size_t smem = tri1_smem_impl(dpmax, smem_bm, hf);
   const int grid = tri1_grid(dpmax, smem_bm, hf);
   const int hb = hash_bits_for(dpmax, hf);
-  auto* fn = loads >= 4 ? (smem_bm ? (cliques ? k_tri1<true, true, 4> : k_tri1<true, false, 4>)
-                                   : (cliques ? k_tri1<false, true, 4> : k_tri1<false, false, 4>))
-                        : (smem_bm ? (cliques ? k_tri1<true, true, 2> : k_tri1<true, false, 2>)
-                                   : (cliques ? k_tri1<false, true, 2> : k_tri1<false, false, 2>));
+  auto* fn = smem_bm ? (cliques ? tri1_fn<true, true>(loads, group) : tri1_fn<true, false>(loads, group))
+                     : (cliques ? tri1_fn<false, true>(loads, group) : tri1_fn<false, false>(loads, group));
   fn<<<grid, smem_bm ? TRI_T : TRI_T_BIG, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, hf, C3o, c3r, k4r,
                                                      smem_bm ? nullptr : gbm, work_ctr, err);
   note_launch();
@@ -455,15 +478,18 @@ cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* 
 
 cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st, int loads,
-                        int hf) {
+                        int hf, int group) {
   if (dpmax < 2) return cudaSuccess;
   const size_t smem = tri2_smem_bytes(dpmax, hf);
   if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
   // the out-degree class beyond the shared-memory bitmap of pass 1 runs with
   // 1024-thread blocks (its tables allow one block per SM)
   const bool big = !tri1_bitmap_fits_smem(dpmax, hf);
-  auto* fn = big ? (loads >= 4 ? k_tri2<4, TRI_T_BIG> : k_tri2<2, TRI_T_BIG>)
-                 : (loads >= 4 ? k_tri2<4, TRI_T> : k_tri2<2, TRI_T>);
+  auto pick = [&](auto f8, auto f16, auto f32) { return group >= 32 ? f32 : (group >= 16 ? f16 : f8); };
+  auto* fn = big ? (loads >= 4 ? pick(k_tri2<4, TRI_T_BIG, 8>, k_tri2<4, TRI_T_BIG, 16>, k_tri2<4, TRI_T_BIG, 32>)
+                               : pick(k_tri2<2, TRI_T_BIG, 8>, k_tri2<2, TRI_T_BIG, 16>, k_tri2<2, TRI_T_BIG, 32>))
+                 : (loads >= 4 ? pick(k_tri2<4, TRI_T, 8>, k_tri2<4, TRI_T, 16>, k_tri2<4, TRI_T, 32>)
+                               : pick(k_tri2<2, TRI_T, 8>, k_tri2<2, TRI_T, 16>, k_tri2<2, TRI_T, 32>));
   allow_max_smem(fn);
   const int threads = big ? TRI_T_BIG : TRI_T;
   const int grid = occupancy_grid((const void*)fn, smem, threads);

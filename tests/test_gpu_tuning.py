@@ -15,7 +15,8 @@ torch = pytest.importorskip("torch")
 
 SETTINGS = [
     dict(),
-    dict(tri_class_bounds=(2, 3)),
+    dict(tri_class_bounds=(2, 3), tri_group_lanes=8),
+    dict(tri_group_lanes=16, tri_probe_loads=2),
     dict(tri_class_bounds=(8, 1024), tri_probe_loads=4, tri_hash_factor=4),
     dict(tri_class_bounds=(3, 2000), tri_probe_loads=4),
     dict(cyc_warp_bits=6),
@@ -68,7 +69,8 @@ def test_invalid_settings_rejected():
     for bad in (dict(tri_class_bounds=(64, 32)), dict(tri_class_bounds=(1, 8)), dict(cyc_warp_bits=11),
                 dict(cyc_warp_bits=5), dict(cyc_mid_threads=(96, 256, 256)), dict(cyc_heavy_threads=300),
                 dict(cyc_hub_span=-1), dict(cyc_hub_span=90113), dict(tri_probe_loads=3),
-                dict(tri_hash_factor=3), dict(cyc_mid_threads=(64, 256, 256)), dict(cyc_dense_min=5000)):
+                dict(tri_hash_factor=3), dict(cyc_mid_threads=(64, 256, 256)), dict(cyc_dense_min=5000),
+                dict(tri_group_lanes=4)):
         with pytest.raises(fg.FgltError) as e:
             fg.Handle(device=0, **bad)
         assert e.value.status == fg.FGLT_ERR_INVALID_ARG
@@ -99,6 +101,7 @@ def test_autotune_installs_setting_and_keeps_results(cases):
         # a fresh handle created with the chosen setting gives the same counts
         kw = dict(tri_class_bounds=tuple(chosen["tri_class_bounds"]), cyc_warp_bits=chosen["cyc_warp_bits"],
                   tri_probe_loads=chosen["tri_probe_loads"], tri_hash_factor=chosen["tri_hash_factor"],
+                  tri_group_lanes=chosen["tri_group_lanes"],
                   cyc_mid_threads=tuple(chosen["cyc_mid_threads"]), cyc_heavy_threads=chosen["cyc_heavy_threads"],
                   cyc_hub_span=chosen["cyc_hub_span"], cyc_dense_min=chosen["cyc_dense_min"])
         with fg.Handle(device=0, **kw) as h2:
@@ -106,8 +109,8 @@ def test_autotune_installs_setting_and_keeps_results(cases):
             np.testing.assert_array_equal(net, onet)
 
 
-@pytest.mark.parametrize("bounds", [(3, 2000), (64, 256)])
-def test_global_bitmap_in_any_class_closed_form(bounds):
+@pytest.mark.parametrize("bounds,lanes", [((3, 2000), 8), ((64, 256), 32)])
+def test_global_bitmap_in_any_class_closed_form(bounds, lanes):
     """K_1200: every out-degree in the degree order is above the shared-memory
     bitmap limit, so with class bounds (3, 2000) a middle class runs on the
     global-memory bitmap. Net counts have the closed form of a clique."""
@@ -117,7 +120,7 @@ def test_global_bitmap_in_any_class_closed_form(bounds):
         pytest.skip("no CUDA device")
     n = 1200
     g = gg.complete(n)
-    with fg.Handle(device=0, tri_class_bounds=bounds) as h:
+    with fg.Handle(device=0, tri_class_bounds=bounds, tri_group_lanes=lanes) as h:
         _, net = _run(h, g)
     want = np.zeros(16, np.int64)
     want[0], want[1], want[4], want[15] = 1, n - 1, comb(n - 1, 2), comb(n - 1, 3)
