@@ -119,6 +119,11 @@ typedef struct {
      *   (and few tops outside the dense window) use the dense-window class
      *   instead of a hash-table class (1 .. 4096; default 4096). */
     int cyc_dense_min;
+    /* cyc_long_segment: in the block classes of the 4-cycle stage, a
+     *   middle's segment of tops at least this long is walked by one warp
+     *   (coalesced); shorter ones are concatenated and split evenly over the
+     *   lanes (2 .. 512; default 32). */
+    int cyc_long_segment;
     /* Sub-dictionary s of Sigma16 (Table II caption): bit k set = sigma_k in
      * s; 0 (or 0xFFFF) selects Sigma16. Bits 0 and 1 must be set and no bit
      * above 15. Outputs then hold C = popcount(s) columns, sigma indices in

@@ -119,6 +119,8 @@ fglt_status tuning_from_options(const fglt_options& o, Tuning* t) {
     if (o.cyc_mid_threads[c]) x.cyc_mid_threads[c] = o.cyc_mid_threads[c];
     if (!pow2_threads(x.cyc_mid_threads[c])) return FGLT_ERR_INVALID_ARG;
   }
+  if (o.cyc_long_segment) x.cyc_long_segment = o.cyc_long_segment;
+  if (x.cyc_long_segment < 2 || x.cyc_long_segment > 512) return FGLT_ERR_INVALID_ARG;
   if (o.cyc_dense_min) x.cyc_dense_min = o.cyc_dense_min;
   if (x.cyc_dense_min < 0 || x.cyc_dense_min > 4096) return FGLT_ERR_INVALID_ARG;
   if (o.cyc_heavy_threads) x.cyc_heavy_threads = o.cyc_heavy_threads;
@@ -138,6 +140,7 @@ void tuning_to_options(const Tuning& t, fglt_options* o) {
   for (int c = 0; c < 3; ++c) o->cyc_mid_threads[c] = t.cyc_mid_threads[c];
   o->cyc_heavy_threads = t.cyc_heavy_threads;
   o->cyc_dense_min = t.cyc_dense_min;
+  o->cyc_long_segment = t.cyc_long_segment;
 }
 
 fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t* out_net, cudaStream_t st,
@@ -459,6 +462,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
       ca.wbits = tu.cyc_warp_bits;
       for (int c = 0; c < 3; ++c) ca.mid_threads[c] = tu.cyc_mid_threads[c];
       ca.heavy_threads = tu.cyc_heavy_threads;
+      ca.long_seg = tu.cyc_long_segment;
       ca.r12r = r12r;
       ca.err = err;
       ca.cap_bound = cap_bound;

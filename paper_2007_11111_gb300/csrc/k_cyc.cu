@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const int64_t* __restrict__
 // ---------------------------------------------------------------------------
 constexpr int CHUNK_MAX = 512;  // middles per chunk: min(block size, 512)
 
-constexpr int LONG_SEG = 32;  // segments at least this long are walked by one warp
+// Segments at least long_seg long are walked warp-per-segment (coalesced, one
+// owner); shorter ones are concatenated and split evenly over the lanes.
 
 struct Segs {
   int64_t* st;      // [chunk] short segments: start in ocol
@@ -357,12 +358,13 @@ __device__ __forceinline__ long long block_excl_scan(long long x, long long* scr
 // Segments of the middles c0 .. c0 + chunk of w: long ones listed for
 // warp-per-segment walks, short non-empty ones compacted with their wedge
 // prefix for the flattened walk (one packed block scan).
-__device__ __forceinline__ void build_chunk(const Segs& S, const Mids& M, int64_t c0, int64_t n, int chunk) {
+__device__ __forceinline__ void build_chunk(const Segs& S, const Mids& M, int64_t c0, int64_t n, int chunk,
+                                            int long_seg) {
   const int64_t k = c0 + threadIdx.x;
   int32_t rv = -1;
   int64_t st = 0, len = 0;
   if ((int)threadIdx.x < chunk && k < M.K) middle_seg(M, k, n, rv, st, len);
-  const bool is_long = len >= LONG_SEG;
+  const bool is_long = len >= long_seg;
   const bool is_short = len > 0 && !is_long;
   // packed: [short wedge sum : 32 | short count : 16 | long count : 16]
   const long long packed = ((is_short ? len : 0LL) << 32) | ((long long)is_short << 16) | (long long)is_long;
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
                                                   const int64_t* __restrict__ wc, const int32_t* __restrict__ list,
                                                   const int32_t* __restrict__ cnt, int* next, u64* r12r, int64_t n,
                                                   const int64_t* __restrict__ wcn, int32_t hub_lo, int tbits,
-                                                  int dense_words, uint32_t* gkeys,
+                                                  int dense_words, int long_seg, uint32_t* gkeys,
                                                   uint32_t* gcnt, int64_t cap_bound, int* err) {
   constexpr bool DENSE = MODE == 1 || MODE == 4;
   constexpr bool GMEM = MODE == 3 || MODE == 4;
@@ -547,7 +549,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
     };
     // Pass A: count the wedges per top u.
     for (int64_t c0 = 0; c0 < M.K; c0 += CH) {
-      build_chunk(S, M, c0, n, CH);
+      build_chunk(S, M, c0, n, CH, long_seg);
       walk_long(S, ocol, [&](uint32_t u) -> u64 { count(u); return 0; }, [](int32_t, u64) {});
       walk_chunk(S, ocol, [&](uint32_t u, int, bool valid) {
         if (valid) count(u);
@@ -557,7 +559,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
     // Pass B: each middle gains cnt[u] - 1 per wedge.
     for (int64_t c0 = 0; c0 < M.K; c0 += CH) {
       if (!single) {
-        build_chunk(S, M, c0, n, CH);
+        build_chunk(S, M, c0, n, CH, long_seg);
       } else {
         if (tid == 0) S.misc[2] = 0;
         __syncthreads();
@@ -754,7 +756,7 @@ void launch_block(const CycArgs& a, int cls, int tbits, int dense_words, cudaStr
   const int grid = MODE >= 3 ? gmem_blocks() : num_sms() * occupancy((const void*)k_cyc_block<MODE, BT>, BT, smem);
   k_cyc_block<MODE, BT><<<grid, BT, smem, st>>>(a.orp, a.ocol, a.irp, a.iin, a.wc, a.lists + cls * a.list_stride,
                                                 a.counts + cls, a.next + cls, a.r12r, a.n, a.wcn, a.hub_lo, tbits,
-                                                dense_words, a.gkeys, a.gcnt, a.cap_bound, a.err);
+                                                dense_words, a.long_seg, a.gkeys, a.gcnt, a.cap_bound, a.err);
   note_launch();
 }
 

@@ -23,7 +23,8 @@ SETTINGS = [
     dict(cyc_warp_bits=8, cyc_mid_threads=(512, 1024, 512)),
     dict(cyc_mid_threads=(1024, 128, 1024), cyc_heavy_threads=256, tri_hash_factor=4),
     dict(cyc_heavy_threads=512, cyc_hub_span=64, cyc_dense_min=1),
-    dict(cyc_dense_min=1024, cyc_mid_threads=(128, 128, 128)),
+    dict(cyc_dense_min=1024, cyc_mid_threads=(128, 128, 128), cyc_long_segment=2),
+    dict(cyc_long_segment=512, cyc_heavy_threads=512),
     dict(cyc_hub_span=1, cyc_warp_bits=7, tri_class_bounds=(16, 32)),
 ]
 
@@ -70,7 +71,7 @@ def test_invalid_settings_rejected():
                 dict(cyc_warp_bits=5), dict(cyc_mid_threads=(96, 256, 256)), dict(cyc_heavy_threads=300),
                 dict(cyc_hub_span=-1), dict(cyc_hub_span=90113), dict(tri_probe_loads=3),
                 dict(tri_hash_factor=3), dict(cyc_mid_threads=(64, 256, 256)), dict(cyc_dense_min=5000),
-                dict(tri_group_lanes=4)):
+                dict(tri_group_lanes=4), dict(cyc_long_segment=1)):
         with pytest.raises(fg.FgltError) as e:
             fg.Handle(device=0, **bad)
         assert e.value.status == fg.FGLT_ERR_INVALID_ARG
@@ -103,7 +104,8 @@ def test_autotune_installs_setting_and_keeps_results(cases):
                   tri_probe_loads=chosen["tri_probe_loads"], tri_hash_factor=chosen["tri_hash_factor"],
                   tri_group_lanes=chosen["tri_group_lanes"],
                   cyc_mid_threads=tuple(chosen["cyc_mid_threads"]), cyc_heavy_threads=chosen["cyc_heavy_threads"],
-                  cyc_hub_span=chosen["cyc_hub_span"], cyc_dense_min=chosen["cyc_dense_min"])
+                  cyc_hub_span=chosen["cyc_hub_span"], cyc_dense_min=chosen["cyc_dense_min"],
+                  cyc_long_segment=chosen["cyc_long_segment"])
         with fg.Handle(device=0, **kw) as h2:
             raw, net = _run(h2, g)
             np.testing.assert_array_equal(net, onet)
