@@ -104,6 +104,10 @@ typedef struct {
      *   triangle passes, 8, 16 or 32 (default 32): short out-lists leave most
      *   lanes of a 32-lane group idle. */
     int tri_group_lanes;
+    /* tri_warp_max: vertices whose out-degree in the degree order is at most
+     *   this run the triangle passes one warp per vertex instead of one block
+     *   (0 = off, at most 32; default 0). */
+    int tri_warp_max;
     /* cyc_warp_bits: log2 of the per-warp hash-table slots of the 4-cycle
      *   stage's warp class, which takes vertices with at most 2^(bits-1)
      *   wedges (6..10, default 10). */
@@ -243,9 +247,10 @@ fglt_status fglt_csr_from_edges(fglt_t handle, const int32_t* src, const int32_t
  * the stages in order (degree, spmv1, rank, orient, sort, tri1, c3_edges,
  * spmv2, tri2, wedges, cyc, epilogue), then their parts: the seven 4-cycle
  * vertex classes inside "cyc" (cyc.warp, cyc.hash11, cyc.hash12, cyc.hash13,
- * cyc.dense, cyc.dense_spill, cyc.global) and the four out-degree classes of
- * each triangle pass (tri1.c0 .. tri1.c3, tri2.c0 .. tri2.c3); a part that
- * did not run reads 0. */
+ * cyc.dense, cyc.dense_spill, cyc.global) and the five out-degree classes of
+ * each triangle pass (tri1.w, tri1.c0 .. tri1.c3, tri2.w, tri2.c0 ..
+ * tri2.c3; ".w" is the warp-per-vertex class); a part that did not run reads
+ * 0. */
 fglt_status fglt_stage_times(fglt_t handle, const char** names, float* ms,
                              int max_stages, int* count);
 

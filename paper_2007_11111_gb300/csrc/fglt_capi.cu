@@ -227,10 +227,11 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
     if ((s = time_once(h, g, st, start, 1, &base)) != FGLT_OK) return s;  // warm-up (sizes the workspace)
     if ((s = time_once(h, g, st, start, reps, &base)) != FGLT_OK) return s;
     // Candidate values per parameter, tried one parameter at a time.
-    // triangle candidates: class bounds t0, t1, loads in flight, hash slots per element, group lanes
-    const int t_bounds[][5] = {{128, 512, 4, 4, 8},  {128, 512, 4, 4, 16}, {64, 256, 4, 4, 8},  {128, 512, 2, 4, 8},
-                               {256, 768, 4, 4, 8},  {32, 128, 4, 4, 16},  {128, 512, 4, 2, 8}, {64, 256, 4, 4, 32},
-                               {128, 384, 4, 4, 16}};
+    // triangle candidates: class bounds t0, t1, loads in flight, hash slots per element, group lanes,
+    // warp-per-vertex bound
+    const int t_bounds[][6] = {{128, 512, 4, 4, 32, 32}, {128, 512, 4, 4, 32, 16}, {128, 512, 4, 4, 8, 32},
+                               {64, 256, 4, 4, 32, 32},  {256, 768, 4, 4, 32, 32}, {128, 512, 2, 4, 32, 32},
+                               {128, 512, 4, 4, 16, 0},  {64, 256, 4, 4, 32, 0},   {128, 384, 4, 2, 32, 32}};
     const int wbits[] = {8, 9, 10};
     const int spans[] = {0, 16384, 32768, 65536, 90112};
     const int threads[] = {128, 256, 512, 1024};
@@ -242,8 +243,9 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
       t.tri_loads = tb[2];
       t.tri_hash_factor = tb[3];
       t.tri_group = tb[4];
+      t.tri_warp = tb[5];
       if (t.tri_t0 != start.tri_t0 || t.tri_t1 != start.tri_t1 || t.tri_loads != start.tri_loads ||
-          t.tri_hash_factor != start.tri_hash_factor || t.tri_group != start.tri_group)
+          t.tri_hash_factor != start.tri_hash_factor || t.tri_group != start.tri_group || t.tri_warp != start.tri_warp)
         tri_c.push_back(t);
     }
     TuneScore cur = base;
@@ -262,6 +264,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
           run.tri_loads = tri_c.back().tri_loads;
           run.tri_hash_factor = tri_c.back().tri_hash_factor;
           run.tri_group = tri_c.back().tri_group;
+          run.tri_warp = tri_c.back().tri_warp;
         }
         TuneScore sc;
         fglt_status e = time_once(h, g, st, run, reps, &sc);
@@ -273,14 +276,16 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
             best.tri_loads = run.tri_loads;
             best.tri_hash_factor = run.tri_hash_factor;
             best.tri_group = run.tri_group;
+            best.tri_warp = run.tri_warp;
             cur.tri = sc.tri;
           }
           tri_c.pop_back();
         }
         if (sc.cyc < cur.cyc) {
           const int t0 = best.tri_t0, t1 = best.tri_t1, tl = best.tri_loads, thf = best.tri_hash_factor,
-                    tg = best.tri_group;
+                    tg = best.tri_group, tw = best.tri_warp;
           best = t;
+          best.tri_warp = tw;
           best.tri_t0 = t0;
           best.tri_t1 = t1;
           best.tri_loads = tl;
@@ -317,6 +322,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
       run.tri_loads = tri_c.back().tri_loads;
       run.tri_hash_factor = tri_c.back().tri_hash_factor;
       run.tri_group = tri_c.back().tri_group;
+      run.tri_warp = tri_c.back().tri_warp;
       tri_c.pop_back();
       TuneScore sc;
       if ((s = time_once(h, g, st, run, reps, &sc)) != FGLT_OK) return s;
@@ -326,6 +332,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
         best.tri_loads = run.tri_loads;
         best.tri_hash_factor = run.tri_hash_factor;
         best.tri_group = run.tri_group;
+        best.tri_warp = run.tri_warp;
         cur.tri = sc.tri;
       }
     }

@@ -62,9 +62,9 @@ cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int32
 // Vertices (rank labels) with at least `min_out` out-neighbours.
 cudaError_t launch_worklist_outdeg(const int32_t* opc, int64_t n, int min_out, int32_t* list,
                                    int32_t* count, cudaStream_t st);
-// The same split into four lists by out-degree: [min_out, t0], (t0, t1],
-// (t1, t2], (t2, ...) at lists + c * stride, sizes in counts[0..3].
-cudaError_t launch_worklist_outdeg4(const int32_t* opc, int64_t n, int min_out, int t0, int t1, int t2,
+// The same split into five lists by out-degree: [min_out, tw], (tw, t0],
+// (t0, t1], (t1, t2], (t2, ...) at lists + c * stride, sizes in counts[0..4].
+cudaError_t launch_worklist_outdeg5(const int32_t* opc, int64_t n, int min_out, int tw, int t0, int t1, int t2,
                                     int32_t* lists, int64_t stride, int32_t* counts, cudaStream_t st);
 
 // --- scans -----------------------------------------------------------------
@@ -92,6 +92,14 @@ cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* 
                         u64* work_ctr, int* err, cudaStream_t st, bool cliques = true, int loads = 2, int hf = 2,
                         int group = 32);
 size_t tri1_gbm_bytes(int dpmax, int hf = 2);
+// The same two passes for vertices of out-degree at most tri_warp_max(): one
+// warp per vertex, everything in shared memory.
+int tri_warp_max();
+cudaError_t launch_tri1_warp(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
+                             int* next, int32_t* C3o, u64* c3r, u64* k4r, u64* work_ctr, int* err, cudaStream_t st,
+                             bool cliques, int loads);
+cudaError_t launch_tri2_warp(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
+                             int* next, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st, int loads);
 // d^13 (diamond, off-cord) per vertex from the final C3.
 cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st,
@@ -105,7 +113,7 @@ cudaError_t launch_unrank_u64(const u64* src_r, const int32_t* perm, int64_t n, 
 
 // --- 4-cycles (rank space) ---------------------------------------------------
 constexpr int CYC_CLASSES = 7;
-constexpr int TRI_CLASSES = 4;  // out-degree classes of the triangle passes
+constexpr int TRI_CLASSES = 5;  // out-degree classes of the triangle passes (the first: one warp per vertex)
 // Largest window of top ranks the dense class can hold (16-bit counters in
 // shared memory).
 int cyc_dense_span_max();

@@ -23,9 +23,10 @@ namespace fglt {
 
 const char* const STAGE_NAMES[NUM_STAGES] = {"degree", "spmv1", "rank", "orient", "sort", "tri1", "c3_edges",
                                              "spmv2", "tri2", "wedges", "cyc", "epilogue"};
-const char* const SUB_NAMES[NUM_SUB] = {"cyc.warp",    "cyc.hash11",      "cyc.hash12", "cyc.hash13", "cyc.dense",
-                                        "cyc.dense_spill", "cyc.global",   "tri1.c0",    "tri1.c1",    "tri1.c2",
-                                        "tri1.c3",     "tri2.c0",         "tri2.c1",    "tri2.c2",    "tri2.c3"};
+const char* const SUB_NAMES[NUM_SUB] = {"cyc.warp",   "cyc.hash11", "cyc.hash12", "cyc.hash13", "cyc.dense",
+                                        "cyc.dense_spill", "cyc.global", "tri1.w", "tri1.c0",  "tri1.c1",
+                                        "tri1.c2",    "tri1.c3",    "tri2.w",     "tri2.c0",    "tri2.c1",
+                                        "tri2.c2",    "tri2.c3"};
 
 namespace {
 
@@ -111,6 +112,8 @@ fglt_status tuning_from_options(const fglt_options& o, Tuning* t) {
   if (x.tri_loads != 2 && x.tri_loads != 4) return FGLT_ERR_INVALID_ARG;
   if (o.tri_hash_factor) x.tri_hash_factor = o.tri_hash_factor;
   if (x.tri_hash_factor != 2 && x.tri_hash_factor != 4) return FGLT_ERR_INVALID_ARG;
+  if (o.tri_warp_max < 0 || o.tri_warp_max > tri_warp_max()) return FGLT_ERR_INVALID_ARG;
+  x.tri_warp = o.tri_warp_max;
   if (o.tri_group_lanes) x.tri_group = o.tri_group_lanes;
   if (x.tri_group != 8 && x.tri_group != 16 && x.tri_group != 32) return FGLT_ERR_INVALID_ARG;
   if (o.cyc_warp_bits) x.cyc_warp_bits = o.cyc_warp_bits;
@@ -136,6 +139,7 @@ void tuning_to_options(const Tuning& t, fglt_options* o) {
   o->tri_probe_loads = t.tri_loads;
   o->tri_hash_factor = t.tri_hash_factor;
   o->tri_group_lanes = t.tri_group;
+  o->tri_warp_max = t.tri_warp;
   o->cyc_warp_bits = t.cyc_warp_bits;
   for (int c = 0; c < 3; ++c) o->cyc_mid_threads[c] = t.cyc_mid_threads[c];
   o->cyc_heavy_threads = t.cyc_heavy_threads;
@@ -313,11 +317,15 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   // pass only fits in global memory.
   const int HF = tu.tri_hash_factor;
   const int T2 = std::max(T1, tri1_smem_bitmap_max(HF));
+  // The first class (out-degree up to TW) runs one warp per vertex.
+  const int TW = std::min(tu.tri_warp, tri_warp_max());
   int32_t* twork;
   NEED(B_TWORK, (int64_t)TRI_CLASSES * n, twork);
-  CK(launch_worklist_outdeg4(opc, n, 2, T0, T1, T2, twork, n, cnt + C_NTRI0, st));
-  const int tri_cap[TRI_CLASSES] = {std::min(dpmax, T0), std::min(dpmax, T1), std::min(dpmax, T2), dpmax};
-  const bool tri_on[TRI_CLASSES] = {dpmax >= 2, dpmax > T0, dpmax > T1, dpmax > T2};
+  CK(launch_worklist_outdeg5(opc, n, 2, std::max(TW, 1), T0, T1, T2, twork, n, cnt + C_NTRI0, st));
+  const int tri_cap[TRI_CLASSES] = {std::min(dpmax, TW), std::min(dpmax, T0), std::min(dpmax, T1),
+                                    std::min(dpmax, T2), dpmax};
+  const bool tri_on[TRI_CLASSES] = {TW >= 2 && dpmax >= 2, dpmax > std::max(TW, 1) && T0 > TW, dpmax > T0,
+                                    dpmax > T1, dpmax > T2};
 
   // Triangle pass 1: C3, c3, 4-cliques.
   mark(5);
@@ -335,7 +343,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   int tri_hf[TRI_CLASSES];
   for (int c = 0; c < TRI_CLASSES; ++c) {
     tri_hf[c] = HF;
-    if (!tri_on[c]) continue;
+    if (!tri_on[c] || c == 0) continue;  // the warp class has fixed per-warp tables
     auto fits = [&](int hf) {
       return tri1_smem_bytes(tri_cap[c], tri1_bitmap_fits_smem(tri_cap[c], hf), hf) <= tri_smem_limit() &&
              tri2_smem_bytes(tri_cap[c], hf) <= tri_smem_limit();
@@ -345,7 +353,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   }
   uint32_t* gbm = nullptr;
   size_t gbm_need = 0;  // classes whose bitmap does not fit in shared memory share one buffer
-  for (int c = 0; c < TRI_CLASSES; ++c)
+  for (int c = 1; c < TRI_CLASSES; ++c)
     if (tri_on[c]) gbm_need = std::max(gbm_need, tri1_gbm_bytes(tri_cap[c], tri_hf[c]));
   if (size_t gb = gbm_need) {
     unsigned char* p = nullptr;
@@ -355,9 +363,13 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   for (int c = 0; c < TRI_CLASSES; ++c)
     if (tri_on[c] && need_tri1) {
       sub(CYC_CLASSES + c, 0);
-      CK(launch_tri1(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT1_0 + c, tri_cap[c], C3o, c3r, k4r,
-                     tri1_gbm_bytes(tri_cap[c], tri_hf[c]) ? gbm : nullptr, ctr + W_PROBES, err, st, need_k4,
-                     tu.tri_loads, tri_hf[c], tu.tri_group));
+      if (c == 0)
+        CK(launch_tri1_warp(orp, ocol, twork, cnt + C_NTRI0, cnt + C_NEXT1_0, C3o, c3r, k4r, ctr + W_PROBES, err, st,
+                            need_k4, tu.tri_loads));
+      else
+        CK(launch_tri1(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT1_0 + c, tri_cap[c], C3o, c3r, k4r,
+                       tri1_gbm_bytes(tri_cap[c], tri_hf[c]) ? gbm : nullptr, ctr + W_PROBES, err, st, need_k4,
+                       tu.tri_loads, tri_hf[c], tu.tri_group));
       sub(CYC_CLASSES + c, 1);
     }
 
@@ -391,8 +403,11 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   for (int c = 0; c < TRI_CLASSES; ++c)
     if (tri_on[c] && need_tri2) {
       sub(CYC_CLASSES + TRI_CLASSES + c, 0);
-      CK(launch_tri2(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT2_0 + c, tri_cap[c], C3o, r13r, err,
-                     st, tu.tri_loads, tri_hf[c], tu.tri_group));
+      if (c == 0)
+        CK(launch_tri2_warp(orp, ocol, twork, cnt + C_NTRI0, cnt + C_NEXT2_0, C3o, r13r, err, st, tu.tri_loads));
+      else
+        CK(launch_tri2(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT2_0 + c, tri_cap[c], C3o, r13r, err,
+                       st, tu.tri_loads, tri_hf[c], tu.tri_group));
       sub(CYC_CLASSES + TRI_CLASSES + c, 1);
     }
 

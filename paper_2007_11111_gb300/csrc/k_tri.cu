@@ -381,6 +381,181 @@ __global__ void __launch_bounds__(BT) k_tri2(const int64_t* __restrict__ orp, co
   }
 }
 
+// ---------------------------------------------------------------------------
+// Small out-degree (|N+(a)| <= 32): one warp per vertex a, no block barriers.
+// Each bitmap row of G_a is one word, so the 4-clique tallies are per-lane
+// popcounts. Per warp: a 128-slot hash table of N+(a) (at most 4 slots per
+// element), a 512-bit filter, the bitmap rows and the tallies.
+// ---------------------------------------------------------------------------
+constexpr int TW_MAX = 32;      // largest out-degree of the warp class
+constexpr int TW_HBITS = 7;     // 128 slots
+constexpr int TW_FBITS = 9;     // 512-bit filter
+constexpr int TW_T = 256;       // 8 warps per block
+struct WarpTri {                // per-warp shared memory
+  uint32_t keys[1 << TW_HBITS];
+  int32_t vals[1 << TW_HBITS];
+  uint32_t filt[(1 << TW_FBITS) / 32];
+  uint32_t S[TW_MAX];
+  uint32_t k2[TW_MAX];
+  u64 acc[TW_MAX];
+  int32_t tv[TW_MAX];
+};
+
+// Loads N+(a) into the warp's table and filter; returns the lane's element
+// (or 0x7fffffff past D) and sets *D, *base.
+__device__ __forceinline__ int32_t warp_load_out(WarpTri& w, const int64_t* __restrict__ orp,
+                                                 const int32_t* __restrict__ ocol, int32_t a, int lane, int* D,
+                                                 int64_t* base, int* hb, int* err) {
+  *base = orp[a];
+  *D = (int)(orp[a + 1] - *base);
+  int b = 5;
+  while ((1 << b) < 4 * *D) ++b;
+  *hb = b;
+  for (int i = lane; i < (1 << b); i += 32) w.keys[i] = EMPTY_KEY;
+  if (lane < (1 << TW_FBITS) / 32) w.filt[lane] = 0u;
+  __syncwarp();
+  const int32_t x = lane < *D ? ocol[*base + lane] : 0x7fffffff;
+  if (lane < *D) {
+    table_insert(w.keys, w.vals, (uint32_t)x, lane, b, err);
+    filter_set(w.filt, (uint32_t)x, TW_FBITS);
+  }
+  __syncwarp();
+  return x;
+}
+
+template <int PL, bool K4>
+__global__ void __launch_bounds__(TW_T) k_tri1_warp(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                                    const int32_t* __restrict__ work,
+                                                    const int32_t* __restrict__ nwork, int* next, int32_t* C3o,
+                                                    u64* c3r, u64* k4r, u64* work_ctr, int* err) {
+  __shared__ WarpTri sw[TW_T / 32];
+  const int lane = threadIdx.x & 31;
+  WarpTri& w = sw[threadIdx.x >> 5];
+  const int total = *nwork;
+  u64 probes = 0, tri_total = 0, k4_total = 0;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(next, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    const int32_t a = work[item];
+    int D, hb;
+    int64_t base;
+    const int32_t x = warp_load_out(w, orp, ocol, a, lane, &D, &base, &hb, err);
+    w.S[lane] = 0u;
+    w.k2[lane] = 0u;
+    __syncwarp();
+    const int32_t lastA = __shfl_sync(0xffffffffu, x, D - 1);
+    for (int ib = 0; ib < D; ++ib) {
+      const int32_t b = __shfl_sync(0xffffffffu, x, ib);
+      const int64_t bb = orp[b], be = orp[b + 1];
+      auto probe = [&](int32_t c, int64_t k) {
+        if (c <= lastA) {
+          ++probes;
+          if (filter_test(w.filt, (uint32_t)c, TW_FBITS)) {
+            const int ic = table_find(w.keys, w.vals, (uint32_t)c, hb);
+            if (ic >= 0) {
+              atomicOr(&w.S[ib], 1u << ic);
+              atomicOr(&w.S[ic], 1u << ib);
+              atomicAdd(&C3o[k], 1);  // edge b -> c
+            }
+          }
+        }
+      };
+      scan_sorted<PL, 32>(ocol, bb, be, lastA, lane, 0xffffffffu, probe);
+    }
+    __syncwarp();
+    const uint32_t Sx = lane < D ? w.S[lane] : 0u;
+    const int deg = __popc(Sx);
+    if (deg) {
+      atomicAdd(&C3o[base + lane], deg);
+      atomicAdd(&c3r[x], (u64)deg);
+    }
+    const u64 tri_a = (u64)warp_sum_i32(deg) / 2;
+    if (K4) {
+      // per edge x-y of G_a with y > x: t = |S_x ∩ S_y|, added to both ends
+      uint32_t up = lane < 31 ? (Sx & ~((2u << lane) - 1u)) : 0u;
+      uint32_t kx = 0;
+      while (up) {
+        const int y = __ffs(up) - 1;
+        up &= up - 1;
+        const uint32_t t = __popc(Sx & w.S[y]);
+        if (t) {
+          atomicAdd(&w.k2[y], t);
+          kx += t;
+        }
+      }
+      if (kx) atomicAdd(&w.k2[lane], kx);
+      __syncwarp();
+      const uint32_t k2 = lane < D ? w.k2[lane] : 0u;
+      if (k2) atomicAdd(&k4r[x], (u64)(k2 / 2));
+      const u64 k4_a = (u64)warp_sum_i32((int)k2) / 6;
+      if (lane == 0 && k4_a) atomicAdd(&k4r[a], k4_a);
+      k4_total += k4_a;
+    }
+    if (lane == 0 && tri_a) atomicAdd(&c3r[a], tri_a);
+    tri_total += tri_a;
+    __syncwarp();
+  }
+  probes = warp_sum_u64(probes);
+  if (lane == 0) {
+    if (probes) atomicAdd(&work_ctr[0], probes);
+    if (tri_total) atomicAdd(&work_ctr[1], tri_total);
+    if (k4_total) atomicAdd(&work_ctr[2], k4_total);
+  }
+}
+
+template <int PL>
+__global__ void __launch_bounds__(TW_T) k_tri2_warp(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                                    const int32_t* __restrict__ work,
+                                                    const int32_t* __restrict__ nwork, int* next,
+                                                    const int32_t* __restrict__ C3o, u64* r13r, int* err) {
+  __shared__ WarpTri sw[TW_T / 32];
+  const int lane = threadIdx.x & 31;
+  WarpTri& w = sw[threadIdx.x >> 5];
+  const int total = *nwork;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(next, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    const int32_t a = work[item];
+    int D, hb;
+    int64_t base;
+    const int32_t x = warp_load_out(w, orp, ocol, a, lane, &D, &base, &hb, err);
+    w.acc[lane] = 0;
+    w.tv[lane] = lane < D ? C3o[base + lane] : 0;
+    __syncwarp();
+    const int32_t lastA = __shfl_sync(0xffffffffu, x, D - 1);
+    long long acc_a = 0;
+    for (int ib = 0; ib < D; ++ib) {
+      const int32_t b = __shfl_sync(0xffffffffu, x, ib);
+      const int64_t bb = orp[b], be = orp[b + 1];
+      const long long tab = w.tv[ib];
+      long long accb = 0;
+      auto probe = [&](int32_t c, int64_t k) {
+        if (c <= lastA && filter_test(w.filt, (uint32_t)c, TW_FBITS)) {
+          const int32_t c3bc = C3o[k];  // issued before the table probe so that the two overlap
+          const int ic = table_find(w.keys, w.vals, (uint32_t)c, hb);
+          if (ic >= 0) {
+            acc_a += (long long)c3bc - 1;   // a: opposite edge b-c
+            accb += (long long)w.tv[ic] - 1;  // b: opposite edge a-c
+            if (tab > 1) atomicAdd(&w.acc[ic], (u64)(tab - 1));  // c: opposite edge a-b
+          }
+        }
+      };
+      scan_sorted<PL, 32>(ocol, bb, be, lastA, lane, 0xffffffffu, probe);
+      accb = warp_sum_i64(accb);
+      if (lane == 0 && accb) atomicAdd(&w.acc[ib], (u64)accb);
+    }
+    __syncwarp();
+    if (lane < D && w.acc[lane]) atomicAdd(&r13r[x], w.acc[lane]);
+    const u64 sa = (u64)warp_sum_i64(acc_a);
+    if (lane == 0 && sa) atomicAdd(&r13r[a], sa);
+    __syncwarp();
+  }
+}
+
 int host_filter_words(int D) {
   int fb = 5;
   while ((1 << fb) < 16 * D) ++fb;
@@ -494,6 +669,28 @@ cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* 
   const int threads = big ? TRI_T_BIG : TRI_T;
   const int grid = occupancy_grid((const void*)fn, smem, threads);
   fn<<<grid, threads, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hash_bits_for(dpmax, hf), hf, C3o, r13r, err);
+  note_launch();
+  return cudaGetLastError();
+}
+
+int tri_warp_max() { return TW_MAX; }
+
+cudaError_t launch_tri1_warp(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
+                             int* next, int32_t* C3o, u64* c3r, u64* k4r, u64* work_ctr, int* err, cudaStream_t st,
+                             bool cliques, int loads) {
+  auto* fn = loads >= 4 ? (cliques ? k_tri1_warp<4, true> : k_tri1_warp<4, false>)
+                        : (cliques ? k_tri1_warp<2, true> : k_tri1_warp<2, false>);
+  const int grid = occupancy_grid((const void*)fn, 0, TW_T);
+  fn<<<grid, TW_T, 0, st>>>(orp, ocol, work, nwork, next, C3o, c3r, k4r, work_ctr, err);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tri2_warp(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
+                             int* next, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st, int loads) {
+  auto* fn = loads >= 4 ? k_tri2_warp<4> : k_tri2_warp<2>;
+  const int grid = occupancy_grid((const void*)fn, 0, TW_T);
+  fn<<<grid, TW_T, 0, st>>>(orp, ocol, work, nwork, next, C3o, r13r, err);
   note_launch();
   return cudaGetLastError();
 }

@@ -16,7 +16,9 @@ torch = pytest.importorskip("torch")
 SETTINGS = [
     dict(),
     dict(tri_class_bounds=(2, 3), tri_group_lanes=8),
-    dict(tri_group_lanes=16, tri_probe_loads=2),
+    dict(tri_group_lanes=16, tri_probe_loads=2, tri_warp_max=32),
+    dict(tri_warp_max=16, tri_class_bounds=(8, 20)),
+    dict(tri_warp_max=32, tri_probe_loads=2, tri_class_bounds=(2, 3)),
     dict(tri_class_bounds=(8, 1024), tri_probe_loads=4, tri_hash_factor=4),
     dict(tri_class_bounds=(3, 2000), tri_probe_loads=4),
     dict(cyc_warp_bits=6),
@@ -71,7 +73,7 @@ def test_invalid_settings_rejected():
                 dict(cyc_warp_bits=5), dict(cyc_mid_threads=(96, 256, 256)), dict(cyc_heavy_threads=300),
                 dict(cyc_hub_span=-1), dict(cyc_hub_span=90113), dict(tri_probe_loads=3),
                 dict(tri_hash_factor=3), dict(cyc_mid_threads=(64, 256, 256)), dict(cyc_dense_min=5000),
-                dict(tri_group_lanes=4), dict(cyc_long_segment=1)):
+                dict(tri_group_lanes=4), dict(cyc_long_segment=1), dict(tri_warp_max=33)):
         with pytest.raises(fg.FgltError) as e:
             fg.Handle(device=0, **bad)
         assert e.value.status == fg.FGLT_ERR_INVALID_ARG
@@ -102,7 +104,7 @@ def test_autotune_installs_setting_and_keeps_results(cases):
         # a fresh handle created with the chosen setting gives the same counts
         kw = dict(tri_class_bounds=tuple(chosen["tri_class_bounds"]), cyc_warp_bits=chosen["cyc_warp_bits"],
                   tri_probe_loads=chosen["tri_probe_loads"], tri_hash_factor=chosen["tri_hash_factor"],
-                  tri_group_lanes=chosen["tri_group_lanes"],
+                  tri_group_lanes=chosen["tri_group_lanes"], tri_warp_max=chosen["tri_warp_max"],
                   cyc_mid_threads=tuple(chosen["cyc_mid_threads"]), cyc_heavy_threads=chosen["cyc_heavy_threads"],
                   cyc_hub_span=chosen["cyc_hub_span"], cyc_dense_min=chosen["cyc_dense_min"],
                   cyc_long_segment=chosen["cyc_long_segment"])
