@@ -408,6 +408,11 @@ __device__ __forceinline__ int32_t warp_load_out(WarpTri& w, const int64_t* __re
                                                  int64_t* base, int* hb, int* err) {
   *base = orp[a];
   *D = (int)(orp[a + 1] - *base);
+  if (*D > TW_MAX || *D < 2) {  // outside the class (a sizing bug): flag it, skip the vertex
+    if (lane == 0) atomicOr(err, ERR_INTERNAL);
+    *D = 0;
+    return 0x7fffffff;
+  }
   int b = 5;
   while ((1 << b) < 4 * *D) ++b;
   *hb = b;
@@ -442,6 +447,7 @@ __global__ void __launch_bounds__(TW_T) k_tri1_warp(const int64_t* __restrict__ 
     int D, hb;
     int64_t base;
     const int32_t x = warp_load_out(w, orp, ocol, a, lane, &D, &base, &hb, err);
+    if (D == 0) continue;
     w.S[lane] = 0u;
     w.k2[lane] = 0u;
     __syncwarp();
@@ -523,6 +529,7 @@ __global__ void __launch_bounds__(TW_T) k_tri2_warp(const int64_t* __restrict__ 
     int D, hb;
     int64_t base;
     const int32_t x = warp_load_out(w, orp, ocol, a, lane, &D, &base, &hb, err);
+    if (D == 0) continue;
     w.acc[lane] = 0;
     w.tv[lane] = lane < D ? C3o[base + lane] : 0;
     __syncwarp();
