@@ -329,6 +329,17 @@ def bench_serving(fg, torch, dev, num_requests=400, pool_size=24, seed=0, loads=
     return out
 
 
+def tuning_args(args) -> dict:
+    """--set name=value options for the handle (tuning fields of fglt_options;
+    tuples as comma-separated values)."""
+    out = {}
+    for item in args.set or []:
+        k, v = item.split("=", 1)
+        vals = [int(x) for x in v.split(",")]
+        out[k] = tuple(vals) if len(vals) > 1 else vals[0]
+    return out
+
+
 def slowest_rank_ms(ms: float, world: int, device=None) -> float:
     """Max over ranks of a per-rank time (the job is as fast as its slowest rank)."""
     if world <= 1:
@@ -385,7 +396,7 @@ def run_gpu(args, rank, world, local_rank):
     raw = torch.empty((g.n, 16), dtype=torch.int64, device=dev)
     net = torch.empty((g.n, 16), dtype=torch.int64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
-    h = fg.Handle(device=local_rank, profile_stages=True)
+    h = fg.Handle(device=local_rank, profile_stages=True, **tuning_args(args))
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -504,6 +515,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--set", action="append", metavar="NAME=VALUE",
+                    help="tuning field of the handle, e.g. --set cyc_spill_bits=13 (with --no-autotune to keep it)")
     ap.add_argument("--serving-full", action="store_true",
                     help="serve 5000 requests with |E| up to 2e7 at loads 1 and 2 (several minutes)")
     args = ap.parse_args()

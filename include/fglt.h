@@ -128,6 +128,11 @@ typedef struct {
      *   (coalesced); shorter ones are concatenated and split evenly over the
      *   lanes (2 .. 512; default 32). */
     int cyc_long_segment;
+    /* cyc_spill_bits: the dense-window class keeps the tops outside its window
+     *   in a shared-memory table of 2^bits slots and takes vertices with at
+     *   most 2^(bits-1) wedges there; the others use a global-memory table
+     *   (11 .. 13; default 11). */
+    int cyc_spill_bits;
     /* Sub-dictionary s of Sigma16 (Table II caption): bit k set = sigma_k in
      * s; 0 (or 0xFFFF) selects Sigma16. Bits 0 and 1 must be set and no bit
      * above 15. Outputs then hold C = popcount(s) columns, sigma indices in

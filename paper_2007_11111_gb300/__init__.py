@@ -72,6 +72,7 @@ class fglt_options(ctypes.Structure):
         ("cyc_heavy_threads", ctypes.c_int),
         ("cyc_dense_min", ctypes.c_int),
         ("cyc_long_segment", ctypes.c_int),
+        ("cyc_spill_bits", ctypes.c_int),
         ("dictionary_mask", ctypes.c_uint),
     ]
 
@@ -82,7 +83,7 @@ class fglt_options(ctypes.Structure):
                 "tri_group_lanes": self.tri_group_lanes, "tri_warp_max": self.tri_warp_max,
                 "cyc_warp_bits": self.cyc_warp_bits, "cyc_mid_threads": list(self.cyc_mid_threads),
                 "cyc_heavy_threads": self.cyc_heavy_threads, "cyc_dense_min": self.cyc_dense_min,
-                "cyc_long_segment": self.cyc_long_segment}
+                "cyc_long_segment": self.cyc_long_segment, "cyc_spill_bits": self.cyc_spill_bits}
 
 
 class fglt_graph_host(ctypes.Structure):
@@ -327,7 +328,8 @@ class Handle:
                  cyc_hub_span: int = 0, tri_class_bounds=(0, 0), cyc_warp_bits: int = 0,
                  cyc_mid_threads=(0, 0, 0), cyc_heavy_threads: int = 0, dictionary: int = 0,
                  tri_probe_loads: int = 0, tri_hash_factor: int = 0, cyc_dense_min: int = 0,
-                 tri_group_lanes: int = 0, cyc_long_segment: int = 0, tri_warp_max: int = 0):
+                 tri_group_lanes: int = 0, cyc_long_segment: int = 0, tri_warp_max: int = 0,
+                 cyc_spill_bits: int = 0):
         """dictionary: sub-dictionary bit mask (0 = Sigma16; DICT_SIGMA5 = Sigma5)."""
         opt = fglt_options_default()
         opt.dictionary_mask = int(dictionary)
@@ -344,6 +346,7 @@ class Handle:
         opt.tri_group_lanes = int(tri_group_lanes)
         opt.cyc_long_segment = int(cyc_long_segment)
         opt.tri_warp_max = int(tri_warp_max)
+        opt.cyc_spill_bits = int(cyc_spill_bits)
         opt.validate = int(validate)
         opt.profile_stages = int(profile_stages)
         opt.serve_memory_budget = int(serve_memory_budget)

@@ -311,6 +311,9 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
     const int dmins[] = {1024, 2048, 4096};
     if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_dense_min == v) return false; t.cyc_dense_min = v; return true; },
                      dmins, 3)) != FGLT_OK) return s;
+    const int sbits[] = {12, 13, 11};
+    if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_spill_bits == v) return false; t.cyc_spill_bits = v; return true; },
+                     sbits, 3)) != FGLT_OK) return s;
     const int lsegs[] = {12, 20, 32};
     if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_long_segment == v) return false; t.cyc_long_segment = v; return true; },
                      lsegs, 3)) != FGLT_OK) return s;

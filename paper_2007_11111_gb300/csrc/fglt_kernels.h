@@ -117,6 +117,9 @@ constexpr int TRI_CLASSES = 5;  // out-degree classes of the triangle passes (th
 // Largest window of top ranks the dense class can hold (16-bit counters in
 // shared memory).
 int cyc_dense_span_max();
+// Largest spill-table size (at most spill_bits, at least 11) whose dense-class
+// block fits in shared memory next to a window of span tops.
+int cyc_fit_spill_bits(int span, int spill_bits, int threads);
 // Largest per-vertex table need served by shared-memory tables; vertices above
 // it may need the global-memory class.
 int cyc_block_cap();
@@ -133,6 +136,7 @@ cudaError_t launch_in_lists(const int64_t* orp, const int32_t* ocol, const int32
 // Splits the vertices with at least two wedges into CYC_CLASSES classes (lists
 // at lists + c * list_stride, counts[c]): warp table (wc <= 2^(wbits-1)),
 // three block hash-table sizes, dense hub counters with a shared spill table
+// of 2^spill_bits slots (at most 2^(spill_bits-1) wedges outside the window)
 // and with a global spill table (only if dense_ok, for vertices of degree
 // dr < 65536), global hash table; *gcap_max = largest global table need;
 // *wmax, *wsum = largest and total wedge count; cls_wedges[c] += wedges of the
@@ -143,7 +147,7 @@ cudaError_t launch_in_lists(const int64_t* orp, const int32_t* ocol, const int32
 cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, const int32_t* dr, int64_t n, int32_t* lists,
                                  int64_t list_stride, int32_t* counts, u64* gcap_max, u64* wmax, u64* wsum,
                                  u64* cls_wedges, bool dense_ok, int64_t cap_bound, int wbits, int64_t dense_min,
-                                 cudaStream_t st);
+                                 int spill_bits, cudaStream_t st);
 struct CycArgs {
   int64_t n;
   const int64_t* orp;
@@ -161,6 +165,7 @@ struct CycArgs {
   int mid_threads[3];     // block sizes of the three hash-table classes (128 .. 1024)
   int heavy_threads;      // block size of the dense and global classes
   int long_seg;           // block classes: segments at least this long are walked warp-per-segment
+  int spill_bits;         // dense class: shared spill table of 2^spill_bits slots
   int gbits;              // global tables: cyc_gmem_blocks() << gbits slots each array
   uint32_t* gkeys;        // NULL when both global-table classes are empty
   uint32_t* gcnt;

@@ -122,6 +122,8 @@ fglt_status tuning_from_options(const fglt_options& o, Tuning* t) {
     if (o.cyc_mid_threads[c]) x.cyc_mid_threads[c] = o.cyc_mid_threads[c];
     if (!pow2_threads(x.cyc_mid_threads[c])) return FGLT_ERR_INVALID_ARG;
   }
+  if (o.cyc_spill_bits) x.cyc_spill_bits = o.cyc_spill_bits;
+  if (x.cyc_spill_bits < 11 || x.cyc_spill_bits > 13) return FGLT_ERR_INVALID_ARG;
   if (o.cyc_long_segment) x.cyc_long_segment = o.cyc_long_segment;
   if (x.cyc_long_segment < 2 || x.cyc_long_segment > 512) return FGLT_ERR_INVALID_ARG;
   if (o.cyc_dense_min) x.cyc_dense_min = o.cyc_dense_min;
@@ -145,6 +147,7 @@ void tuning_to_options(const Tuning& t, fglt_options* o) {
   o->cyc_heavy_threads = t.cyc_heavy_threads;
   o->cyc_dense_min = t.cyc_dense_min;
   o->cyc_long_segment = t.cyc_long_segment;
+  o->cyc_spill_bits = t.cyc_spill_bits;
 }
 
 fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t* out_net, cudaStream_t st,
@@ -422,6 +425,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
     // 2^21 vertices (their wedge tops spread over more hubs).
     int64_t span = tu.cyc_hub_span > 0 ? tu.cyc_hub_span : (n > (1 << 21) ? 65536 : 32768);
     const int32_t hub_lo = (int32_t)std::max<int64_t>(0, n - span);
+    const int spill_bits = cyc_fit_spill_bits((int)std::min<int64_t>(span, n), tu.cyc_spill_bits, tu.cyc_heavy_threads);
     int64_t *wc, *wcn, *irp;
     int32_t *hc, *indeg, *icur;
     int2* iin;
@@ -442,7 +446,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
     const int64_t cap_bound = b ? std::min<int64_t>(b->cap, n) : n;
     CK(launch_cyc_worklists(wc, wcn, dr, n, lists, n, cnt + C_NCYC0, ctr + W_GCAP, ctr + W_WMAX, ctr + W_WSUM, ctr + W_CLS,
                             hub_lo < n,
-                            cap_bound, tu.cyc_warp_bits, tu.cyc_dense_min, st));
+                            cap_bound, tu.cyc_warp_bits, tu.cyc_dense_min, spill_bits, st));
     int32_t n_gmem = 0;
     u64 gcap = 0;
     if (b) {
@@ -478,6 +482,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
       for (int c = 0; c < 3; ++c) ca.mid_threads[c] = tu.cyc_mid_threads[c];
       ca.heavy_threads = tu.cyc_heavy_threads;
       ca.long_seg = tu.cyc_long_segment;
+      ca.spill_bits = spill_bits;
       ca.r12r = r12r;
       ca.err = err;
       ca.cap_bound = cap_bound;

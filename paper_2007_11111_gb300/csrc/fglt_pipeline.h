@@ -54,6 +54,7 @@ struct Tuning {
   int cyc_hub_span = 0;
   int cyc_dense_min = 4096;
   int cyc_long_segment = 32;
+  int cyc_spill_bits = 11;
 };
 
 // Fills t from the options (0 fields keep the defaults) and checks ranges.

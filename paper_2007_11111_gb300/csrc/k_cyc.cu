@@ -43,7 +43,8 @@ namespace {
 
 constexpr int WARP_T = 256;
 constexpr int DENSE_SPAN_MAX = 90112;  // 16-bit counters: 176 KB of shared memory at most
-constexpr int DHASH_BITS = 11;      // 2048-slot table for the non-hub tops of the dense class
+// The dense class keeps the tops outside its window in a shared table of
+// 2^spill_bits slots (11 .. 13, tunable).
 constexpr int MID_BITS0 = 11, MID_BITS1 = 12, MID_BITS2 = 13;  // table sizes of the three hash-only block classes
 constexpr int MID_BITS[3] = {MID_BITS0, MID_BITS1, MID_BITS2};
 
@@ -677,7 +678,7 @@ __global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* _
                                 const int32_t* __restrict__ dr, int64_t n,
                                 int32_t* lists, int64_t list_stride, int32_t* counts, u64* gcap_max, u64* wmax,
                                 u64* wsum, u64* cls_wedges, int dense_ok, int64_t cap_bound, int wbits,
-                                int64_t dense_min) {
+                                int64_t dense_min, int spill_bits) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   u64 lmax = 0, lsum = 0;
@@ -696,7 +697,7 @@ __global__ void k_cyc_worklists(const int64_t* __restrict__ wc, const int64_t* _
       if (cap > cap_bound) cap = cap_bound;
       const bool dense_fit = dense_ok && dr[r] < 65536;
       if (wc[r] <= (1LL << (wbits - 1))) cls = 0;
-      else if (cap > dense_min && dense_fit && wcn[r] <= (1 << (DHASH_BITS - 1))) cls = 4;
+      else if (cap > dense_min && dense_fit && wcn[r] <= (1 << (spill_bits - 1))) cls = 4;
       else if (cap <= (1LL << (MID_BITS0 - 1))) cls = 1;
       else if (cap <= (1LL << (MID_BITS1 - 1))) cls = 2;
       else if (cap <= (1LL << (MID_BITS2 - 1))) cls = 3;
@@ -738,10 +739,10 @@ int occupancy(const void* fn, int threads, size_t smem) {
   return per_sm < 1 ? 1 : per_sm;
 }
 
-size_t block_smem(int mode, int bt, int tbits, int dense_words) {
+size_t block_smem(int mode, int bt, int tbits, int dense_words) {  // tbits: table bits of modes 0 and 1
   const size_t seg = seg_bytes(bt < CHUNK_MAX ? bt : CHUNK_MAX);
   if (mode == 0) return seg + ((size_t)8 << tbits);
-  if (mode == 1) return seg + (size_t)dense_words * 4 + ((size_t)8 << DHASH_BITS);
+  if (mode == 1) return seg + (size_t)dense_words * 4 + ((size_t)8 << tbits);
   if (mode == 4) return seg + (size_t)dense_words * 4;
   return seg;
 }
@@ -771,6 +772,18 @@ void launch_block_bt(const CycArgs& a, int cls, int tbits, int dense_words, int 
 }  // namespace
 
 int cyc_dense_span_max() { return DENSE_SPAN_MAX; }
+
+int cyc_fit_spill_bits(int span, int spill_bits, int threads) {
+  int optin = 0, dev = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
+    optin = 227 * 1024;
+  const size_t limit = (size_t)optin - 1024;  // room for the kernel's static shared memory
+  const int bt = threads >= 1024 ? 1024 : (threads >= 512 ? 512 : (threads >= 256 ? 256 : 128));
+  int b = spill_bits;
+  while (b > 11 && block_smem(1, bt, b, (span + 1) / 2) > limit) --b;
+  return b;
+}
 int cyc_block_cap() { return 1 << (MID_BITS[2] - 1); }
 int cyc_gmem_blocks() { return gmem_blocks(); }
 int cyc_warp_bits_max() { return 10; }
@@ -798,12 +811,13 @@ cudaError_t launch_in_lists(const int64_t* orp, const int32_t* ocol, const int32
 cudaError_t launch_cyc_worklists(const int64_t* wc, const int64_t* wcn, const int32_t* dr, int64_t n, int32_t* lists,
                                  int64_t list_stride, int32_t* counts, u64* gcap_max, u64* wmax, u64* wsum,
                                  u64* cls_wedges, bool dense_ok, int64_t cap_bound, int wbits, int64_t dense_min,
-                                 cudaStream_t st) {
+                                 int spill_bits, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int64_t blocks = (n + 255) / 256;
   if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
   k_cyc_worklists<<<(unsigned)blocks, 256, 0, st>>>(wc, wcn, dr, n, lists, list_stride, counts, gcap_max, wmax, wsum,
-                                                     cls_wedges, dense_ok ? 1 : 0, cap_bound, wbits, dense_min);
+                                                     cls_wedges, dense_ok ? 1 : 0, cap_bound, wbits, dense_min,
+                                                     spill_bits);
   note_launch();
   return cudaGetLastError();
 }
@@ -832,7 +846,7 @@ cudaError_t launch_cyc(const CycArgs& a, cudaStream_t st) {
   const int span = (int)(a.n - a.hub_lo);
   if (span > 0) {
     mark(4, 0);
-    launch_block_bt<1>(a, 4, DHASH_BITS, (span + 1) / 2, a.heavy_threads, st);
+    launch_block_bt<1>(a, 4, a.spill_bits, (span + 1) / 2, a.heavy_threads, st);
     mark(4, 1);
   }
   if (a.gkeys && span > 0) {

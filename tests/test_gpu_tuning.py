@@ -26,7 +26,8 @@ SETTINGS = [
     dict(cyc_mid_threads=(1024, 128, 1024), cyc_heavy_threads=256, tri_hash_factor=4),
     dict(cyc_heavy_threads=512, cyc_hub_span=64, cyc_dense_min=1),
     dict(cyc_dense_min=1024, cyc_mid_threads=(128, 128, 128), cyc_long_segment=2),
-    dict(cyc_long_segment=512, cyc_heavy_threads=512),
+    dict(cyc_long_segment=512, cyc_heavy_threads=512, cyc_spill_bits=13),
+    dict(cyc_spill_bits=12, cyc_hub_span=64, cyc_dense_min=1),
     dict(cyc_hub_span=1, cyc_warp_bits=7, tri_class_bounds=(16, 32)),
 ]
 
@@ -73,7 +74,7 @@ def test_invalid_settings_rejected():
                 dict(cyc_warp_bits=5), dict(cyc_mid_threads=(96, 256, 256)), dict(cyc_heavy_threads=300),
                 dict(cyc_hub_span=-1), dict(cyc_hub_span=90113), dict(tri_probe_loads=3),
                 dict(tri_hash_factor=3), dict(cyc_mid_threads=(64, 256, 256)), dict(cyc_dense_min=5000),
-                dict(tri_group_lanes=4), dict(cyc_long_segment=1), dict(tri_warp_max=33)):
+                dict(tri_group_lanes=4), dict(cyc_long_segment=1), dict(tri_warp_max=33), dict(cyc_spill_bits=14)):
         with pytest.raises(fg.FgltError) as e:
             fg.Handle(device=0, **bad)
         assert e.value.status == fg.FGLT_ERR_INVALID_ARG
@@ -107,7 +108,7 @@ def test_autotune_installs_setting_and_keeps_results(cases):
                   tri_group_lanes=chosen["tri_group_lanes"], tri_warp_max=chosen["tri_warp_max"],
                   cyc_mid_threads=tuple(chosen["cyc_mid_threads"]), cyc_heavy_threads=chosen["cyc_heavy_threads"],
                   cyc_hub_span=chosen["cyc_hub_span"], cyc_dense_min=chosen["cyc_dense_min"],
-                  cyc_long_segment=chosen["cyc_long_segment"])
+                  cyc_long_segment=chosen["cyc_long_segment"], cyc_spill_bits=chosen["cyc_spill_bits"])
         with fg.Handle(device=0, **kw) as h2:
             raw, net = _run(h2, g)
             np.testing.assert_array_equal(net, onet)
