@@ -169,6 +169,7 @@ struct CycArgs {
   int gbits;              // global tables: cyc_gmem_blocks() << gbits slots each array
   uint32_t* gkeys;        // NULL when both global-table classes are empty
   uint32_t* gcnt;
+  uint32_t* gtouch;       // cyc_gmem_blocks() << (gbits - 1) claimed-slot lists
   u64* r12r;
   int* err;
   int64_t cap_bound;      // bound on distinct tops of one vertex (n when unknown)

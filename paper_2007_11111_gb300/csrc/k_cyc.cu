@@ -59,6 +59,11 @@ template <bool GMEM>
 struct Table {
   uint32_t* keys;
   uint32_t* cnts;
+  // global tables: the slots claimed since the last pass C (so that pass C
+  // visits only those), with room for tcap entries
+  uint32_t* touched = nullptr;
+  int* ntouched = nullptr;
+  int tcap = 0;
   __device__ __forceinline__ uint32_t load_key(uint32_t h) const {
     if (GMEM) return __ldcg(keys + h);
     return *((volatile uint32_t*)keys + h);
@@ -83,7 +88,14 @@ struct Table {
       uint32_t k = load_key(h);
       if (k == EMPTY_KEY) {
         k = atomicCAS(keys + h, EMPTY_KEY, key);
-        if (k == EMPTY_KEY) k = key;
+        if (k == EMPTY_KEY) {
+          k = key;
+          if (GMEM) {
+            const int pos = atomicAdd(ntouched, 1);
+            if (pos < tcap) touched[pos] = h;
+            else atomicOr(err, ERR_HASH_FULL);
+          }
+        }
       }
       if (k == key) {
         atomicAdd(cnts + h, 1u);
@@ -465,7 +477,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
                                                   const int64_t* __restrict__ wc, const int32_t* __restrict__ list,
                                                   const int32_t* __restrict__ cnt, int* next, u64* r12r, int64_t n,
                                                   const int64_t* __restrict__ wcn, int32_t hub_lo, int tbits,
-                                                  int dense_words, int long_seg, uint32_t* gkeys,
+                                                  int dense_words, int long_seg, uint32_t* gkeys, uint32_t* gtouch,
                                                   uint32_t* gcnt, int64_t cap_bound, int* err) {
   constexpr bool DENSE = MODE == 1 || MODE == 4;
   constexpr bool GMEM = MODE == 3 || MODE == 4;
@@ -487,10 +499,14 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
   uint32_t* after = reinterpret_cast<uint32_t*>(S.misc + 4);
   uint32_t* dense = after;
   uint32_t* hbase = DENSE ? after + dense_words : after;
+  __shared__ int s_ntouched;
   Table<GMEM> T;
   if (GMEM) {
     T.keys = gkeys + ((size_t)blockIdx.x << tbits);
     T.cnts = gcnt + ((size_t)blockIdx.x << tbits);
+    T.touched = gtouch + ((size_t)blockIdx.x << (tbits - 1));
+    T.ntouched = &s_ntouched;
+    T.tcap = 1 << (tbits - 1);
   } else {
     T.keys = hbase;
     T.cnts = hbase + (1 << tbits);
@@ -508,11 +524,11 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
     return (dense[i >> 1] >> ((i & 1u) << 4)) & 0xFFFFu;
   };
 
-  // Shared-memory tables and the dense window start empty; pass C empties
-  // what it reads, so each vertex finds them empty again. Global tables are
-  // cleared per vertex (only the part the vertex uses).
-  if (!GMEM)
-    for (uint32_t i = tid; i < (1u << tbits); i += blockDim.x) T.clear(i);
+  // Every table and the dense window start empty; pass C empties what it
+  // reads (for a global table: the slots listed as claimed), so each vertex
+  // finds them empty again.
+  for (uint32_t i = tid; i < (1u << tbits); i += blockDim.x) T.clear(i);
+  if (tid == 0) s_ntouched = 0;
   if (DENSE)
     for (int i = tid; i < (hub_n + 1) >> 1; i += blockDim.x) dense[i] = 0u;
   for (;;) {
@@ -533,10 +549,6 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
       if (hb > tbits) hb = tbits;  // the class (or the table sizing) guarantees 2 * cap <= 2^tbits
     }
     const uint32_t H = 1u << hb;
-    if (GMEM) {
-      for (uint32_t i = tid; i < H; i += blockDim.x) T.clear(i);
-      __syncthreads();
-    }
 
     const Mids M = mids_of(orp, ocol, irp, iin, w);
     const bool single = M.K <= CH;
@@ -600,20 +612,38 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
         }
       }
     }
-    for (uint32_t i = tid; i < H; i += blockDim.x) {
-      const uint32_t key = T.load_key(i);
-      if (key != EMPTY_KEY) {
-        const u64 c = T.load_cnt(i);
+    if (GMEM) {
+      const int nt = min(s_ntouched, T.tcap);
+      for (int i = tid; i < nt; i += blockDim.x) {
+        const uint32_t h = __ldcg(T.touched + i);
+        const uint32_t key = T.load_key(h);
+        const u64 c = T.load_cnt(h);
         if (c >= 2) {
           const u64 v = c * (c - 1) / 2;
           atomicAdd(&r12r[key], v);
           accw += v;
         }
-        if (!GMEM) T.clear(i);
+        T.clear(h);
+      }
+    } else {
+      for (uint32_t i = tid; i < H; i += blockDim.x) {
+        const uint32_t key = T.load_key(i);
+        if (key != EMPTY_KEY) {
+          const u64 c = T.load_cnt(i);
+          if (c >= 2) {
+            const u64 v = c * (c - 1) / 2;
+            atomicAdd(&r12r[key], v);
+            accw += v;
+          }
+          T.clear(i);
+        }
       }
     }
     accw = block_sum(accw, red);
-    if (tid == 0 && accw) atomicAdd(&r12r[w], accw);
+    if (tid == 0) {
+      if (accw) atomicAdd(&r12r[w], accw);
+      if (GMEM) s_ntouched = 0;
+    }
     __syncthreads();
   }
 }
@@ -757,7 +787,8 @@ void launch_block(const CycArgs& a, int cls, int tbits, int dense_words, cudaStr
   const int grid = MODE >= 3 ? gmem_blocks() : num_sms() * occupancy((const void*)k_cyc_block<MODE, BT>, BT, smem);
   k_cyc_block<MODE, BT><<<grid, BT, smem, st>>>(a.orp, a.ocol, a.irp, a.iin, a.wc, a.lists + cls * a.list_stride,
                                                 a.counts + cls, a.next + cls, a.r12r, a.n, a.wcn, a.hub_lo, tbits,
-                                                dense_words, a.long_seg, a.gkeys, a.gcnt, a.cap_bound, a.err);
+                                                dense_words, a.long_seg, a.gkeys, a.gtouch, a.gcnt, a.cap_bound,
+                                                a.err);
   note_launch();
 }
 
