@@ -106,7 +106,7 @@ typedef struct {
     int tri_group_lanes;
     /* tri_warp_max: vertices whose out-degree in the degree order is at most
      *   this run the triangle passes one warp per vertex instead of one block
-     *   (0 = off, at most 32; default 0). */
+     *   (at most 32; 0 selects the default 32; -1 turns the warp class off). */
     int tri_warp_max;
     /* cyc_warp_bits: log2 of the per-warp hash-table slots of the 4-cycle
      *   stage's warp class, which takes vertices with at most 2^(bits-1)

@@ -231,7 +231,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
     // warp-per-vertex bound
     const int t_bounds[][6] = {{128, 512, 4, 4, 32, 32}, {128, 512, 4, 4, 32, 16}, {128, 512, 4, 4, 8, 32},
                                {64, 256, 4, 4, 32, 32},  {256, 768, 4, 4, 32, 32}, {128, 512, 2, 4, 32, 32},
-                               {128, 512, 4, 4, 16, 0},  {64, 256, 4, 4, 32, 0},   {128, 384, 4, 2, 32, 32}};
+                               {128, 512, 4, 4, 16, -1}, {64, 256, 4, 4, 32, -1},  {128, 384, 4, 2, 32, 32}};
     const int wbits[] = {8, 9, 10};
     const int spans[] = {0, 16384, 32768, 65536, 90112};
     const int threads[] = {128, 256, 512, 1024};
@@ -243,7 +243,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
       t.tri_loads = tb[2];
       t.tri_hash_factor = tb[3];
       t.tri_group = tb[4];
-      t.tri_warp = tb[5];
+      t.tri_warp = tb[5] < 0 ? 0 : tb[5];
       if (t.tri_t0 != start.tri_t0 || t.tri_t1 != start.tri_t1 || t.tri_loads != start.tri_loads ||
           t.tri_hash_factor != start.tri_hash_factor || t.tri_group != start.tri_group || t.tri_warp != start.tri_warp)
         tri_c.push_back(t);

@@ -112,8 +112,8 @@ fglt_status tuning_from_options(const fglt_options& o, Tuning* t) {
   if (x.tri_loads != 2 && x.tri_loads != 4) return FGLT_ERR_INVALID_ARG;
   if (o.tri_hash_factor) x.tri_hash_factor = o.tri_hash_factor;
   if (x.tri_hash_factor != 2 && x.tri_hash_factor != 4) return FGLT_ERR_INVALID_ARG;
-  if (o.tri_warp_max < 0 || o.tri_warp_max > tri_warp_max()) return FGLT_ERR_INVALID_ARG;
-  x.tri_warp = o.tri_warp_max;
+  if (o.tri_warp_max < -1 || o.tri_warp_max > tri_warp_max()) return FGLT_ERR_INVALID_ARG;
+  if (o.tri_warp_max) x.tri_warp = o.tri_warp_max < 0 ? 0 : o.tri_warp_max;
   if (o.tri_group_lanes) x.tri_group = o.tri_group_lanes;
   if (x.tri_group != 8 && x.tri_group != 16 && x.tri_group != 32) return FGLT_ERR_INVALID_ARG;
   if (o.cyc_warp_bits) x.cyc_warp_bits = o.cyc_warp_bits;
@@ -141,7 +141,7 @@ void tuning_to_options(const Tuning& t, fglt_options* o) {
   o->tri_probe_loads = t.tri_loads;
   o->tri_hash_factor = t.tri_hash_factor;
   o->tri_group_lanes = t.tri_group;
-  o->tri_warp_max = t.tri_warp;
+  o->tri_warp_max = t.tri_warp ? t.tri_warp : -1;
   o->cyc_warp_bits = t.cyc_warp_bits;
   for (int c = 0; c < 3; ++c) o->cyc_mid_threads[c] = t.cyc_mid_threads[c];
   o->cyc_heavy_threads = t.cyc_heavy_threads;

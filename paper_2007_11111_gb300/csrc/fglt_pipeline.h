@@ -47,7 +47,7 @@ struct Tuning {
   int tri_loads = 4;
   int tri_hash_factor = 4;
   int tri_group = 32;
-  int tri_warp = 0;  // out-degrees up to this run one warp per vertex (0: off)
+  int tri_warp = 32;  // out-degrees up to this run one warp per vertex (0: off)
   int cyc_warp_bits = 10;
   int cyc_mid_threads[3] = {256, 256, 256};
   int cyc_heavy_threads = 1024;

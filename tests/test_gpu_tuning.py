@@ -18,6 +18,7 @@ SETTINGS = [
     dict(tri_class_bounds=(2, 3), tri_group_lanes=8),
     dict(tri_group_lanes=16, tri_probe_loads=2, tri_warp_max=32),
     dict(tri_warp_max=16, tri_class_bounds=(8, 20)),
+    dict(tri_warp_max=-1, tri_class_bounds=(64, 256)),
     dict(tri_warp_max=32, tri_probe_loads=2, tri_class_bounds=(2, 3)),
     dict(tri_class_bounds=(8, 1024), tri_probe_loads=4, tri_hash_factor=4),
     dict(tri_class_bounds=(3, 2000), tri_probe_loads=4),
@@ -74,7 +75,7 @@ def test_invalid_settings_rejected():
                 dict(cyc_warp_bits=5), dict(cyc_mid_threads=(96, 256, 256)), dict(cyc_heavy_threads=300),
                 dict(cyc_hub_span=-1), dict(cyc_hub_span=90113), dict(tri_probe_loads=3),
                 dict(tri_hash_factor=3), dict(cyc_mid_threads=(64, 256, 256)), dict(cyc_dense_min=5000),
-                dict(tri_group_lanes=4), dict(cyc_long_segment=1), dict(tri_warp_max=33), dict(cyc_spill_bits=14)):
+                dict(tri_group_lanes=4), dict(cyc_long_segment=1), dict(tri_warp_max=33), dict(cyc_spill_bits=14), dict(tri_warp_max=-2)):
         with pytest.raises(fg.FgltError) as e:
             fg.Handle(device=0, **bad)
         assert e.value.status == fg.FGLT_ERR_INVALID_ARG
