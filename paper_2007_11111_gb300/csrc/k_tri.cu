@@ -155,11 +155,11 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int6
   if (SMEM_BM) {
     lists_base = reinterpret_cast<int32_t*>(filt + FWmax);
     bm = reinterpret_cast<uint32_t*>(lists_base + nwarps * (Dmax + Wmax));
-    k2loc = bm + (size_t)Dmax * Wmax;
+    k2loc = bm + (size_t)Dmax * (Wmax + 1);
   } else {
-    uint32_t* slot = gbm + (size_t)blockIdx.x * ((size_t)Dmax * Wmax + (size_t)nwarps * (Dmax + Wmax));
+    uint32_t* slot = gbm + (size_t)blockIdx.x * ((size_t)Dmax * (Wmax + 1) + (size_t)nwarps * (Dmax + Wmax));
     bm = slot;
-    lists_base = reinterpret_cast<int32_t*>(slot + (size_t)Dmax * Wmax);
+    lists_base = reinterpret_cast<int32_t*>(slot + (size_t)Dmax * (Wmax + 1));
     k2loc = filt + FWmax;
   }
   int32_t* ylist = lists_base + warp * (Dmax + Wmax);
@@ -182,7 +182,10 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int6
 
     for (int i = tid; i < (1 << hb); i += blockDim.x) keys[i] = EMPTY_KEY;
     for (int i = tid; i < (1 << (fb - 5)); i += blockDim.x) filt[i] = 0u;
-    for (int i = tid; i < D * W; i += blockDim.x) bm[i] = 0u;
+    // bitmap rows at an odd stride of words: lanes reading different rows
+    // at the same word offset hit different shared-memory banks
+    const int WS = W | 1;
+    for (int i = tid; i < D * WS; i += blockDim.x) bm[i] = 0u;
     for (int i = tid; K4 && i < D; i += blockDim.x) k2loc[i] = 0u;
     __syncthreads();
     for (int x = tid; x < D; x += blockDim.x) {
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int6
     for (int ib = grp.first; ib < D; ib += grp.stride) {
       const int32_t b = ocol[base + ib];
       const int64_t bb = orp[b], be = orp[b + 1];
-      uint32_t* row = bm + (size_t)ib * W;
+      uint32_t* row = bm + (size_t)ib * WS;
       auto probe = [&](int32_t c, int64_t k) {
         if (c <= lastA) {
           ++probes;
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int6
             const int ic = table_find(keys, vals, (uint32_t)c, hb);
             if (ic >= 0) {
               atomicOr(&row[ic >> 5], 1u << (ic & 31));
-              atomicOr(&bm[(size_t)ic * W + (ib >> 5)], 1u << (ib & 31));
+              atomicOr(&bm[(size_t)ic * WS + (ib >> 5)], 1u << (ib & 31));
               atomicAdd(&C3o[k], 1);  // edge b -> c
             }
           }
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int6
     // twice the 4-cliques {a, x, ., .}.
     u64 tri2x = 0;
     for (int x = warp; x < D; x += nwarps) {
-      const uint32_t* Sx = bm + (size_t)x * W;
+      const uint32_t* Sx = bm + (size_t)x * WS;
       int deg = 0, nzw = 0, nup = 0;
       const int xw = x >> 5;
       const uint32_t above = ~((2u << (x & 31)) - 1u);  // bits of the word of x above x
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int6
         int kx = 0;
         for (int i = lane; i < nup; i += 32) {
           const int y = ylist[i];
-          const uint32_t* Sy = bm + (size_t)y * W;
+          const uint32_t* Sy = bm + (size_t)y * WS;
           int t = 0;
           for (int q = 0; q < nzw; ++q) {
             const int w = wlist[q];
@@ -574,7 +577,7 @@ size_t tri1_smem_impl(int D, bool smem_bm, int hf) {
   const size_t W = (size_t)(D + 31) / 32;
   size_t bytes = (size_t)H * 8 + (size_t)host_filter_words(D) * 4;
   bytes += (size_t)D * 4;  // per-vertex 4-clique tallies
-  if (smem_bm) bytes += (size_t)(TRI_T / 32) * (D + W) * 4 + (size_t)D * W * 4;  // lists and bitmap
+  if (smem_bm) bytes += (size_t)(TRI_T / 32) * (D + W) * 4 + (size_t)D * (W + 1) * 4;  // lists and bitmap
   return (bytes + 15) & ~(size_t)15;
 }
 
@@ -638,7 +641,7 @@ static int tri1_grid(int dpmax, bool smem_bm, int hf) {
 size_t tri1_gbm_bytes(int dpmax, int hf) {
   if (dpmax < 2 || tri1_bitmap_fits_smem(dpmax, hf)) return 0;
   const size_t W = (size_t)(dpmax + 31) / 32;
-  const size_t per_block = (size_t)dpmax * W + (size_t)(TRI_T_BIG / 32) * ((size_t)dpmax + W);  // bitmap + lists
+  const size_t per_block = (size_t)dpmax * (W + 1) + (size_t)(TRI_T_BIG / 32) * ((size_t)dpmax + W);  // bitmap + lists
   return (size_t)tri1_grid(dpmax, false, hf) * per_block * 4;
 }
 
