@@ -83,7 +83,7 @@ typedef struct {
      * selects the default):
      * cyc_hub_span: number of top-ranked (highest-degree) vertices that get
      *   dense 16-bit shared-memory counters in the 4-cycle stage (at most
-     *   90112). 0 selects 32768, or 65536 for graphs above 2^21 vertices.
+     *   90112). 0 selects 32768, or 65536 for graphs above 2^22 vertices.
      *   Smaller values move work to the hash-table paths and raise occupancy. */
     int cyc_hub_span;
     /* tri_class_bounds: the triangle passes split the vertices by out-degree
@@ -121,7 +121,7 @@ typedef struct {
     int cyc_heavy_threads;
     /* cyc_dense_min: vertices with more possible 4-cycle tops than this
      *   (and few tops outside the dense window) use the dense-window class
-     *   instead of a hash-table class (1 .. 4096; default 4096). */
+     *   instead of a hash-table class (1 .. 4096; default 2048). */
     int cyc_dense_min;
     /* cyc_long_segment: in the block classes of the 4-cycle stage, a
      *   middle's segment of tops at least this long is walked by one warp

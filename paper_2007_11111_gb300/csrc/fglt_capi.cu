@@ -306,11 +306,20 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
            }, threads, 4)) != FGLT_OK) return s;
     if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_heavy_threads == v) return false; t.cyc_heavy_threads = v; return true; },
                      threads + 2, 2)) != FGLT_OK) return s;
-    if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_hub_span == v) return false; t.cyc_hub_span = v; return true; },
-                     spans, 5)) != FGLT_OK) return s;
+    // The dense window and the dense-class threshold decide together which
+    // vertices go dense, spill or hash: try them as pairs.
     const int dmins[] = {1024, 2048, 4096};
-    if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_dense_min == v) return false; t.cyc_dense_min = v; return true; },
-                     dmins, 3)) != FGLT_OK) return s;
+    int pairs[5 * 3];
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 3; ++b) pairs[a * 3 + b] = a * 3 + b;
+    if ((s = try_cyc([&](Tuning& t, int v) {
+           const int sp = spans[v / 3], dm = dmins[v % 3];
+           if (t.cyc_hub_span == sp && t.cyc_dense_min == dm) return false;
+           if (sp == 90112 && dm != 4096) return false;  // the widest window only pays for the heaviest vertices
+           t.cyc_hub_span = sp;
+           t.cyc_dense_min = dm;
+           return true;
+         }, pairs, 15)) != FGLT_OK) return s;
     const int sbits[] = {12, 13, 11};
     if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_spill_bits == v) return false; t.cyc_spill_bits = v; return true; },
                      sbits, 3)) != FGLT_OK) return s;

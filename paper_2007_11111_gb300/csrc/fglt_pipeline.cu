@@ -423,7 +423,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   if (need_cyc) {
     // Dense window of top ranks: 32768 by default, 65536 for graphs above
     // 2^21 vertices (their wedge tops spread over more hubs).
-    int64_t span = tu.cyc_hub_span > 0 ? tu.cyc_hub_span : (n > (1 << 21) ? 65536 : 32768);
+    int64_t span = tu.cyc_hub_span > 0 ? tu.cyc_hub_span : (n > (1 << 22) ? 65536 : 32768);
     const int32_t hub_lo = (int32_t)std::max<int64_t>(0, n - span);
     const int spill_bits = cyc_fit_spill_bits((int)std::min<int64_t>(span, n), tu.cyc_spill_bits, tu.cyc_heavy_threads);
     int64_t *wc, *wcn, *irp;

@@ -52,7 +52,7 @@ struct Tuning {
   int cyc_mid_threads[3] = {256, 256, 256};
   int cyc_heavy_threads = 1024;
   int cyc_hub_span = 0;
-  int cyc_dense_min = 4096;
+  int cyc_dense_min = 2048;
   int cyc_long_segment = 32;
   int cyc_spill_bits = 11;
 };

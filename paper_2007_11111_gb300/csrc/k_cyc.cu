@@ -467,8 +467,8 @@ __device__ __forceinline__ void walk_chunk(const Segs& S, const int32_t* __restr
   }
 }
 
-size_t seg_bytes(int ch) {  // segment arrays, plus 16 bytes to align what follows them
-  return (size_t)ch * 8 * 3 + 64 * 8 + (size_t)(ch + 1) * 4 + (size_t)ch * 4 * 3 + 16 + 16;
+size_t seg_bytes(int ch) {
+  return (size_t)ch * 8 * 3 + 64 * 8 + (size_t)(ch + 1) * 4 + (size_t)ch * 4 * 3 + 16;
 }
 
 template <int MODE, int BT>
@@ -496,8 +496,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
   S.llen = S.rv + CH;
   S.lrv = S.llen + CH;
   S.misc = S.lrv + CH;
-  // the dense window starts on a 16-byte boundary (pass C reads it 4 words at a time)
-  uint32_t* after = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(S.misc + 4) + 15) & ~(uintptr_t)15);
+  uint32_t* after = reinterpret_cast<uint32_t*>(S.misc + 4);
   uint32_t* dense = after;
   uint32_t* hbase = DENSE ? after + dense_words : after;
   __shared__ int s_ntouched;
@@ -597,34 +596,18 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
     // Pass C: top u and bottom w gain binom(cnt[u], 2).
     u64 accw = 0;
     if (DENSE) {
-      // word i holds the counters of tops hub_lo + 2i and hub_lo + 2i + 1;
-      // four words per load, all-zero groups skipped
-      auto flush_word = [&](int i, uint32_t x) {
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          const u64 c = (x >> (16 * half)) & 0xFFFFu;
-          if (c >= 2) {
-            const u64 v = c * (c - 1) / 2;
-            atomicAdd(&r12r[hub_lo + 2 * i + half], v);
-            accw += v;
-          }
-        }
-      };
-      const int words = (hub_n + 1) >> 1;
-      uint4* d4 = reinterpret_cast<uint4*>(dense);
-      for (int q = tid; q < (words >> 2); q += blockDim.x) {
-        const uint4 x = d4[q];
-        if ((x.x | x.y | x.z | x.w) == 0u) continue;
-        if (x.x) flush_word(4 * q, x.x);
-        if (x.y) flush_word(4 * q + 1, x.y);
-        if (x.z) flush_word(4 * q + 2, x.z);
-        if (x.w) flush_word(4 * q + 3, x.w);
-        d4[q] = make_uint4(0u, 0u, 0u, 0u);
-      }
-      for (int i = ((words >> 2) << 2) + tid; i < words; i += blockDim.x) {
-        const uint32_t x = dense[i];
+      for (int i = tid; i < (hub_n + 1) >> 1; i += blockDim.x) {
+        const uint32_t x = dense[i];  // counters of tops hub_lo + 2i and hub_lo + 2i + 1
         if (x) {
-          flush_word(i, x);
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const u64 c = (x >> (16 * half)) & 0xFFFFu;
+            if (c >= 2) {
+              const u64 v = c * (c - 1) / 2;
+              atomicAdd(&r12r[hub_lo + 2 * i + half], v);
+              accw += v;
+            }
+          }
           dense[i] = 0u;
         }
       }
