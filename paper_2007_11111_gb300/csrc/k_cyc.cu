@@ -420,7 +420,15 @@ __device__ __forceinline__ void walk_long(const Segs& S, const int32_t* __restri
     const int32_t* p = ocol + S.lst[i];
     const int len = S.llen[i];
     u64 sum = 0;
-    for (int q = lane; q < len; q += 32) sum += g((uint32_t)__ldg(p + q));
+    // four coalesced loads in flight before the first update
+    for (int q = lane; q < len; q += 128) {
+      uint32_t x[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) x[r] = q + 32 * r < len ? (uint32_t)__ldg(p + q + 32 * r) : 0u;
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (q + 32 * r < len) sum += g(x[r]);
+    }
     done(S.lrv[i], sum);
   }
 }
@@ -445,9 +453,12 @@ __device__ __forceinline__ void walk_chunk(const Segs& S, const int32_t* __restr
     const int mid = (lo + hi + 1) >> 1;
     if (S.pre[mid] <= w0) lo = mid; else hi = mid - 1;
   }
-  int base = lo;
   const uint32_t upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-  for (int t0 = w0; t0 < w1; t0 += 32) {
+  // Step t0: this lane's owner segment j and its list entry u. The next
+  // step's load is issued before f runs on the current one (two loads in
+  // flight per lane).
+  int base = lo;  // owner of wedge t0
+  auto locate = [&](int t0, int& j, uint32_t& u, bool& valid, int& nbase) {
     const int jb = base + 1 + lane;
     uint32_t bit = 0;
     if (jb < ns) {
@@ -455,15 +466,30 @@ __device__ __forceinline__ void walk_chunk(const Segs& S, const int32_t* __restr
       if (r < 32) bit = 1u << r;
     }
     const uint32_t M = __reduce_or_sync(0xffffffffu, bit);
-    const int j = base + __popc(M & upto);
+    j = base + __popc(M & upto);
     const int t = t0 + lane;
-    const bool valid = t < w1;
-    uint32_t u = 0;
+    valid = t < w1;
+    u = 0;
     if (valid) u = (uint32_t)__ldg(ocol + S.st[j] + (t - S.pre[j]));
-    f(u, j, valid);
     // owner of t0 + 32
-    base += __popc(M);
-    if (base + 1 < ns && S.pre[base + 1] == t0 + 32) ++base;
+    nbase = base + __popc(M);
+    if (nbase + 1 < ns && S.pre[nbase + 1] == t0 + 32) ++nbase;
+  };
+  int j, nbase;
+  uint32_t u;
+  bool valid;
+  locate(w0, j, u, valid, nbase);
+  for (int t0 = w0; t0 < w1; t0 += 32) {
+    base = nbase;
+    int j2 = 0, nb2 = nbase;
+    uint32_t u2 = 0;
+    bool v2 = false;
+    if (t0 + 32 < w1) locate(t0 + 32, j2, u2, v2, nb2);
+    f(u, j, valid);
+    j = j2;
+    u = u2;
+    valid = v2;
+    nbase = nb2;
   }
 }
 
