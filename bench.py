@@ -470,6 +470,7 @@ def run_gpu(args, rank, world, local_rank):
     achieved = ab / (stage_ms[dom] / 1000) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic_for(dom, args.workload),
+                "traffic_source": "ncu capture at the default tuning (profiles/traffic.json)",
                 "kernel": dom, "kernel_ms": stage_ms[dom], "algorithmic_bytes": ab,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s"}
