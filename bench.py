@@ -193,6 +193,64 @@ def cpu_baseline(threads=0):
 
 
 # ---------------------------------------------------------------------------
+# The library's entries beyond the full transform, timed on the benchmark
+# graph: the Sigma5 sub-dictionary transform, edge-list ingest and degree
+# relabelling. CUDA events on the launching stream, L2 flushed before each
+# timed call, mean of `reps` calls after two untimed ones.
+# ---------------------------------------------------------------------------
+def bench_extensions(fg, torch, dev, n, rp, ci, flush, full_ms, reps=5):
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.mean(ts), out
+
+    m = int(ci.numel()) // 2
+    out = {}
+    # Sigma5: the stages only the 4-node graphlets need are skipped
+    with fg.Handle(device=dev.index or 0, dictionary=fg.DICT_SIGMA5) as h5, fg.Handle(device=dev.index or 0) as hf:
+        raw5 = torch.empty((n, 5), dtype=torch.int64, device=dev)
+        net5 = torch.empty((n, 5), dtype=torch.int64, device=dev)
+        ms5, _ = timed(lambda: h5.transform(rp, ci, n, raw5, net5, stream=stream))
+        raw16, net16 = hf.transform(rp, ci, n, stream=stream)
+        same = bool(torch.equal(raw5, raw16[:, :5]) and torch.equal(net5, net16[:, :5]))
+        del raw16, net16
+        out["sub_dictionary"] = {
+            "dictionary": "Sigma5 (sigma_0 .. sigma_4)", "ms": ms5, "edges_per_s": m / (ms5 / 1e3),
+            "full_ms": full_ms, "speedup_vs_full": full_ms / ms5, "bit_exact_vs_full_columns": same}
+        # ingest: one direction of every edge, in a seeded random order
+        rows = torch.repeat_interleave(torch.arange(n, device=dev, dtype=torch.int32), torch.diff(rp))
+        keep = rows < ci
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(0)
+        order = torch.randperm(int(keep.sum().item()), device=dev, generator=gen)
+        src = rows[keep][order].contiguous()
+        dst = ci[keep][order].contiguous()
+        del rows, keep, order
+        msi, (irp, ici) = timed(lambda: hf.csr_from_edges(src, dst, n, stream=stream))
+        out["ingest"] = {"pairs": int(src.numel()), "ms": msi, "pairs_per_s": src.numel() / (msi / 1e3),
+                         "equal_to_input_csr": bool(torch.equal(irp, rp) and torch.equal(ici, ci))}
+        del src, dst, irp, ici
+        # degree relabelling (non-increasing degree)
+        msr, (rrp, _, _) = timed(lambda: hf.relabel_by_degree(rp, ci, n, stream=stream))
+        out["relabel"] = {"ms": msr, "edges_per_s": m / (msr / 1e3),
+                          "degree_ordered": bool((torch.diff(torch.diff(rrp)) <= 0).all().item())}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Batched (20,000 small graphs in one block-diagonal launch) and served
 # (continuous batching of a Poisson request stream) forms, each against one
 # single-graph transform per graph on the same GPU.
@@ -490,6 +548,8 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if not args.no_extensions and rank == 0:
+        line["extensions"] = bench_extensions(fg, torch, dev, g.n, rp, ci, flush, ms)
     if not args.no_batched:
         line["batched"] = bench_batched(fg, torch, dev)
     if args.serving_full:
@@ -516,6 +576,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-extensions", action="store_true",
+                    help="skip timing the Sigma5 transform, edge-list ingest and relabelling")
     ap.add_argument("--set", action="append", metavar="NAME=VALUE",
                     help="tuning field of the handle, e.g. --set cyc_spill_bits=13 (with --no-autotune to keep it)")
     ap.add_argument("--serving-full", action="store_true",

@@ -211,13 +211,13 @@ fglt_status fglt_transform_batched(fglt_t handle, const void* rowptr, int rowptr
  * Autotuner: times the transform of the given graph (device buffers, as for
  * fglt_transform) under candidate settings of the tuning fields of
  * fglt_options (degree-class bounds of the triangle passes, hash-table sizes
- * and thread-block shapes of the 4-cycle classes, dense hub span), one
- * parameter at a time from the current settings, keeps every change that
- * lowers the device time of the stage it affects, and installs the result
- * on the handle for its later single-graph, host and batched calls (serving
- * lanes take the handle's settings when the first request is submitted).
- * The counts never depend on these settings. Runs about 12 + 2 *
- * reps transforms on `stream`; reps >= 1 timings per candidate (minimum
+ * and thread-block shapes of the 4-cycle classes, dense hub span and dense
+ * threshold, the last two as pairs), one parameter at a time from the
+ * current settings, keeps every change that lowers the device time of the
+ * stage it affects, and installs the result on the handle for its later
+ * single-graph, host and batched calls (serving lanes take the handle's
+ * settings when the first request is submitted). The counts never depend on
+ * these settings. Runs about 30 + 2 * reps transforms on `stream`; reps >= 1 timings per candidate (minimum
  * taken). chosen (nullable) receives the full option set in use afterwards.
  * tuned_ms / default_ms (nullable) receive the device time of one transform
  * with the chosen and with the starting settings.
@@ -245,6 +245,30 @@ fglt_status fglt_autotune(fglt_t handle, const void* rowptr, int rowptr_is_64bit
 fglt_status fglt_csr_from_edges(fglt_t handle, const int32_t* src, const int32_t* dst, int64_t num_edges,
                                 int64_t n, int64_t* out_rowptr, int32_t* out_colidx, int64_t* out_nnz,
                                 void* stream);
+
+/*
+ * Degree-ordered relabelling of a CSR graph (device buffers), for locality:
+ * vertex v gets the new id perm[v] = its position in non-increasing degree
+ * order (descending = 1) or non-decreasing degree order (descending = 0);
+ * vertices of equal degree take their positions in an unspecified order. The
+ * transform of the relabelled graph is the transform of the input with its
+ * rows permuted by perm (Sec. 2: the transform is invariant under graph
+ * isomorphism, vertex by vertex).
+ *   rowptr, colidx  the input CSR (int64 or int32 row pointers, int32
+ *                   columns in [0, n)); it is not modified
+ *   out_rowptr      device int64[n+1], the relabelled row pointers
+ *   out_colidx      device int32[rowptr[n]], the relabelled columns, each
+ *                   row sorted ascending (may be NULL when rowptr[n] = 0)
+ *   out_perm        device int32[n], perm[old id] = new id
+ * FGLT_ERR_INVALID_GRAPH if a column is outside [0, n) (the outputs are then
+ * unspecified); FGLT_ERR_UNSUPPORTED above 2^31 - 2 vertices. The outputs
+ * must not overlap the inputs. Uses the handle's workspace; returns after
+ * the work completed on stream (NULL = the handle's stream).
+ */
+fglt_status fglt_csr_relabel_by_degree(fglt_t handle, const void* rowptr, int rowptr_is_64bit,
+                                       const int32_t* colidx, int64_t n, int descending,
+                                       int64_t* out_rowptr, int32_t* out_colidx, int32_t* out_perm,
+                                       void* stream);
 
 /* Per-stage device times (ms) of the last transform on this handle; requires
  * fglt_options.profile_stages = 1. names[i] points to static strings.

@@ -100,7 +100,7 @@ EXPORTED = [
     "fglt_options_default", "fglt_create", "fglt_destroy", "fglt_status_string", "fglt_last_cuda_error",
     "fglt_transform", "fglt_transform_host", "fglt_transform_batched", "fglt_stage_times", "fglt_work_counters",
     "fglt_stream_submit", "fglt_stream_poll", "fglt_stream_cancel", "fglt_transform_noalloc", "fglt_autotune",
-    "fglt_csr_from_edges",
+    "fglt_csr_from_edges", "fglt_csr_relabel_by_degree",
 ]
 
 _lib = None
@@ -137,6 +137,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                      c_int, ctypes.POINTER(c_int)]
     lib.fglt_transform_noalloc.argtypes = [vp, c_int, vp, i64, vp, vp, vp]
     lib.fglt_csr_from_edges.argtypes = [h_t, vp, vp, i64, i64, vp, vp, ctypes.POINTER(i64), vp]
+    lib.fglt_csr_relabel_by_degree.argtypes = [h_t, vp, c_int, vp, i64, c_int, vp, vp, vp, vp]
     lib.fglt_autotune.argtypes = [h_t, vp, c_int, vp, i64, c_int, vp, ctypes.POINTER(fglt_options),
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
     lib.fglt_work_counters.argtypes = [h_t, ctypes.POINTER(ctypes.c_int64), c_int, ctypes.POINTER(c_int)]
@@ -261,6 +262,15 @@ def fglt_csr_from_edges(h, src, dst, num_edges: int, n: int, out_rowptr, out_col
                                       _ptr(out_colidx), ctypes.byref(nnz), _stream_ptr(stream)),
            "fglt_csr_from_edges", h)
     return nnz.value
+
+
+def fglt_csr_relabel_by_degree(h, rowptr, rowptr_is_64bit: int, colidx, n: int, descending: int, out_rowptr,
+                               out_colidx, out_perm, stream=None) -> None:
+    """Degree-ordered relabelling of a CSR (device buffers); perm[old] = new."""
+    _check(load().fglt_csr_relabel_by_degree(h, _ptr(rowptr), int(rowptr_is_64bit), _ptr(colidx), int(n),
+                                             int(descending), _ptr(out_rowptr), _ptr(out_colidx), _ptr(out_perm),
+                                             _stream_ptr(stream)),
+           "fglt_csr_relabel_by_degree", h)
 
 
 def fglt_stage_times(h) -> dict:
@@ -414,6 +424,20 @@ class Handle:
         colidx = torch.empty(max(2 * src.numel(), 1), dtype=torch.int32, device=src.device)
         nnz = fglt_csr_from_edges(self.h, src, dst, src.numel(), n, rowptr, colidx, stream)
         return rowptr, colidx[:nnz]
+
+    def relabel_by_degree(self, rowptr, colidx, n: int, descending: bool = True, stream=None):
+        """Degree-ordered relabelling (torch CUDA tensors) -> (rowptr int64[n+1],
+        colidx int32[nnz], perm int32[n]) with perm[old id] = new id: new ids
+        follow non-increasing (descending) or non-decreasing degree."""
+        import torch
+        rp64 = 1 if rowptr.dtype == torch.int64 else 0
+        nnz = int(rowptr[n].item()) if n > 0 else 0
+        out_rp = torch.empty(n + 1, dtype=torch.int64, device=rowptr.device)
+        out_ci = torch.empty(max(nnz, 1), dtype=torch.int32, device=rowptr.device)
+        perm = torch.empty(max(n, 1), dtype=torch.int32, device=rowptr.device)
+        fglt_csr_relabel_by_degree(self.h, rowptr, rp64, colidx, n, 1 if descending else 0, out_rp, out_ci, perm,
+                                   stream)
+        return out_rp, out_ci[:nnz], perm[:n]
 
     def autotune(self, rowptr, colidx, n: int, reps: int = 1, stream=None):
         """Autotunes on this graph (torch CUDA tensors); returns (tuning dict,

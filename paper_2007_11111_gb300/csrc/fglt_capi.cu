@@ -22,6 +22,7 @@ namespace {
 enum HandleBufId {
   X_H_ROWPTR = B_PIPELINE_COUNT, X_H_COLIDX, X_H_RAW, X_H_NET, X_BATCH_OFF,
   X_IN_DEG0, X_IN_RP0, X_IN_CUR, X_IN_TMP, X_IN_DEG, X_IN_SCAN, X_IN_CNT, X_IN_SORT,
+  X_RL_D, X_RL_HIST, X_RL_BASE, X_RL_CURSOR, X_RL_RANK, X_RL_INV, X_RL_NDEG,
   X_COUNT
 };
 
@@ -634,18 +635,86 @@ fglt_status fglt_csr_from_edges(fglt_t h, const int32_t* src, const int32_t* dst
   CK(launch_scan_i32_to_i64(static_cast<int32_t*>(deg0), n, rp0p, scan, st));
   CK(launch_edge_fill(src, dst, num_edges, n, rp0p, static_cast<int32_t*>(cur), static_cast<int32_t*>(tmp), st));
   int32_t* sort_scratch = nullptr;
-  if (hc[0] > 16384) {
-    int64_t P = 16384;
-    while (P < hc[0]) P <<= 1;
+  if (const int64_t sort_ints = sort_rows_scratch_ints(cap, hc[0])) {
     void* p = nullptr;
-    if ((s = need(h, X_IN_SORT, (size_t)P * 4, &p, st)) != FGLT_OK) return s;
+    if ((s = need(h, X_IN_SORT, (size_t)sort_ints * 4, &p, st)) != FGLT_OK) return s;
     sort_scratch = static_cast<int32_t*>(p);
   }
-  CK(launch_sort_rows(rp0p, n, hc[0], static_cast<int32_t*>(tmp), sort_scratch, st));
+  CK(launch_sort_rows(rp0p, n, hc[0], cap, static_cast<int32_t*>(tmp), sort_scratch, st));
   CK(launch_row_unique(rp0p, static_cast<int32_t*>(tmp), n, static_cast<int32_t*>(deg), nullptr, nullptr, st));
   CK(launch_scan_i32_to_i64(static_cast<int32_t*>(deg), n, out_rowptr, scan, st));
   CK(launch_row_unique(rp0p, static_cast<int32_t*>(tmp), n, nullptr, out_rowptr, out_colidx, st));
   return ws.read(out_nnz, out_rowptr + n, 8, st);
+}
+
+fglt_status fglt_csr_relabel_by_degree(fglt_t h, const void* rowptr, int rowptr_is_64bit, const int32_t* colidx,
+                                       int64_t n, int descending, int64_t* out_rowptr, int32_t* out_colidx,
+                                       int32_t* out_perm, void* stream) {
+  if (!h || n < 0 || (rowptr_is_64bit != 0 && rowptr_is_64bit != 1) || (descending != 0 && descending != 1) ||
+      !out_rowptr || (n > 0 && (!rowptr || !out_perm)))
+    return FGLT_ERR_INVALID_ARG;
+  if (n > 0x7ffffffeLL) return FGLT_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (cudaSetDevice(h->device) != cudaSuccess) return FGLT_ERR_CUDA;
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+  HandleWs ws(h, st);
+  fglt_status s;
+  if (n == 0) {
+    CK(cudaMemsetAsync(out_rowptr, 0, 8, st));
+    CK(cudaStreamSynchronize(st));
+    return FGLT_OK;
+  }
+  const bool rp64 = rowptr_is_64bit != 0;
+  int64_t nnz = 0;
+  if (rp64) {
+    if ((s = ws.read(&nnz, static_cast<const int64_t*>(rowptr) + n, 8, st)) != FGLT_OK) return s;
+  } else {
+    int32_t nnz32 = 0;
+    if ((s = ws.read(&nnz32, static_cast<const int32_t*>(rowptr) + n, 4, st)) != FGLT_OK) return s;
+    nnz = nnz32;
+  }
+  if (nnz < 0) return FGLT_ERR_INVALID_GRAPH;
+  if (nnz > 0 && (!colidx || !out_colidx)) return FGLT_ERR_INVALID_ARG;
+  void *d, *cnt, *rank, *inv, *ndeg;
+  if ((s = need(h, X_RL_D, (size_t)n * 4, &d, st)) != FGLT_OK) return s;
+  if ((s = need(h, X_IN_CNT, 16, &cnt, st)) != FGLT_OK) return s;
+  if ((s = need(h, X_RL_RANK, (size_t)n * 4, &rank, st)) != FGLT_OK) return s;
+  if ((s = need(h, X_RL_INV, (size_t)n * 4, &inv, st)) != FGLT_OK) return s;
+  if ((s = need(h, X_RL_NDEG, (size_t)n * 4, &ndeg, st)) != FGLT_OK) return s;
+  int32_t* c = static_cast<int32_t*>(cnt);  // [0] max degree, [1] error bits
+  CK(cudaMemsetAsync(cnt, 0, 16, st));
+  CK(launch_row_degree(rowptr, rp64, n, static_cast<int32_t*>(d), c, st));
+  int32_t dmax = 0;
+  if ((s = ws.read(&dmax, c, 4, st)) != FGLT_OK) return s;
+  // counting sort by degree, as for the transform's degree order
+  void *hist, *base, *cursor, *scan;
+  if ((s = need(h, X_RL_HIST, ((size_t)dmax + 1) * 4, &hist, st)) != FGLT_OK) return s;
+  if ((s = need(h, X_RL_BASE, ((size_t)dmax + 2) * 8, &base, st)) != FGLT_OK) return s;
+  if ((s = need(h, X_RL_CURSOR, ((size_t)dmax + 1) * 4, &cursor, st)) != FGLT_OK) return s;
+  if ((s = need(h, X_IN_SCAN, scan_temp_bytes(std::max<int64_t>(n, (int64_t)dmax + 1) + 1), &scan, st)) != FGLT_OK)
+    return s;
+  CK(cudaMemsetAsync(hist, 0, ((size_t)dmax + 1) * 4, st));
+  CK(cudaMemsetAsync(cursor, 0, ((size_t)dmax + 1) * 4, st));
+  CK(launch_degree_hist(static_cast<int32_t*>(d), n, static_cast<int32_t*>(hist), st));
+  CK(launch_scan_i32_to_i64(static_cast<int32_t*>(hist), (int64_t)dmax + 1, static_cast<int64_t*>(base), scan, st));
+  CK(launch_rank_assign(static_cast<int32_t*>(d), n, static_cast<int64_t*>(base), static_cast<int32_t*>(cursor),
+                        static_cast<int32_t*>(rank), static_cast<int32_t*>(inv), static_cast<int32_t*>(ndeg), st));
+  // inv and ndeg are rewritten for the requested direction
+  CK(launch_relabel_ids(static_cast<int32_t*>(rank), static_cast<int32_t*>(d), n, descending != 0, out_perm,
+                        static_cast<int32_t*>(inv), static_cast<int32_t*>(ndeg), st));
+  CK(launch_scan_i32_to_i64(static_cast<int32_t*>(ndeg), n, out_rowptr, scan, st));
+  CK(launch_relabel_fill(rowptr, rp64, colidx, out_perm, static_cast<int32_t*>(inv), n, out_rowptr, out_colidx,
+                         c + 1, st));
+  int32_t* sort_scratch = nullptr;
+  if (const int64_t sort_ints = sort_rows_scratch_ints(nnz, dmax)) {
+    void* p = nullptr;
+    if ((s = need(h, X_IN_SORT, (size_t)sort_ints * 4, &p, st)) != FGLT_OK) return s;
+    sort_scratch = static_cast<int32_t*>(p);
+  }
+  CK(launch_sort_rows(out_rowptr, n, dmax, nnz, out_colidx, sort_scratch, st));
+  int32_t errw = 0;
+  if ((s = ws.read(&errw, c + 1, 4, st)) != FGLT_OK) return s;
+  return (errw & ERR_BAD_GRAPH) ? FGLT_ERR_INVALID_GRAPH : FGLT_OK;
 }
 
 fglt_status fglt_work_counters(fglt_t h, int64_t* counters, int max_counters, int* count) {

@@ -55,9 +55,12 @@ cudaError_t launch_orient_count(const Csr& g, const int32_t* rank, const int32_t
 cudaError_t launch_orient_fill(const Csr& g, const int32_t* rank, const int64_t* orp, const int32_t* heavy,
                                const int32_t* nheavy, int64_t heavy_cap, int32_t* cursor, int32_t* ocol,
                                cudaStream_t st);
-// Sorts every oriented row ascending. Rows longer than 16384 use gscratch
-// (at least next_pow2(max row) int32).
-cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int32_t* ocol,
+// Sorts every row of a CSR ascending (entries = total row length, dpmax = the
+// longest row). Rows longer than 16384 are sorted one block per row in
+// gscratch, which must hold sort_rows_scratch_ints(entries, dpmax) int32
+// (none needed when dpmax <= 16384).
+int64_t sort_rows_scratch_ints(int64_t entries, int32_t dpmax);
+cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int64_t entries, int32_t* ocol,
                              int32_t* gscratch, cudaStream_t st);
 // Vertices (rank labels) with at least `min_out` out-neighbours.
 cudaError_t launch_worklist_outdeg(const int32_t* opc, int64_t n, int min_out, int32_t* list,
@@ -190,6 +193,16 @@ cudaError_t launch_edge_fill(const int32_t* src, const int32_t* dst, int64_t E, 
 // into deg; otherwise writes them to colidx at rowptr.
 cudaError_t launch_row_unique(const int64_t* rp0, const int32_t* tmp, int64_t n, int32_t* deg, const int64_t* rowptr,
                               int32_t* colidx, cudaStream_t st);
+// Degree relabelling: d[v] from the row pointers and *dmax = max d (dmax
+// zeroed by the caller); ids from the degree ranks (perm[v] = rank or n - 1 -
+// rank, inv = perm^-1, ndeg[perm[v]] = d[v]); rows of the relabelled CSR,
+// unsorted (ERR_BAD_GRAPH in *err for a column outside [0, n)).
+cudaError_t launch_row_degree(const void* rowptr, bool rp64, int64_t n, int32_t* d, int32_t* dmax, cudaStream_t st);
+cudaError_t launch_relabel_ids(const int32_t* rank, const int32_t* d, int64_t n, bool descending, int32_t* perm,
+                               int32_t* inv, int32_t* ndeg, cudaStream_t st);
+cudaError_t launch_relabel_fill(const void* rowptr, bool rp64, const int32_t* colidx, const int32_t* perm,
+                                const int32_t* inv, int64_t n, const int64_t* out_rowptr, int32_t* out_colidx,
+                                int* err, cudaStream_t st);
 
 // --- epilogue ------------------------------------------------------------------
 struct EpilogueIn {

@@ -307,12 +307,9 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
 
   mark(4);
   int32_t* sort_scratch = nullptr;
-  if (dpmax > 16384) {
-    int64_t P = 16384;
-    while (P < dpmax) P <<= 1;
-    NEED(B_SORT, P, sort_scratch);
-  }
-  CK(launch_sort_rows(orp, n, dpmax, ocol, sort_scratch, st));
+  const int64_t sort_ints = sort_rows_scratch_ints(m_or, dpmax);
+  if (sort_ints > 0) NEED(B_SORT, sort_ints, sort_scratch);
+  CK(launch_sort_rows(orp, n, dpmax, m_or, ocol, sort_scratch, st));
   // Triangle-pass work lists by out-degree; each class is launched with shared
   // memory sized for its largest out-degree.
   const int T0 = tu.tri_t0, T1 = tu.tri_t1;

@@ -5,6 +5,8 @@
 // most HEAVY_DEGREE and by a whole block otherwise (degree-binned scheduling:
 // power-law graphs have a few rows with 10^4-10^6 entries next to millions of
 // rows with a handful).
+#include <algorithm>
+
 #include "fglt_device.cuh"
 #include "fglt_kernels.h"
 
@@ -380,17 +382,39 @@ __global__ void k_sort_rows_block(const int64_t* __restrict__ orp, int64_t n, in
   }
 }
 
-__global__ void k_sort_rows_global(const int64_t* __restrict__ orp, int64_t n, int32_t* ocol, int32_t* scratch) {
-  for (int64_t r = 0; r < n; ++r) {
+// Rows longer than the shared-memory sort holds, listed (at most cap of
+// them; list[-1] is the count).
+__global__ void k_long_rows(const int64_t* __restrict__ orp, int64_t n, int32_t* list, int64_t cap) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < n; r0 += stride) {
+    const int64_t r = r0 + lane;
+    const bool take = r < n && orp[r + 1] - orp[r] > SORT_SMEM_MAX;
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    int pos0 = 0;
+    if (lane == 0 && m) pos0 = atomicAdd(list - 1, __popc(m));
+    pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+    const int64_t pos = (int64_t)pos0 + __popc(m & ((1u << lane) - 1));
+    if (take && pos < cap) list[pos] = (int32_t)r;
+  }
+}
+
+// One listed row per block at a time, bitonic-sorted in the block's own
+// power-of-two slot of scratch (P int32 per slot).
+__global__ void k_sort_rows_global(const int64_t* __restrict__ orp, const int32_t* __restrict__ list, int64_t cap,
+                                   int32_t* ocol, int32_t* scratch, int P) {
+  int32_t* slot = scratch + (size_t)blockIdx.x * P;
+  const int64_t count = min((int64_t)list[-1], cap);
+  for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
+    const int64_t r = list[i];
     const int64_t b = orp[r];
     const int64_t L = orp[r + 1] - b;
-    if (L <= SORT_SMEM_MAX) continue;
-    int P = SORT_SMEM_MAX;
-    while (P < L) P <<= 1;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) scratch[i] = i < L ? ocol[b + i] : 0x7fffffff;
+    int Q = SORT_SMEM_MAX;
+    while (Q < L) Q <<= 1;  // L <= the longest row, so Q <= P
+    for (int j = threadIdx.x; j < Q; j += blockDim.x) slot[j] = j < L ? ocol[b + j] : 0x7fffffff;
     __syncthreads();
-    bitonic_block(scratch, P);
-    for (int i = threadIdx.x; i < L; i += blockDim.x) ocol[b + i] = scratch[i];
+    bitonic_block(slot, Q);
+    for (int j = threadIdx.x; j < L; j += blockDim.x) ocol[b + j] = slot[j];
     __syncthreads();
   }
 }
@@ -753,8 +777,29 @@ cudaError_t launch_orient_fill(const Csr& g, const int32_t* rank, const int64_t*
   return dispatch_rows(g, heavy, nheavy, heavy_cap, OrientFillOp{rank, orp, cursor, ocol, g.n}, st);
 }
 
-cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int32_t* ocol, int32_t* gscratch,
-                             cudaStream_t st) {
+namespace {
+// Layout of the long-row scratch: [count][list of cap rows][pad][slots x P].
+struct LongRowScratch {
+  int64_t cap, slots, P, slot_off, total;
+};
+LongRowScratch long_row_scratch(int64_t entries, int32_t dpmax) {
+  LongRowScratch x{0, 0, 0, 0, 0};
+  if (dpmax <= SORT_SMEM_MAX) return x;
+  x.P = SORT_SMEM_MAX;
+  while (x.P < dpmax) x.P <<= 1;
+  x.cap = entries / (SORT_SMEM_MAX + 1) + 1;
+  // one slot per SM, at most 2^28 int32 in all
+  x.slots = std::max<int64_t>(1, std::min<int64_t>(num_sms(), ((int64_t)1 << 28) / x.P));
+  x.slot_off = ((1 + x.cap) + 3) & ~(int64_t)3;  // 16-byte aligned slots
+  x.total = x.slot_off + x.slots * x.P;
+  return x;
+}
+}  // namespace
+
+int64_t sort_rows_scratch_ints(int64_t entries, int32_t dpmax) { return long_row_scratch(entries, dpmax).total; }
+
+cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int64_t entries, int32_t* ocol,
+                             int32_t* gscratch, cudaStream_t st) {
   if (n <= 0 || dpmax < 2) return cudaSuccess;
   k_sort_rows_warp<<<grid_for(n * 32, 256), 256, 0, st>>>(orp, n, ocol);
   note_launch();
@@ -767,7 +812,14 @@ cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int32
     note_launch();
   }
   if (dpmax > SORT_SMEM_MAX) {
-    k_sort_rows_global<<<1, 1024, 0, st>>>(orp, n, ocol, gscratch);
+    const LongRowScratch x = long_row_scratch(entries, dpmax);
+    if (!gscratch || x.P > ((int64_t)1 << 30)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(gscratch, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    k_long_rows<<<grid_for(n, 256), 256, 0, st>>>(orp, n, gscratch + 1, x.cap);
+    note_launch();
+    k_sort_rows_global<<<(unsigned)x.slots, 1024, 0, st>>>(orp, gscratch + 1, x.cap, ocol, gscratch + x.slot_off,
+                                                           (int)x.P);
     note_launch();
   }
   return cudaGetLastError();
