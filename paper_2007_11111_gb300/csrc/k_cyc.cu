@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const int64_t* __restrict__
     if (lane == 0) item = atomicAdd(next, 1);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= total) break;
-    const int32_t w = list[item];
+    const int32_t w = list[total - 1 - item];  // lists run in rising rank: the largest vertices first
     int64_t cap = wc[w];
     if (cap > n - 1 - w) cap = n - 1 - w;
     if (cap > cap_bound) cap = cap_bound;
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
     __syncthreads();
     const int item = s_item;
     if (item >= total) break;
-    const int32_t w = list[item];
+    const int32_t w = list[total - 1 - item];  // lists run in rising rank: the largest vertices first
     int hb = tbits;
     if (!DENSE || GMEM) {
       // distinct tops the table must hold: all of them, or (dense window)

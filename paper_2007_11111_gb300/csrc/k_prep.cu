@@ -366,19 +366,41 @@ __device__ void bitonic_block(int32_t* buf, int P) {
 
 constexpr int SORT_SMEM_MAX = 16384;
 
-__global__ void k_sort_rows_block(const int64_t* __restrict__ orp, int64_t n, int32_t* ocol) {
+constexpr int SORT_BLOCK_T = 256;
+
+// Rows of 33 .. SORT_SMEM_MAX entries, one block per row in shared memory.
+// Block b owns rows b, b + grid, b + 2 grid, ... (rows of similar length sit
+// together in rank order, so interleaving spreads them over the blocks); its
+// threads test SORT_BLOCK_T of its rows at once, then it sorts the ones in
+// range one after the other.
+__global__ void __launch_bounds__(SORT_BLOCK_T) k_sort_rows_block(const int64_t* __restrict__ orp, int64_t n,
+                                                                   int32_t* ocol) {
   extern __shared__ int32_t sbuf[];
-  for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
-    const int64_t b = orp[r];
-    const int L = (int)(orp[r + 1] - b);
-    if (L <= 32 || L > SORT_SMEM_MAX) continue;
-    int P = 64;
-    while (P < L) P <<= 1;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) sbuf[i] = i < L ? ocol[b + i] : 0x7fffffff;
+  __shared__ int64_t rows[SORT_BLOCK_T];
+  __shared__ int nrows;
+  const int64_t G = gridDim.x;
+  for (int64_t k0 = 0; (int64_t)blockIdx.x + k0 * G < n; k0 += SORT_BLOCK_T) {
+    if (threadIdx.x == 0) nrows = 0;
     __syncthreads();
-    bitonic_block(sbuf, P);
-    for (int i = threadIdx.x; i < L; i += blockDim.x) ocol[b + i] = sbuf[i];
+    const int64_t rr = (int64_t)blockIdx.x + (k0 + threadIdx.x) * G;
+    if (rr < n) {
+      const int64_t L = orp[rr + 1] - orp[rr];
+      if (L > 32 && L <= SORT_SMEM_MAX) rows[atomicAdd(&nrows, 1)] = rr;
+    }
     __syncthreads();
+    const int count = nrows;
+    for (int q = 0; q < count; ++q) {
+      const int64_t r = rows[q];
+      const int64_t b = orp[r];
+      const int L = (int)(orp[r + 1] - b);
+      int P = 64;
+      while (P < L) P <<= 1;
+      for (int i = threadIdx.x; i < P; i += blockDim.x) sbuf[i] = i < L ? ocol[b + i] : 0x7fffffff;
+      __syncthreads();
+      bitonic_block(sbuf, P);
+      for (int i = threadIdx.x; i < L; i += blockDim.x) ocol[b + i] = sbuf[i];
+      __syncthreads();
+    }
   }
 }
 
@@ -808,7 +830,7 @@ cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int64
     while (P < dpmax && P < SORT_SMEM_MAX) P <<= 1;
     const size_t smem = (size_t)P * sizeof(int32_t);
     allow_max_smem(k_sort_rows_block);
-    k_sort_rows_block<<<grid_for(n, 1, 4), 256, smem, st>>>(orp, n, ocol);
+    k_sort_rows_block<<<grid_for(n, SORT_BLOCK_T, 4), SORT_BLOCK_T, smem, st>>>(orp, n, ocol);
     note_launch();
   }
   if (dpmax > SORT_SMEM_MAX) {

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int6
     __syncthreads();
     const int item = s_item;
     if (item >= total) break;
-    const int a = work[item];
+    const int a = work[total - 1 - item];  // lists run in rising rank: the largest vertices first
     const int64_t base = orp[a];
     const int D = (int)(orp[a + 1] - base);
     int hb = 5;
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(BT) k_tri2(const int64_t* __restrict__ orp, co
     __syncthreads();
     const int item = s_item;
     if (item >= total) break;
-    const int a = work[item];
+    const int a = work[total - 1 - item];  // lists run in rising rank: the largest vertices first
     const int64_t base = orp[a];
     const int D = (int)(orp[a + 1] - base);
     int hb = 5;
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(TW_T) k_tri1_warp(const int64_t* __restrict__ 
     if (lane == 0) item = atomicAdd(next, 1);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= total) break;
-    const int32_t a = work[item];
+    const int32_t a = work[total - 1 - item];  // the largest vertices first
     int D, hb;
     int64_t base;
     const int32_t x = warp_load_out(w, orp, ocol, a, lane, &D, &base, &hb, err);
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(TW_T) k_tri2_warp(const int64_t* __restrict__ 
     if (lane == 0) item = atomicAdd(next, 1);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= total) break;
-    const int32_t a = work[item];
+    const int32_t a = work[total - 1 - item];  // the largest vertices first
     int D, hb;
     int64_t base;
     const int32_t x = warp_load_out(w, orp, ocol, a, lane, &D, &base, &hb, err);
