@@ -56,7 +56,8 @@ WORKLOADS = {
 # Bounded sample for the CPU oracle: the same generator and parameters at a
 # smaller scale.
 CPU_SAMPLE = dict(kind="rmat", scale=15, ef=16, seed=0,
-                  desc="R-MAT scale 15, edge factor 16, a=.57 b=.19 c=.19, seed 0 (same generator, 1/32 of the vertices)")
+                  desc="R-MAT scale 15, edge factor 16, a=.57 b=.19 c=.19, seed 0 "
+                       "(same generator, 1/32 of the vertices)")
 
 
 def make_graph(spec, device=None):

@@ -208,6 +208,22 @@ fglt_status time_once(fglt_t h, const Csr& g, cudaStream_t st, const Tuning& t, 
   return FGLT_OK;
 }
 
+// The triangle-pass settings of a tuning (class bounds, loads in flight, hash
+// slots per element, lanes per scanned list, warp-per-vertex bound).
+void copy_tri(Tuning& dst, const Tuning& src) {
+  dst.tri_t0 = src.tri_t0;
+  dst.tri_t1 = src.tri_t1;
+  dst.tri_loads = src.tri_loads;
+  dst.tri_hash_factor = src.tri_hash_factor;
+  dst.tri_group = src.tri_group;
+  dst.tri_warp = src.tri_warp;
+}
+
+bool same_tri(const Tuning& a, const Tuning& b) {
+  return a.tri_t0 == b.tri_t0 && a.tri_t1 == b.tri_t1 && a.tri_loads == b.tri_loads &&
+         a.tri_hash_factor == b.tri_hash_factor && a.tri_group == b.tri_group && a.tri_warp == b.tri_warp;
+}
+
 }  // namespace
 
 extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is_64bit, const int32_t* colidx,
@@ -236,7 +252,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
     const int wbits[] = {8, 9, 10};
     const int spans[] = {0, 16384, 32768, 65536, 90112};
     const int threads[] = {128, 256, 512, 1024};
-    std::vector<Tuning> tri_c, cyc_c;
+    std::vector<Tuning> tri_c;
     for (auto& tb : t_bounds) {
       Tuning t = best;
       t.tri_t0 = tb[0];
@@ -245,9 +261,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
       t.tri_hash_factor = tb[3];
       t.tri_group = tb[4];
       t.tri_warp = tb[5] < 0 ? 0 : tb[5];
-      if (t.tri_t0 != start.tri_t0 || t.tri_t1 != start.tri_t1 || t.tri_loads != start.tri_loads ||
-          t.tri_hash_factor != start.tri_hash_factor || t.tri_group != start.tri_group || t.tri_warp != start.tri_warp)
-        tri_c.push_back(t);
+      if (!same_tri(t, start)) tri_c.push_back(t);
     }
     TuneScore cur = base;
     // The 4-cycle parameters interact through the class split: search them in
@@ -259,54 +273,42 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
         // pair this 4-cycle candidate with the next triangle candidate, if any
         Tuning run = t;
         const bool with_tri = !tri_c.empty();
-        if (with_tri) {
-          run.tri_t0 = tri_c.back().tri_t0;
-          run.tri_t1 = tri_c.back().tri_t1;
-          run.tri_loads = tri_c.back().tri_loads;
-          run.tri_hash_factor = tri_c.back().tri_hash_factor;
-          run.tri_group = tri_c.back().tri_group;
-          run.tri_warp = tri_c.back().tri_warp;
-        }
+        if (with_tri) copy_tri(run, tri_c.back());
         TuneScore sc;
         fglt_status e = time_once(h, g, st, run, reps, &sc);
         if (e != FGLT_OK) return e;
         if (with_tri) {
           if (sc.tri < cur.tri) {
-            best.tri_t0 = run.tri_t0;
-            best.tri_t1 = run.tri_t1;
-            best.tri_loads = run.tri_loads;
-            best.tri_hash_factor = run.tri_hash_factor;
-            best.tri_group = run.tri_group;
-            best.tri_warp = run.tri_warp;
+            copy_tri(best, run);
             cur.tri = sc.tri;
           }
           tri_c.pop_back();
         }
-        if (sc.cyc < cur.cyc) {
-          const int t0 = best.tri_t0, t1 = best.tri_t1, tl = best.tri_loads, thf = best.tri_hash_factor,
-                    tg = best.tri_group, tw = best.tri_warp;
-          best = t;
-          best.tri_warp = tw;
-          best.tri_t0 = t0;
-          best.tri_t1 = t1;
-          best.tri_loads = tl;
-          best.tri_hash_factor = thf;
-          best.tri_group = tg;
+        if (sc.cyc < cur.cyc) {  // keep the best triangle settings found so far
+          Tuning next = t;
+          copy_tri(next, best);
+          best = next;
           cur.cyc = sc.cyc;
         }
       }
       return FGLT_OK;
     };
-    if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_warp_bits == v) return false; t.cyc_warp_bits = v; return true; },
-                     wbits, 3)) != FGLT_OK) return s;
+    // a candidate that sets one integer field (none if it already has that value)
+    auto field = [](int Tuning::*f) {
+      return [f](Tuning& t, int v) {
+        if (t.*f == v) return false;
+        t.*f = v;
+        return true;
+      };
+    };
+    if ((s = try_cyc(field(&Tuning::cyc_warp_bits), wbits, 3)) != FGLT_OK) return s;
     for (int c = 0; c < 3; ++c)
       if ((s = try_cyc([c](Tuning& t, int v) {
              if (t.cyc_mid_threads[c] == v) return false;
              t.cyc_mid_threads[c] = v;
              return true;
            }, threads, 4)) != FGLT_OK) return s;
-    if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_heavy_threads == v) return false; t.cyc_heavy_threads = v; return true; },
-                     threads + 2, 2)) != FGLT_OK) return s;
+    if ((s = try_cyc(field(&Tuning::cyc_heavy_threads), threads + 2, 2)) != FGLT_OK) return s;
     // The dense window and the dense-class threshold decide together which
     // vertices go dense, spill or hash: try them as pairs.
     const int dmins[] = {1024, 2048, 4096};
@@ -322,30 +324,18 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
            return true;
          }, pairs, 15)) != FGLT_OK) return s;
     const int sbits[] = {12, 13, 11};
-    if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_spill_bits == v) return false; t.cyc_spill_bits = v; return true; },
-                     sbits, 3)) != FGLT_OK) return s;
+    if ((s = try_cyc(field(&Tuning::cyc_spill_bits), sbits, 3)) != FGLT_OK) return s;
     const int lsegs[] = {12, 20, 32};
-    if ((s = try_cyc([](Tuning& t, int v) { if (t.cyc_long_segment == v) return false; t.cyc_long_segment = v; return true; },
-                     lsegs, 3)) != FGLT_OK) return s;
+    if ((s = try_cyc(field(&Tuning::cyc_long_segment), lsegs, 3)) != FGLT_OK) return s;
     // triangle candidates left over
     while (!tri_c.empty()) {
       Tuning run = best;
-      run.tri_t0 = tri_c.back().tri_t0;
-      run.tri_t1 = tri_c.back().tri_t1;
-      run.tri_loads = tri_c.back().tri_loads;
-      run.tri_hash_factor = tri_c.back().tri_hash_factor;
-      run.tri_group = tri_c.back().tri_group;
-      run.tri_warp = tri_c.back().tri_warp;
+      copy_tri(run, tri_c.back());
       tri_c.pop_back();
       TuneScore sc;
       if ((s = time_once(h, g, st, run, reps, &sc)) != FGLT_OK) return s;
       if (sc.tri < cur.tri) {
-        best.tri_t0 = run.tri_t0;
-        best.tri_t1 = run.tri_t1;
-        best.tri_loads = run.tri_loads;
-        best.tri_hash_factor = run.tri_hash_factor;
-        best.tri_group = run.tri_group;
-        best.tri_warp = run.tri_warp;
+        copy_tri(best, run);
         cur.tri = sc.tri;
       }
     }

@@ -88,8 +88,8 @@ int tri1_smem_bitmap_max(int hf = 2);
 int tri_grid_blocks();
 // C3 per oriented edge, c3 per vertex, 4-clique count per vertex (only with
 // cliques = true). loads: list entries each lane has in flight per scan step
-// (2 or 4); group: lanes that scan one out-list N+(b) together (8, 16, 32). work_ctr[0..2] += (scanned out-list entries, triangles,
-// 4-cliques).
+// (2 or 4); group: lanes that scan one out-list N+(b) together (8, 16, 32).
+// work_ctr[0..2] += (scanned out-list entries, triangles, 4-cliques).
 cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm,
                         u64* work_ctr, int* err, cudaStream_t st, bool cliques = true, int loads = 2, int hf = 2,

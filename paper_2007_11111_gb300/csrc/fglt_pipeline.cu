@@ -101,8 +101,8 @@ fglt_status make_subdict(uint32_t mask, SubDict* sd) {
 
 fglt_status tuning_from_options(const fglt_options& o, Tuning* t) {
   Tuning x;
-  if (o.cyc_hub_span < 0 || o.cyc_hub_span > cyc_dense_span_max() || o.tri_class_bounds[0] < 0 || o.tri_class_bounds[1] < 0 || o.cyc_warp_bits < 0 ||
-      o.cyc_heavy_threads < 0)
+  if (o.cyc_hub_span < 0 || o.cyc_hub_span > cyc_dense_span_max() || o.tri_class_bounds[0] < 0 ||
+      o.tri_class_bounds[1] < 0 || o.cyc_warp_bits < 0 || o.cyc_heavy_threads < 0)
     return FGLT_ERR_INVALID_ARG;
   x.cyc_hub_span = o.cyc_hub_span;
   if (o.tri_class_bounds[0]) x.tri_t0 = o.tri_class_bounds[0];
@@ -441,9 +441,8 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
     int32_t* lists;
     NEED(B_LS, (int64_t)CYC_CLASSES * n, lists);
     const int64_t cap_bound = b ? std::min<int64_t>(b->cap, n) : n;
-    CK(launch_cyc_worklists(wc, wcn, dr, n, lists, n, cnt + C_NCYC0, ctr + W_GCAP, ctr + W_WMAX, ctr + W_WSUM, ctr + W_CLS,
-                            hub_lo < n,
-                            cap_bound, tu.cyc_warp_bits, tu.cyc_dense_min, spill_bits, st));
+    CK(launch_cyc_worklists(wc, wcn, dr, n, lists, n, cnt + C_NCYC0, ctr + W_GCAP, ctr + W_WMAX, ctr + W_WSUM,
+                            ctr + W_CLS, hub_lo < n, cap_bound, tu.cyc_warp_bits, tu.cyc_dense_min, spill_bits, st));
     int32_t n_gmem = 0;
     u64 gcap = 0;
     if (b) {

@@ -132,11 +132,10 @@ struct Groups {
 // and a's own counts are the sums over x divided by 2 and 6.
 // ---------------------------------------------------------------------------
 template <bool SMEM_BM, bool K4, int PL, int G>
-__global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG) k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
-                                                const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
-                                                int* next, int Dmax, int Hbits, int hf, int32_t* C3o, u64* c3r,
-                                                u64* k4r,
-                                                uint32_t* gbm, u64* work_ctr, int* err) {
+__global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG)
+    k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol, const int32_t* __restrict__ work,
+           const int32_t* __restrict__ nwork, int* next, int Dmax, int Hbits, int hf, int32_t* C3o, u64* c3r,
+           u64* k4r, uint32_t* gbm, u64* work_ctr, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ u64 red[32];
@@ -615,7 +614,8 @@ int tri_grid_blocks() { return num_sms(); }
 // Kernel instance for (bitmap in shared memory, cliques, loads, group lanes).
 template <bool SMEM_BM, bool K4>
 auto tri1_fn(int loads, int g) {
-  if (loads >= 4) return g >= 32 ? k_tri1<SMEM_BM, K4, 4, 32> : (g >= 16 ? k_tri1<SMEM_BM, K4, 4, 16> : k_tri1<SMEM_BM, K4, 4, 8>);
+  if (loads >= 4)
+    return g >= 32 ? k_tri1<SMEM_BM, K4, 4, 32> : (g >= 16 ? k_tri1<SMEM_BM, K4, 4, 16> : k_tri1<SMEM_BM, K4, 4, 8>);
   return g >= 32 ? k_tri1<SMEM_BM, K4, 2, 32> : (g >= 16 ? k_tri1<SMEM_BM, K4, 2, 16> : k_tri1<SMEM_BM, K4, 2, 8>);
 }
 

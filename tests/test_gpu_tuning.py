@@ -75,7 +75,8 @@ def test_invalid_settings_rejected():
                 dict(cyc_warp_bits=5), dict(cyc_mid_threads=(96, 256, 256)), dict(cyc_heavy_threads=300),
                 dict(cyc_hub_span=-1), dict(cyc_hub_span=90113), dict(tri_probe_loads=3),
                 dict(tri_hash_factor=3), dict(cyc_mid_threads=(64, 256, 256)), dict(cyc_dense_min=5000),
-                dict(tri_group_lanes=4), dict(cyc_long_segment=1), dict(tri_warp_max=33), dict(cyc_spill_bits=14), dict(tri_warp_max=-2)):
+                dict(tri_group_lanes=4), dict(cyc_long_segment=1), dict(tri_warp_max=33), dict(cyc_spill_bits=14),
+                dict(tri_warp_max=-2)):
         with pytest.raises(fg.FgltError) as e:
             fg.Handle(device=0, **bad)
         assert e.value.status == fg.FGLT_ERR_INVALID_ARG
