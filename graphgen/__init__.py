@@ -220,6 +220,32 @@ class Batch(NamedTuple):
     offsets: np.ndarray      # int64[num_graphs+1], first vertex of each graph
 
 
+def dense_neighbourhoods(core: int, p: float, roots: Sequence[float], boosters: int, q: float,
+                         seed: int) -> Graph:
+    """A random graph G(core, p) on vertices 0..core-1, plus one root vertex per
+    entry f of `roots`, joined to a random fraction f of the core, plus
+    `boosters` vertices each joined to a random fraction q of the core (they
+    raise the core's degrees above the roots', so that in degree order the
+    roots' higher neighbours are exactly their core neighbours, and the
+    subgraph induced on them is dense)."""
+    rng = np.random.default_rng(seed)
+    iu, ju = np.triu_indices(core, 1)
+    keep = rng.random(iu.size) < p
+    src, dst = [iu[keep]], [ju[keep]]
+    v = core
+    for f in roots:
+        nb = np.flatnonzero(rng.random(core) < f)
+        src.append(np.full(nb.size, v))
+        dst.append(nb)
+        v += 1
+    for _ in range(boosters):
+        nb = np.flatnonzero(rng.random(core) < q)
+        src.append(np.full(nb.size, v))
+        dst.append(nb)
+        v += 1
+    return csr_from_pairs(v, np.concatenate(src), np.concatenate(dst))
+
+
 def pack_block_diagonal(graphs: Sequence[Graph]) -> Batch:
     ns = np.array([g.n for g in graphs], dtype=np.int64)
     offsets = np.zeros(len(graphs) + 1, dtype=np.int64)

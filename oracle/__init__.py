@@ -42,6 +42,10 @@ def _bind(path):
     lib.oracle_fglt.argtypes = [ctypes.c_int64, i64p, i32p, i64p, ctypes.c_int64,
                                 i64p, i64p, ctypes.c_int]
     lib.oracle_fglt.restype = ctypes.c_int
+    f64p = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_fglt_timed.argtypes = [ctypes.c_int64, i64p, i32p, i64p, ctypes.c_int64,
+                                      i64p, i64p, ctypes.c_int, f64p, f64p]
+    lib.oracle_fglt_timed.restype = ctypes.c_int
     lib.oracle_raw_to_net.argtypes = [ctypes.c_int64, i64p, i64p]
     lib.oracle_raw_to_net.restype = None
     lib.oracle_raw_to_net_sub.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64p, i64p]
@@ -103,6 +107,32 @@ def fglt(graph, vertices=None, threads: int = 0, _lib_override=None, dictionary:
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return raw[:rows], net[:rows]
+
+
+def fglt_timed(graph, vertices, threads: int = 0):
+    """Sampled-mode rows (as ``fglt(graph, vertices)``) plus per-row wall
+    seconds: t_c3[j] for the C3 row of every vertex j whose row step 2
+    computed (0 elsewhere) and t_row[r] for steps 4-8 of output row r. The
+    timers are measurements for the benchmark's CPU baseline; the results are
+    the same as ``fglt``'s."""
+    lib = _load()
+    n = int(graph.n)
+    rowptr = np.ascontiguousarray(graph.rowptr, dtype=np.int64)
+    colidx = np.ascontiguousarray(graph.colidx, dtype=np.int32)
+    if colidx.size == 0:
+        colidx = np.zeros(1, np.int32)
+    verts = np.ascontiguousarray(vertices, dtype=np.int64)
+    rows = verts.size
+    raw = np.zeros((max(rows, 1), 16), dtype=np.int64)
+    net = np.zeros((max(rows, 1), 16), dtype=np.int64)
+    t_c3 = np.zeros(max(n, 1), dtype=np.float64)
+    t_row = np.zeros(max(rows, 1), dtype=np.float64)
+    f64p = ctypes.POINTER(ctypes.c_double)
+    rc = lib.oracle_fglt_timed(n, _p64(rowptr), _p32(colidx), _p64(verts), rows, _p64(raw), _p64(net),
+                               int(threads), t_c3.ctypes.data_as(f64p), t_row.ctypes.data_as(f64p))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return raw[:rows], net[:rows], t_c3[:n], t_row[:rows]
 
 
 def sub_dictionary(raw16: np.ndarray, mask: int):

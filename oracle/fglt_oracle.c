@@ -40,12 +40,24 @@
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
+#else
+#include <time.h>
 #endif
 
 typedef int64_t i64;
 typedef int32_t i32;
 
 #define NG 16
+
+/* Wall clock in seconds (measurement only: the CPU-baseline leg of the
+ * benchmark reads per-row times to extrapolate from a vertex sample). */
+static double wall_s(void) {
+#ifdef _OPENMP
+    return omp_get_wtime();
+#else
+    return (double)clock() / CLOCKS_PER_SEC;
+#endif
+}
 
 /* Rectified difference of the paper's notation paragraph: max(x - y, 0). */
 static inline i64 rsub(i64 x, i64 y) { return x > y ? x - y : 0; }
@@ -145,17 +157,19 @@ static int adjacent(const graph* g, i64 k, i32 l) {
  * Step 2: C3(i,j) = (A o A^2)(i,j) = a_i^T a_j for every directed edge, stored
  * aligned with the column indices.
  * ------------------------------------------------------------------------- */
-static void step_C3(const graph* g, i64* C3, const unsigned char* rows_needed, int nthreads) {
+static void step_C3(const graph* g, i64* C3, const unsigned char* rows_needed, int nthreads, double* t_c3) {
     (void)nthreads;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
     for (i64 i = 0; i < g->n; i++) {
         if (rows_needed && !rows_needed[i]) continue;
+        const double t0 = t_c3 ? wall_s() : 0.0;
         const i32* Ni = g->ci + g->rp[i];
         i64 di = deg(g, i);
         for (i64 e = g->rp[i]; e < g->rp[i + 1]; e++) {
             i64 j = g->ci[e];
             C3[e] = merge_count(Ni, di, g->ci + g->rp[j], deg(g, j));
         }
+        if (t_c3) t_c3[i] = wall_s() - t0;
     }
 }
 
@@ -279,10 +293,13 @@ void oracle_raw_to_net_sub(i64 n, int k, const int* cols, const i64* raw, i64* n
  * rows of the closed neighbourhoods of the requested vertices, and p3 only at
  * the requested vertices; every value the requested rows read is the same as
  * in the full computation.
+ * t_c3 (nullable, [n]) receives the seconds step 2 spent on each row it
+ * computed; t_row (nullable, [rows]) the seconds steps 4-8 spent on each
+ * output row. They are measurements only and change no result.
  * Returns 0 on success, -1 on allocation failure.
  * ------------------------------------------------------------------------- */
-int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i64 nv,
-                i64* raw, i64* net, int nthreads) {
+int oracle_fglt_timed(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i64 nv,
+                      i64* raw, i64* net, int nthreads, double* t_c3, double* t_row) {
     graph G = {n, rowptr, colidx};
     const graph* g = &G;
     if (nthreads <= 0) {
@@ -322,7 +339,7 @@ int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i
     }
 
     /* Step 2: C3 and c3 = C3 e / 2. */
-    step_C3(g, C3, need, nthreads);
+    step_C3(g, C3, need, nthreads, t_c3);
     for (i64 i = 0; i < n; i++) {
         if (need && !need[i]) { c3[i] = 0; continue; }
         i64 s = 0;
@@ -351,6 +368,7 @@ int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i
         } else {
 #pragma omp for schedule(dynamic, 1)
             for (i64 r = 0; r < rows; r++) {
+                const double t0 = t_row ? wall_s() : 0.0;
                 i64 i = verts ? verts[r] : r;
                 i64 d = p1[i];
                 i64* f = raw + NG * r;
@@ -381,6 +399,7 @@ int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i
                 f[14] = qt.d43 / 2;                                  /* D4,3 e / 2 */
                 f[15] = qt.T / 6;                                    /* T e / 6 */
                 if (net) raw_to_net_row(f, net + NG * r);
+                if (t_row) t_row[r] = wall_s() - t0;
             }
         }
         free(acc);
@@ -388,6 +407,11 @@ int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i
     }
     free(p1); free(p2); free(c3); free(p3); free(C3); free(need);
     return failed ? -1 : 0;
+}
+
+int oracle_fglt(i64 n, const i64* rowptr, const i32* colidx, const i64* verts, i64 nv,
+                i64* raw, i64* net, int nthreads) {
+    return oracle_fglt_timed(n, rowptr, colidx, verts, nv, raw, net, nthreads, NULL, NULL);
 }
 
 /* Number of threads an OpenMP region would use (for reporting). */

@@ -121,6 +121,87 @@ struct Groups {
   }
 };
 
+// Clique phase of the global-bitmap class. The bitmap S of G_a (D rows of W
+// words at stride WS, in global memory) is taken in row bands of TB rows: a
+// band X is staged in shared memory, then every band Y at or after it, and
+// for each x in X and each neighbour y > x of x in Y the warp's lanes add
+// t = popc(S_x & S_y) over all W words to the tallies of x and y. G_a of a
+// vertex in this class is dense (rows rarely hold an empty word), so every
+// word is ANDed. Each band pair is read from global memory once, and the
+// popcounts read only shared memory.
+__device__ __forceinline__ void hub_cliques(const uint32_t* __restrict__ bm, int D, int W, int WS, int Wmax, int TB,
+                                            uint32_t* k2loc, unsigned char* smem) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  uint32_t* Xs = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* Ys = Xs + (size_t)TB * (Wmax | 1);
+  int32_t* yl = reinterpret_cast<int32_t*>(Ys + (size_t)TB * (Wmax | 1)) + warp * TB;
+  for (int x0 = 0; x0 < D; x0 += TB) {
+    const int nx = min(TB, D - x0);
+    __syncthreads();  // the previous band's readers (or the probe tables' users) are done
+    for (int i = tid; i < nx * WS; i += blockDim.x) Xs[i] = __ldcg(bm + (size_t)x0 * WS + i);
+    for (int y0 = x0; y0 < D; y0 += TB) {
+      const int ny = min(TB, D - y0);
+      const uint32_t* Yb = Xs;
+      if (y0 != x0) {
+        __syncthreads();  // the previous Y band's readers are done
+        for (int i = tid; i < ny * WS; i += blockDim.x) Ys[i] = __ldcg(bm + (size_t)y0 * WS + i);
+        Yb = Ys;
+      }
+      __syncthreads();
+      const int yw0 = y0 >> 5;  // TB is a multiple of 32
+      const int nyw = (ny + 31) >> 5;
+      for (int xi = warp; xi < nx; xi += nwarps) {
+        const int x = x0 + xi;
+        const uint32_t* xr = Xs + (size_t)xi * WS;
+        uint32_t bits = 0u;
+        if (lane < nyw) {
+          bits = xr[yw0 + lane];
+          const int yb = (yw0 + lane) << 5;
+          if (yb + 31 <= x) bits = 0u;
+          else if (yb <= x) bits &= ~((2u << (x - yb)) - 1u);  // keep y > x
+        }
+        const int c = __popc(bits);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        int p = incl - c;
+        while (bits) {
+          const int t = __ffs(bits) - 1;
+          bits &= bits - 1;
+          yl[p++] = ((yw0 + lane) << 5) + t - y0;
+        }
+        const int nyl = __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        uint32_t kx = 0;
+        for (int i = lane; i < nyl; i += 32) {
+          const int yi = yl[i];
+          const uint32_t* yr = Yb + (size_t)yi * WS;
+          uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+          int w = 0;
+          for (; w + 4 <= W; w += 4) {
+            t0 += __popc(xr[w] & yr[w]);
+            t1 += __popc(xr[w + 1] & yr[w + 1]);
+            t2 += __popc(xr[w + 2] & yr[w + 2]);
+            t3 += __popc(xr[w + 3] & yr[w + 3]);
+          }
+          for (; w < W; ++w) t0 += __popc(xr[w] & yr[w]);
+          const uint32_t t = t0 + t1 + t2 + t3;
+          if (t) {
+            atomicAdd(&k2loc[y0 + yi], t);
+            kx += t;
+          }
+        }
+        kx = (uint32_t)warp_sum_i32((int)kx);
+        if (lane == 0 && kx) atomicAdd(&k2loc[x], kx);
+        __syncwarp();
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Pass 1
 //
@@ -131,11 +212,23 @@ struct Groups {
 //                                  i.e. twice the 4-cliques {a, x, ., .}
 // and a's own counts are the sums over x divided by 2 and 6.
 // ---------------------------------------------------------------------------
-template <bool SMEM_BM, bool K4, int PL, int G>
-__global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG)
+// Shared-memory words of the region that holds, in turn, the probe tables of
+// N+(a) (hash keys and values, filter) and the two row bands of the clique
+// phase of the global-bitmap class (TB rows each, plus a TB-entry list per
+// warp); the clique tallies follow it.
+__host__ __device__ __forceinline__ size_t hub_region_words(int Hbits, int fwords, int Wmax, int TB, int nwarps) {
+  const size_t table = 2 * ((size_t)1 << Hbits) + (size_t)fwords;
+  const size_t bands = 2 * (size_t)TB * (size_t)(Wmax | 1) + (size_t)nwarps * TB;
+  return table > bands ? table : bands;
+}
+
+constexpr int TRI_YL = 256;  // y-list entries per warp in the clique phase of the shared-memory classes
+
+template <bool SMEM_BM, bool K4, int PL, int G, int BT>
+__global__ void __launch_bounds__(BT)
     k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol, const int32_t* __restrict__ work,
            const int32_t* __restrict__ nwork, int* next, int Dmax, int Hbits, int hf, int32_t* C3o, u64* c3r,
-           u64* k4r, uint32_t* gbm, u64* work_ctr, int* err) {
+           u64* k4r, uint32_t* gbm, u64* work_ctr, int* err, int TB) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ u64 red[32];
@@ -146,23 +239,21 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG)
   int32_t* vals = reinterpret_cast<int32_t*>(keys + Hmax);
   uint32_t* filt = reinterpret_cast<uint32_t*>(vals + Hmax);
   // Shared-memory bitmap: [per-warp lists][bitmap][tallies] in shared memory.
-  // Otherwise the bitmap and the per-warp lists live in this block's slot of
-  // gbm and the tallies in shared memory.
-  int32_t* lists_base;
+  // Otherwise the bitmap lives in this block's slot of gbm, and shared memory
+  // holds [probe tables | row bands][tallies].
+  int32_t* lists_base = nullptr;
   uint32_t* bm;
   uint32_t* k2loc;  // [Dmax] per-vertex 4-clique tallies
   if (SMEM_BM) {
     lists_base = reinterpret_cast<int32_t*>(filt + FWmax);
-    bm = reinterpret_cast<uint32_t*>(lists_base + nwarps * (Dmax + Wmax));
+    bm = reinterpret_cast<uint32_t*>(lists_base + nwarps * (TRI_YL + Wmax));
     k2loc = bm + (size_t)Dmax * (Wmax + 1);
   } else {
-    uint32_t* slot = gbm + (size_t)blockIdx.x * ((size_t)Dmax * (Wmax + 1) + (size_t)nwarps * (Dmax + Wmax));
-    bm = slot;
-    lists_base = reinterpret_cast<int32_t*>(slot + (size_t)Dmax * (Wmax + 1));
-    k2loc = filt + FWmax;
+    bm = gbm + (size_t)blockIdx.x * ((size_t)Dmax * (Wmax + 1));
+    k2loc = reinterpret_cast<uint32_t*>(smem) + hub_region_words(Hbits, FWmax, Wmax, TB, nwarps);
   }
-  int32_t* ylist = lists_base + warp * (Dmax + Wmax);
-  int32_t* wlist = ylist + Dmax;
+  int32_t* ylist = SMEM_BM ? lists_base + warp * (TRI_YL + Wmax) : nullptr;
+  int32_t* wlist = SMEM_BM ? ylist + TRI_YL : nullptr;
   const int total = *nwork;
   const unsigned below = (1u << lane) - 1u;
 
@@ -225,9 +316,25 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG)
     // to both ends, so k2loc[x] ends as twice the triangles of G_a at x, i.e.
     // twice the 4-cliques {a, x, ., .}.
     u64 tri2x = 0;
-    for (int x = warp; x < D; x += nwarps) {
+    if (!SMEM_BM) {
+      for (int x = warp; x < D; x += nwarps) {
+        const uint32_t* Sx = bm + (size_t)x * WS;
+        int deg = 0;
+        for (int w = lane; w < W; w += 32) deg += __popc(__ldcg(Sx + w));
+        deg = warp_sum_i32(deg);
+        if (lane == 0) {
+          if (deg) {
+            atomicAdd(&C3o[base + x], deg);
+            atomicAdd(&c3r[ocol[base + x]], (u64)deg);
+          }
+          tri2x += (u64)deg;
+        }
+      }
+      if (K4) hub_cliques(bm, D, W, WS, Wmax, TB, k2loc, smem);
+    }
+    for (int x = warp; SMEM_BM && x < D; x += nwarps) {
       const uint32_t* Sx = bm + (size_t)x * WS;
-      int deg = 0, nzw = 0, nup = 0;
+      int deg = 0, nzw = 0;
       const int xw = x >> 5;
       const uint32_t above = ~((2u << (x & 31)) - 1u);  // bits of the word of x above x
       for (int w0 = 0; w0 < W; w0 += 32) {
@@ -237,39 +344,50 @@ __global__ void __launch_bounds__(SMEM_BM ? TRI_T : TRI_T_BIG)
         if (bits) wlist[nzw + __popc(mz & below)] = w;
         nzw += __popc(mz);
         deg += warp_sum_i32(__popc(bits));
-        if (!K4) continue;
-        uint32_t ub = w > xw ? bits : (w == xw ? bits & above : 0u);
-        const int c = __popc(ub);
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
-        }
-        int p = nup + incl - c;
-        while (ub) {
-          const int t = __ffs(ub) - 1;
-          ub &= ub - 1;
-          ylist[p++] = (w << 5) + t;
-        }
-        nup += __shfl_sync(0xffffffffu, incl, 31);
       }
       __syncwarp();
       if (K4) {
-        int kx = 0;
-        for (int i = lane; i < nup; i += 32) {
-          const int y = ylist[i];
-          const uint32_t* Sy = bm + (size_t)y * WS;
-          int t = 0;
-          for (int q = 0; q < nzw; ++q) {
-            const int w = wlist[q];
-            t += __popc(Sx[w] & Sy[w]);
+        // neighbours y > x of x, TRI_YL columns at a time
+        uint32_t kx = 0;
+        for (int yw0 = xw; yw0 < W; yw0 += TRI_YL / 32) {
+          const int w = yw0 + lane;
+          uint32_t ub = 0u;
+          if (lane < TRI_YL / 32 && w < W) {
+            const uint32_t bits = Sx[w];
+            ub = w > xw ? bits : (w == xw ? bits & above : 0u);
           }
-          if (t) atomicAdd(&k2loc[y], (uint32_t)t);
-          kx += t;
+          const int c = __popc(ub);
+          int incl = c;
+#pragma unroll
+          for (int o = 1; o < TRI_YL / 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          int p = incl - c;
+          while (ub) {
+            const int t = __ffs(ub) - 1;
+            ub &= ub - 1;
+            ylist[p++] = (w << 5) + t;
+          }
+          const int nyl = __shfl_sync(0xffffffffu, incl, TRI_YL / 32 - 1);
+          __syncwarp();
+          for (int i = lane; i < nyl; i += 32) {
+            const int y = ylist[i];
+            const uint32_t* Sy = bm + (size_t)y * WS;
+            uint32_t t = 0;
+            for (int q = 0; q < nzw; ++q) {
+              const int ww = wlist[q];
+              t += __popc(Sx[ww] & Sy[ww]);
+            }
+            if (t) {
+              atomicAdd(&k2loc[y], t);
+              kx += t;
+            }
+          }
+          __syncwarp();
         }
-        kx = warp_sum_i32(kx);
-        if (lane == 0 && kx) atomicAdd(&k2loc[x], (uint32_t)kx);
+        kx = (uint32_t)warp_sum_i32((int)kx);
+        if (lane == 0 && kx) atomicAdd(&k2loc[x], kx);
       }
       if (lane == 0) {
         if (deg) {
@@ -571,12 +689,29 @@ int host_filter_words(int D) {
   return (1 << fb) >> 5;
 }
 
-size_t tri1_smem_impl(int D, bool smem_bm, int hf) {
+// Rows per band of the global-bitmap class's clique phase: the largest of
+// 128, 64, 32 whose bands fit next to the tallies.
+int hub_tile_rows(int D, int hf) {
+  const int W = (D + 31) / 32;
+  for (int tb : {128, 64, 32}) {
+    const size_t words = hub_region_words(hash_bits_for(D, hf), host_filter_words(D), W, tb, TRI_T_BIG / 32) + D;
+    if (((words * 4 + 15) & ~(size_t)15) <= SMEM_LIMIT - 1024) return tb;
+  }
+  return 32;
+}
+
+size_t tri1_smem_impl(int D, bool smem_bm, int hf, int bt = TRI_T) {
   const int H = 1 << hash_bits_for(D, hf);
   const size_t W = (size_t)(D + 31) / 32;
+  if (!smem_bm) {  // [probe tables | row bands][tallies]
+    const size_t words =
+        hub_region_words(hash_bits_for(D, hf), host_filter_words(D), (int)W, hub_tile_rows(D, hf), TRI_T_BIG / 32) +
+        (size_t)D;
+    return (words * 4 + 15) & ~(size_t)15;
+  }
   size_t bytes = (size_t)H * 8 + (size_t)host_filter_words(D) * 4;
   bytes += (size_t)D * 4;  // per-vertex 4-clique tallies
-  if (smem_bm) bytes += (size_t)(TRI_T / 32) * (D + W) * 4 + (size_t)D * (W + 1) * 4;  // lists and bitmap
+  bytes += (size_t)(bt / 32) * (TRI_YL + W) * 4 + (size_t)D * (W + 1) * 4;  // per-warp lists and bitmap
   return (bytes + 15) & ~(size_t)15;
 }
 
@@ -611,37 +746,57 @@ size_t tri2_smem_bytes(int dpmax, int hf) {
 
 int tri_grid_blocks() { return num_sms(); }
 
-// Kernel instance for (bitmap in shared memory, cliques, loads, group lanes).
-template <bool SMEM_BM, bool K4>
+// Kernel instance for (bitmap in shared memory, cliques, loads, group lanes,
+// block size).
+template <bool SMEM_BM, bool K4, int BT>
 auto tri1_fn(int loads, int g) {
   if (loads >= 4)
-    return g >= 32 ? k_tri1<SMEM_BM, K4, 4, 32> : (g >= 16 ? k_tri1<SMEM_BM, K4, 4, 16> : k_tri1<SMEM_BM, K4, 4, 8>);
-  return g >= 32 ? k_tri1<SMEM_BM, K4, 2, 32> : (g >= 16 ? k_tri1<SMEM_BM, K4, 2, 16> : k_tri1<SMEM_BM, K4, 2, 8>);
+    return g >= 32 ? k_tri1<SMEM_BM, K4, 4, 32, BT>
+                   : (g >= 16 ? k_tri1<SMEM_BM, K4, 4, 16, BT> : k_tri1<SMEM_BM, K4, 4, 8, BT>);
+  return g >= 32 ? k_tri1<SMEM_BM, K4, 2, 32, BT>
+                 : (g >= 16 ? k_tri1<SMEM_BM, K4, 2, 16, BT> : k_tri1<SMEM_BM, K4, 2, 8, BT>);
 }
 
-template <bool SMEM_BM>
+template <bool SMEM_BM, int BT>
 void allow_tri1() {
   for (int loads : {2, 4})
     for (int g : {8, 16, 32}) {
-      allow_max_smem(tri1_fn<SMEM_BM, true>(loads, g));
-      allow_max_smem(tri1_fn<SMEM_BM, false>(loads, g));
+      allow_max_smem(tri1_fn<SMEM_BM, true, BT>(loads, g));
+      allow_max_smem(tri1_fn<SMEM_BM, false, BT>(loads, g));
     }
 }
 
+// Block size of a class: the shared-memory-bitmap classes take 256 threads
+// unless only one such block fits on an SM, then 1024 (more warps streaming
+// out-lists per SM); the global-bitmap class always takes 1024.
+static int tri1_threads(int dpmax, bool smem_bm, int hf) {
+  if (!smem_bm) return TRI_T_BIG;
+  allow_tri1<true, TRI_T>();
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri1<true, true, 2, 32, TRI_T>, TRI_T,
+                                                tri1_smem_impl(dpmax, true, hf));
+  return per_sm <= 1 && tri1_smem_impl(dpmax, true, hf, TRI_T_BIG) <= tri_smem_limit() ? TRI_T_BIG : TRI_T;
+}
+
 static int tri1_grid(int dpmax, bool smem_bm, int hf) {
-  const size_t smem = tri1_smem_impl(dpmax, smem_bm, hf);
-  if (smem_bm) {
-    allow_tri1<true>();
-    return occupancy_grid((const void*)k_tri1<true, true, 2, 32>, smem);
+  const int bt = tri1_threads(dpmax, smem_bm, hf);
+  const size_t smem = tri1_smem_impl(dpmax, smem_bm, hf, bt);
+  if (smem_bm && bt == TRI_T) {
+    allow_tri1<true, TRI_T>();
+    return occupancy_grid((const void*)k_tri1<true, true, 2, 32, TRI_T>, smem);
   }
-  allow_tri1<false>();
-  return occupancy_grid((const void*)k_tri1<false, true, 2, 32>, smem, TRI_T_BIG);
+  if (smem_bm) {
+    allow_tri1<true, TRI_T_BIG>();
+    return occupancy_grid((const void*)k_tri1<true, true, 2, 32, TRI_T_BIG>, smem, TRI_T_BIG);
+  }
+  allow_tri1<false, TRI_T_BIG>();
+  return occupancy_grid((const void*)k_tri1<false, true, 2, 32, TRI_T_BIG>, smem, TRI_T_BIG);
 }
 
 size_t tri1_gbm_bytes(int dpmax, int hf) {
   if (dpmax < 2 || tri1_bitmap_fits_smem(dpmax, hf)) return 0;
   const size_t W = (size_t)(dpmax + 31) / 32;
-  const size_t per_block = (size_t)dpmax * (W + 1) + (size_t)(TRI_T_BIG / 32) * ((size_t)dpmax + W);  // bitmap + lists
+  const size_t per_block = (size_t)dpmax * (W + 1);  // bitmap rows at an odd stride of at most W + 1 words
   return (size_t)tri1_grid(dpmax, false, hf) * per_block * 4;
 }
 
@@ -650,13 +805,18 @@ cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* 
                         int* err, cudaStream_t st, bool cliques, int loads, int hf, int group) {
   if (dpmax < 2) return cudaSuccess;
   const bool smem_bm = tri1_bitmap_fits_smem(dpmax, hf);
-  const size_t smem = tri1_smem_impl(dpmax, smem_bm, hf);
+  const int bt = tri1_threads(dpmax, smem_bm, hf);
+  const size_t smem = tri1_smem_impl(dpmax, smem_bm, hf, bt);
   const int grid = tri1_grid(dpmax, smem_bm, hf);
   const int hb = hash_bits_for(dpmax, hf);
-  auto* fn = smem_bm ? (cliques ? tri1_fn<true, true>(loads, group) : tri1_fn<true, false>(loads, group))
-                     : (cliques ? tri1_fn<false, true>(loads, group) : tri1_fn<false, false>(loads, group));
-  fn<<<grid, smem_bm ? TRI_T : TRI_T_BIG, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, hf, C3o, c3r, k4r,
-                                                     smem_bm ? nullptr : gbm, work_ctr, err);
+  auto* fn = smem_bm ? (bt == TRI_T ? (cliques ? tri1_fn<true, true, TRI_T>(loads, group)
+                                               : tri1_fn<true, false, TRI_T>(loads, group))
+                                    : (cliques ? tri1_fn<true, true, TRI_T_BIG>(loads, group)
+                                               : tri1_fn<true, false, TRI_T_BIG>(loads, group)))
+                     : (cliques ? tri1_fn<false, true, TRI_T_BIG>(loads, group)
+                                : tri1_fn<false, false, TRI_T_BIG>(loads, group));
+  fn<<<grid, bt, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, hf, C3o, c3r, k4r, smem_bm ? nullptr : gbm,
+                             work_ctr, err, smem_bm ? 0 : hub_tile_rows(dpmax, hf));
   note_launch();
   return cudaGetLastError();
 }

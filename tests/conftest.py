@@ -30,3 +30,23 @@ def read_golden_sections(name):
                 continue
             out.setdefault(cur, []).append([int(x) for x in line.split()])
     return out
+
+
+def read_hub_rows(name):
+    """Stored oracle rows of a graph's top-degree vertices (written by
+    tests/golden/make_hub_rows.py): header values, then per vertex its id,
+    raw row and net row."""
+    import numpy as np
+    head, rows = {}, []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            if t[0] == "vertex":
+                rows.append([int(t[1]), None, None])
+            elif t[0] in ("raw", "net"):
+                rows[-1][1 if t[0] == "raw" else 2] = np.array([int(x) for x in t[1:]], dtype=np.int64)
+            else:
+                head[t[0]] = t[1]
+    return head, rows

@@ -8,7 +8,7 @@ import pytest
 import graphgen as gg
 import oracle
 from oracle.brute import brute_fglt, edges_of
-from conftest import read_golden_sections
+from conftest import read_golden_sections, read_hub_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -231,14 +231,61 @@ def test_cycle_paths_with_small_hub_span(span):
             check_vs_oracle(h, g, f"span {span} n={g.n}")
 
 
-def test_rmat_s20_full_size_sampled(handle):
-    """R-MAT scale 20, edge factor 16, seed 0 (the benchmark workload), in the
-    benchmark's launch configuration: every row checked against the invariants
-    that hold at any size, and a vertex sample (high-degree, dense-class,
-    low-degree and isolated vertices, uniform picks) element by element
-    against the oracle."""
+def test_dense_neighbourhoods_hub_classes(handle):
+    """Two roots whose higher-ranked neighbours induce a random subgraph of
+    density 1/2 (the shape of the largest triangle classes on R-MAT s24):
+    out-degree 1100 runs in the class with the bitmap in global memory and its
+    banded clique phase, 991 in the largest shared-memory class. The roots, a
+    few core and booster vertices against the oracle; every row against the
+    invariants."""
+    g = gg.dense_neighbourhoods(1100, 0.5, (1.0, 0.9), 900, 0.75, seed=5)
+    raw, net = gpu(handle, g)
+    assert (net >= 0).all()
+    assert_same(raw, net @ oracle.u16().T, "raw = U16 net")
+    s = net.sum(axis=0)
+    assert s[1] == 2 * g.m and s[2] == 2 * s[3] and s[5] == s[6] and s[7] == 3 * s[8]
+    assert s[10] == 2 * s[9] and s[9] == s[11] and s[13] == s[14]
+    assert s[4] % 3 == 0 and s[12] % 4 == 0 and s[15] % 4 == 0
+    verts = np.array([1100, 1101, 0, 1, 1102, 1103])
+    oraw, onet = oracle.fglt(g, vertices=verts)
+    assert_same(raw[verts], oraw, "sampled raw")
+    assert_same(net[verts], onet, "sampled net")
+
+
+@pytest.fixture(scope="module")
+def s20(handle):
     g = gg.rmat(20, 16, seed=0)
     raw, net = gpu(handle, g)
+    return g, raw, net
+
+
+def test_rmat_s20_top_hubs_vs_stored_oracle_rows(s20):
+    """The 16 highest-degree vertices of R-MAT scale 20 (degrees up to 6.5e4;
+    their rows take the oracle minutes each, so they are stored once by an
+    oracle-only script) element by element, on the benchmark's graph."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
+    from make_hub_rows import csr_digest, top_degree_vertices
+    g, raw, net = s20
+    head, rows = read_hub_rows("hub_rows_rmat-s20-ef16.txt")
+    assert int(head["n"]) == g.n and int(head["nnz"]) == g.nnz
+    assert head["sha256"] == csr_digest(g.rowptr, g.colidx), "stored rows are for another graph"
+    verts = [v for v, _, _ in rows]
+    assert verts == list(top_degree_vertices(g.rowptr, 16))
+    assert np.diff(g.rowptr).max() == max(np.diff(g.rowptr)[verts])  # the largest hub is among them
+    for v, oraw, onet in rows:
+        assert_same(raw[v:v + 1], oraw[None, :], f"hub {v} raw")
+        assert_same(net[v:v + 1], onet[None, :], f"hub {v} net")
+
+
+def test_rmat_s20_full_size_sampled(s20):
+    """R-MAT scale 20, edge factor 16, seed 0, in the benchmark's launch
+    configuration: every row checked against the invariants that hold at any
+    size, and a vertex sample (high-degree, dense-class, low-degree and
+    isolated vertices, uniform picks) element by element against the
+    oracle."""
+    g, raw, net = s20
     deg = np.diff(g.rowptr)
     # invariants on every row
     np.testing.assert_array_equal(raw[:, 0], 1)

@@ -14,7 +14,7 @@ import pytest
 import graphgen as gg
 import oracle
 from oracle.brute import brute_fglt, edges_of
-from conftest import read_golden_sections
+from conftest import read_golden_sections, read_hub_rows
 
 
 def _fig2():
@@ -345,3 +345,23 @@ def test_sub_dictionary_rejects_sets_without_sigma0_sigma1():
     for mask in (0x1, 0x2, 0x1C, 1 << 16 | 0x3):
         with pytest.raises(ValueError):
             oracle.fglt(g, dictionary=mask)
+
+
+def test_stored_hub_rows_are_consistent():
+    """The stored oracle rows of R-MAT scale 20's top-degree vertices belong to
+    the generator's current graph, are those of its 16 largest degrees, and
+    satisfy raw = U16 net, net >= 0 and d1 = degree."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
+    from make_hub_rows import csr_digest, top_degree_vertices
+    head, rows = read_hub_rows("hub_rows_rmat-s20-ef16.txt")
+    g = gg.rmat(20, 16, seed=0)
+    assert head["sha256"] == csr_digest(g.rowptr, g.colidx)
+    assert [v for v, _, _ in rows] == list(top_degree_vertices(g.rowptr, 16))
+    u = oracle.u16()
+    deg = np.diff(g.rowptr)
+    for v, raw, net in rows:
+        assert raw[0] == 1 and raw[1] == deg[v]
+        assert (net >= 0).all()
+        np.testing.assert_array_equal(u @ net, raw)
