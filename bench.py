@@ -1,15 +1,18 @@
 #!/usr/bin/env python3
 """FGLT benchmark: one JSON line on stdout (rank 0).
 
-Default workload: R-MAT scale 20, edge factor 16 (a,b,c = .57,.19,.19, seed 0,
-seeded vertex permutation, symmetrised, deduplicated, no self-loops), int32
-column indices, int64 row pointers, synthetic. A step is one full transform
-(all 16 raw and 16 net frequencies for every vertex) through the C ABI with the
-inputs resident in device memory. L2 is flushed (512 MiB write) before every
-timed step, outside the timed events.
+Default workload: R-MAT scale 24, edge factor 32 (a,b,c = .57,.19,.19, seed 0,
+seeded vertex permutation, symmetrised, deduplicated, no self-loops; drawn by
+the seeded device generator), int32 column indices, int64 row pointers,
+synthetic: n = 16.8 M, m = 5.1e8. A step is one full transform (all 16 raw and
+16 net frequencies for every vertex) through the C ABI with the inputs resident
+in device memory. L2 is flushed (512 MiB write) before every timed step,
+outside the timed events. R-MAT scale 20 is timed as well and reported under
+"extras".
 
 --impl reference times the CPU oracle (the reference arm of this build) on a
-bounded sample of the workload family on the host cores.
+stratified vertex sample of the same graph on the host cores, with the full
+transform's time extrapolated from per-row costs (OracleSampler).
 
 Multi-GPU (torchrun, --gpus N): every rank transforms its own replica of the
 graph (the single-graph path is not sharded); value = all ranks' edges / the
@@ -53,11 +56,9 @@ WORKLOADS = {
                           desc="R-MAT scale 22, edge factor 16, a=.57 b=.19 c=.19, seed 0, permuted, "
                                "symmetric simple CSR generated on the device"),
 }
-# Bounded sample for the CPU oracle: the same generator and parameters at a
-# smaller scale.
-CPU_SAMPLE = dict(kind="rmat", scale=15, ef=16, seed=0,
-                  desc="R-MAT scale 15, edge factor 16, a=.57 b=.19 c=.19, seed 0 "
-                       "(same generator, 1/32 of the vertices)")
+DEFAULT_WORKLOAD = "rmat-s24-ef32"  # the largest single-GPU configuration
+AUTOTUNE_MAX_N = 1 << 22  # larger graphs run at the library's defaults unless --autotune
+EXTRA_WORKLOADS = ("rmat-s20-ef16",)  # also timed and reported under "extras"
 
 
 def make_graph(spec, device=None):
@@ -141,9 +142,9 @@ class ClockSampler:
 # Roofline accounting
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(stage: str, w: dict) -> int:
-    """Bytes the method itself must move for one launch of a stage (see the
-    measurement section of the design doc): 4 B per neighbour-list entry read,
-    4 B per per-edge C3 value, 8 B per per-vertex int64 value."""
+    """Bytes the method itself must move for one launch of a stage: 4 B per
+    neighbour-list entry read, 4 B per per-edge C3 value, 8 B per per-vertex
+    int64 value."""
     n, nnz, m = w["n"], w["nnz"], w["m"]
     if stage == "cyc":
         return 4 * w["wedges"] + 4 * nnz + 8 * n
@@ -178,19 +179,111 @@ def traffic_for(stage: str, workload: str):
 # ---------------------------------------------------------------------------
 # Arms
 # ---------------------------------------------------------------------------
-def oracle_step(g, threads=0):
-    import oracle
-    t0 = time.perf_counter()
-    oracle.fglt(g, threads=threads)
-    return time.perf_counter() - t0
+def neighbour_max_degree(g) -> np.ndarray:
+    """Per vertex, the largest degree among its neighbours (0 if isolated)."""
+    deg = np.diff(g.rowptr)
+    out = np.zeros(g.n, dtype=np.int64)
+    nz = np.flatnonzero(deg > 0)
+    if nz.size:
+        out[nz] = np.maximum.reduceat(deg[g.colidx], g.rowptr[nz])
+    return out
 
 
-def cpu_baseline(threads=0):
-    import oracle
-    g = make_graph(CPU_SAMPLE)
-    dt = oracle_step(g, threads)
-    return {"value": g.m / dt, "unit": UNIT, "cores": threads or oracle.max_threads(), "kind": "oracle",
-            "sample": CPU_SAMPLE["desc"] + f"; full transform of m={g.m} edges in {dt:.2f} s"}
+class OracleSampler:
+    """The CPU oracle timed on a stratified vertex sample of one graph, with the
+    full transform's time extrapolated from per-row costs.
+
+    Vertices are binned by floor(log2(degree)) (isolated vertices form their
+    own bin). Each call picks up to `per_bin` vertices per bin, uniformly among
+    the bin's "affordable" vertices: degree below `deg_cap`, and every
+    neighbour's degree below a cap `nb_cap` (the oracle's sampled mode computes
+    the C3 rows of the whole closed neighbourhood of each requested vertex, and
+    one row of a top hub costs it minutes). nb_cap is the smallest power of two
+    from 2^12 up to `nb_cap_max` for which every bin below deg_cap has an
+    affordable vertex. The oracle reports, per sampled vertex, the seconds of its
+    own C3 row (step 2) and of its Table I/II row (steps 4-8). The full
+    transform's thread-seconds are estimated as the sum over the covered bins
+    of (vertices in the bin) x (mean sampled cost in the bin); the bins left
+    out (the highest degrees) carry most of the oracle's work, so the estimate
+    is a lower bound on its time, i.e. an upper bound on its throughput. The
+    fixed cost (step 1 over all vertices, allocations) is the wall time of a
+    call for one lowest-degree vertex. All cores: fixed + thread-seconds /
+    threads (ideal scaling); one core: fixed + thread-seconds."""
+
+    def __init__(self, g, per_bin=6, deg_cap=1 << 10, nb_cap_max=1 << 15, threads=0, seed=0):
+        import oracle
+        oracle.build()
+        self.g = g
+        self.per_bin = per_bin
+        self.deg_cap = deg_cap
+        self.threads = threads or oracle.max_threads()
+        self.rng = np.random.default_rng(seed)
+        deg = np.diff(g.rowptr)
+        self.deg = deg
+        self.bin = np.where(deg > 0, np.floor(np.log2(np.maximum(deg, 1))).astype(np.int64), -1)
+        nbm = neighbour_max_degree(g)
+        bins, counts = np.unique(self.bin, return_counts=True)
+        self.pops = {int(b): int(c) for b, c in zip(bins, counts)}
+        nb_cap = 1 << 12
+        while True:
+            ok = (deg < deg_cap) & (nbm < nb_cap)
+            self.cands = {}
+            for b in self.pops:
+                c = np.flatnonzero(ok & (self.bin == b))
+                if c.size:
+                    self.cands[b] = c
+            low = [b for b in self.pops if b < 0 or (1 << b) < deg_cap]
+            if all(b in self.cands for b in low) or nb_cap >= nb_cap_max:
+                break
+            nb_cap *= 2
+        self.nb_cap = nb_cap
+        self.excluded = {b: p for b, p in self.pops.items() if b not in self.cands}
+        v0 = int(np.argmin(deg))
+        t0 = time.perf_counter()
+        oracle.fglt(g, vertices=np.array([v0]), threads=self.threads)
+        self.fixed_s = time.perf_counter() - t0
+
+    def step(self):
+        """One sampled oracle call; returns (wall seconds, estimated full
+        thread-seconds)."""
+        import oracle
+        picks, owner = [], []
+        for b, c in self.cands.items():
+            k = min(self.per_bin, c.size)
+            sel = self.rng.choice(c, size=k, replace=False)
+            picks.append(sel)
+            owner.extend([b] * k)
+        verts = np.concatenate(picks).astype(np.int64)
+        owner = np.array(owner)
+        t0 = time.perf_counter()
+        _, _, t_c3, t_row = oracle.fglt_timed(self.g, verts, threads=self.threads)
+        wall = time.perf_counter() - t0
+        cost = t_c3[verts] + t_row
+        est = sum(self.pops[b] * float(cost[owner == b].mean()) for b in self.cands)
+        return wall, est
+
+    def describe(self, nsteps, est_mean):
+        covered = sum(self.pops[b] for b in self.cands)
+        return (f"stratified vertex sample of the same graph: up to {self.per_bin} vertices per log2-degree bin "
+                f"of degree below {self.deg_cap} whose neighbours' degrees are below {self.nb_cap}, new picks every call "
+                f"({nsteps} calls); per-row oracle seconds extrapolated to the {covered} vertices of the sampled "
+                f"bins ({self.g.n - covered} vertices of {len(self.excluded)} hub bins left out, so the full time "
+                f"is under-estimated); fixed cost {self.fixed_s:.2f} s; estimated full transform "
+                f"{est_mean:.0f} thread-seconds")
+
+    def values(self, est):
+        """(all-cores edges/s, one-core edges/s) of the extrapolated full run."""
+        m = self.g.nnz // 2
+        return m / (self.fixed_s + est / self.threads), m / (self.fixed_s + est)
+
+
+def cpu_baseline(g, calls=2):
+    s = OracleSampler(g, per_bin=3)
+    ests = [s.step()[1] for _ in range(calls)]
+    est = statistics.mean(ests)
+    v_all, v_one = s.values(est)
+    return {"value": v_all, "unit": UNIT, "cores": s.threads, "kind": "oracle",
+            "single_core_value": v_one, "sample": s.describe(calls, est)}
 
 
 # ---------------------------------------------------------------------------
@@ -263,16 +356,26 @@ def bench_batched(fg, torch, dev, num_graphs=20000, reps=5):
     ci = torch.from_numpy(G.colidx).to(dev)
     raw = torch.empty((G.n, 16), dtype=torch.int64, device=dev)
     net = torch.empty((G.n, 16), dtype=torch.int64, device=dev)
-    with fg.Handle(device=dev.index or 0) as h:
-        h.transform_batched(rp, ci, batch.offsets, raw, net)  # runs and captures the CUDA graph
-        h.transform_batched(rp, ci, batch.offsets, raw, net)  # first replay
+    def timed_batches(h, out_raw, out_net):
+        h.transform_batched(rp, ci, batch.offsets, out_raw, out_net)  # runs and captures the CUDA graph
+        h.transform_batched(rp, ci, batch.offsets, out_raw, out_net)  # first replay
         torch.cuda.synchronize()
         times = []
         for _ in range(reps):
             t0 = time.perf_counter()
-            h.transform_batched(rp, ci, batch.offsets, raw, net)
+            h.transform_batched(rp, ci, batch.offsets, out_raw, out_net)
             times.append(time.perf_counter() - t0)
-        t_batch = statistics.median(times)
+        return statistics.median(times)
+
+    # the stage sequence of the single-graph path over the block-diagonal union
+    with fg.Handle(device=dev.index or 0, batch_small_max=-1) as hs:
+        sraw = torch.empty_like(raw)
+        snet = torch.empty_like(net)
+        t_seq = timed_batches(hs, sraw, snet)
+    with fg.Handle(device=dev.index or 0) as h:
+        t_batch = timed_batches(h, raw, net)  # the fused one-block-per-graph launch
+        same_seq = bool(torch.equal(raw, sraw) and torch.equal(net, snet))
+        del sraw, snet
         # one transform per graph (device-resident per-graph CSRs)
         per = []
         for g in range(num_graphs):
@@ -294,12 +397,15 @@ def bench_batched(fg, torch, dev, num_graphs=20000, reps=5):
     return {"workload": f"{num_graphs} graphs, n ~ U{{10..500}}, alternating BA (m ~ U{{2..5}}) and "
                         "random-geometric (mean degree 8), block-diagonal CSR, seed 0",
             "vertices": G.n, "edges": G.m, "graphs_per_s": num_graphs / t_batch,
-            "ms_per_batch": 1000 * t_batch, "per_graph_launch_graphs_per_s": num_graphs / t_per,
-            "speedup_vs_per_graph": t_per / t_batch, "cuda_graph_replay": True,
-            "bit_exact_vs_per_graph_sample": bool(ok)}
+            "ms_per_batch": 1000 * t_batch, "form": "one fused launch, one block per graph, replayed as a CUDA graph",
+            "per_graph_launch_graphs_per_s": num_graphs / t_per, "speedup_vs_per_graph": t_per / t_batch,
+            "stage_sequence_graphs_per_s": num_graphs / t_seq, "stage_sequence_ms_per_batch": 1000 * t_seq,
+            "speedup_vs_stage_sequence": t_seq / t_batch, "cuda_graph_replay": True,
+            "bit_exact_vs_stage_sequence": same_seq, "bit_exact_vs_per_graph_sample": bool(ok)}
 
 
-def bench_serving(fg, torch, dev, num_requests=400, pool_size=24, seed=0, loads=(1.0, 2.0), max_edges=2e6):
+def bench_serving(fg, torch, dev, num_requests=400, pool_size=24, seed=0, loads=(1.0, 2.0, 4.0, 8.0),
+                  max_edges=2e6):
     """Poisson arrivals of graphs with |E| log-uniform in [1e3, max_edges] drawn
     from a pool of distinct R-MAT and Barabasi-Albert graphs, served through
     fglt_stream_submit/poll, against a sequential one-at-a-time FIFO of
@@ -385,6 +491,14 @@ def bench_serving(fg, torch, dev, num_requests=400, pool_size=24, seed=0, loads=
                 "sequential_p50_ms": 1000 * float(np.percentile(seq_lat, 50)),
                 "sequential_p99_ms": 1000 * float(np.percentile(seq_lat, 99)),
                 "bit_exact_vs_alone_sample": bool(ok)})
+    # capacity: the best completion rate over the load points (the top loads
+    # offer far more than either form completes)
+    best = max(out["points"], key=lambda p: p["graphs_per_s"])
+    best_seq = max(out["points"], key=lambda p: p["sequential_graphs_per_s"])
+    out["capacity"] = {"served_graphs_per_s": best["graphs_per_s"], "served_p99_ms": best["p99_ms"],
+                       "sequential_graphs_per_s": best_seq["sequential_graphs_per_s"],
+                       "sequential_p99_ms": best_seq["sequential_p99_ms"],
+                       "ratio": best["graphs_per_s"] / best_seq["sequential_graphs_per_s"]}
     return out
 
 
@@ -415,28 +529,124 @@ def job_value(m_per_rank: int, world: int, ms: float) -> float:
     return world * m_per_rank / (ms / 1000.0)
 
 
+def host_graph(spec):
+    """The workload's graph in host memory (the large R-MAT configurations are
+    drawn by the seeded device generator, then copied to the host)."""
+    if spec["kind"] == "rmat_dev":
+        import torch
+        dg = make_graph(spec, torch.device("cuda", 0))
+        g = dg.to_host()
+        del dg
+        torch.cuda.empty_cache()
+        return g
+    return make_graph(spec)
+
+
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands on the host cores, each
+    step one sampled oracle call on the same graph as the GPU arm, the value
+    the extrapolated full-transform throughput (OracleSampler)."""
     if rank != 0:
         return 0
-    import oracle
-    oracle.build()
-    g = make_graph(CPU_SAMPLE)
+    spec = WORKLOADS[args.workload]
+    g = host_graph(spec)
+    s = OracleSampler(g, per_bin=2)
     for _ in range(args.warmup):
-        oracle_step(g)
-    times = [oracle_step(g) for _ in range(args.steps)]
-    ms = 1000 * statistics.mean(times)
-    value = g.m / (ms / 1000)
+        s.step()
+    walls, ests = [], []
+    for _ in range(args.steps):
+        w, e = s.step()
+        walls.append(w)
+        ests.append(e)
+    est = statistics.mean(ests)
+    value, one_core = s.values(est)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": CPU_SAMPLE["desc"], "n": g.n, "m": g.m},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-                         "sample": CPU_SAMPLE["desc"]},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(walls),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": spec["desc"], "n": g.n, "m": g.m, "nnz": g.nnz},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": s.threads, "kind": "oracle",
+                         "single_core_value": one_core, "sample": s.describe(args.steps, est)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def roofline_of(stage_ms: dict, work: dict, workload: str) -> dict:
+    """Roofline of the dominant stage: algorithmic bytes per transform over the
+    stage's CUDA-event time against the measured HBM copy peak, beside the DRAM
+    bytes ncu counted for that stage (null unless measured on the current
+    kernel source) and the limiter the counters show."""
+    dom = max((k for k in stage_ms if "." not in k), key=stage_ms.get)  # "cyc.*" are parts of "cyc"
+    peak, peak_kind = load_peaks()
+    ab = algorithmic_bytes(dom, work)
+    sec = stage_ms[dom] / 1000
+    achieved = ab / sec / 1e9
+    traffic = traffic_for(dom, workload)
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic, "kernel": dom, "kernel_ms": stage_ms[dom], "algorithmic_bytes": ab,
+           "achieved_kind": "algorithmic bytes (list entries, per-edge C3, per-vertex values) / stage time",
+           "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+           else "fallback 6.8 TB/s"}
+    if traffic:
+        out["dram_gbs"] = traffic / sec / 1e9
+        out["dram_frac"] = out["dram_gbs"] / peak
+        out["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum (profiles/traffic.json)"
+    out["limiter"] = LIMITERS.get((workload, dom), "not characterised for this workload")
+    return out
+
+
+# What the ncu counters of the dominant stages show (profiles/*.md).
+LIMITERS = {
+    ("rmat-s24-ef32", "cyc"): "latency of scattered neighbour-list gathers from DRAM (lists 2 GB, beyond L2): "
+                              "DRAM at a fifth of the copy peak, few loads in flight per warp",
+    ("rmat-s24-ef32", "tri1"): "out-list streaming from DRAM and popcount issue in the clique phase",
+    ("rmat-s20-ef16", "cyc"): "shared-memory atomics and instruction issue; lists and tables stay in L2 "
+                              "(DRAM traffic a few percent of the algorithmic bytes)",
+}
+
+
+def bench_extra_workload(fg, torch, dev, name, flush, args, steps=10, warmup=3):
+    """A second single-graph workload on the same GPU (autotuned, inputs
+    resident, L2 flushed before each timed transform): edges/s, stage times and
+    its roofline."""
+    spec = WORKLOADS[name]
+    g = make_graph(spec, dev)
+    if isinstance(g, gg.DeviceGraph):
+        rp, ci = g.rowptr, g.colidx
+    else:
+        rp = torch.from_numpy(g.rowptr).to(dev)
+        ci = torch.from_numpy(g.colidx).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    with fg.Handle(device=dev.index or 0, profile_stages=True) as h:
+        raw = torch.empty((g.n, 16), dtype=torch.int64, device=dev)
+        net = torch.empty((g.n, 16), dtype=torch.int64, device=dev)
+        tune = None
+        if not args.no_autotune and g.n <= AUTOTUNE_MAX_N:
+            chosen, tuned_ms, default_ms = h.autotune(rp, ci, g.n, reps=1, stream=stream)
+            tune = {"tuned_ms": tuned_ms, "default_ms": default_ms}
+        for _ in range(warmup):
+            h.transform(rp, ci, g.n, raw, net, stream=stream)
+        ts, acc = [], {}
+        for _ in range(steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.transform(rp, ci, g.n, raw, net, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            for k, v in h.stage_times().items():
+                acc.setdefault(k, []).append(v)
+        work = h.work_counters()
+    ms = statistics.mean(ts)
+    stage_ms = {k: statistics.mean(v) for k, v in acc.items()}
+    return {"desc": spec["desc"], "n": g.n, "m": g.m, "value": g.m / (ms / 1000), "unit": UNIT, "steps": steps,
+            "ms_per_step": ms, "stage_ms": {k: v for k, v in stage_ms.items() if "." not in k},
+            "roofline": roofline_of(stage_ms, work, name), "autotune": tune}
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -462,11 +672,14 @@ def run_gpu(args, rank, world, local_rank):
         h.transform(rp, ci, g.n, raw, net, stream=stream)
 
     tune = None
-    if not args.no_autotune:
+    if not args.no_autotune and (args.autotune or g.n <= AUTOTUNE_MAX_N):
         t0 = time.perf_counter()
         chosen, tuned_ms, default_ms = h.autotune(rp, ci, g.n, reps=1, stream=stream)
         tune = {"chosen": chosen, "tuned_ms": tuned_ms, "default_ms": default_ms,
                 "seconds": time.perf_counter() - t0, "note": "untimed set-up before the warm-up steps"}
+    elif not args.no_autotune:
+        tune = {"chosen": "library defaults", "note": f"graphs above {AUTOTUNE_MAX_N} vertices are not "
+                "autotuned by default (about 30 transforms); the defaults were set from autotuner runs"}
 
     for _ in range(args.warmup):
         step()
@@ -509,7 +722,7 @@ def run_gpu(args, rank, world, local_rank):
         hnet = torch.empty((g.n, 16), dtype=torch.int64).pin_memory().numpy()
         fg.fglt_transform_host(h.h, prp, 1, pci, g.n, hraw, hnet)
         tl = []
-        for _ in range(max(3, min(args.steps, 10))):
+        for _ in range(3 if g.n > AUTOTUNE_MAX_N else max(3, min(args.steps, 10))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             fg.fglt_transform_host(h.h, prp, 1, pci, g.n, hraw, hnet)
@@ -523,16 +736,7 @@ def run_gpu(args, rank, world, local_rank):
         return 0
 
     stage_ms = {k: statistics.mean(v) for k, v in stage_acc.items()}
-    dom = max((k for k in stage_ms if "." not in k), key=stage_ms.get)  # "cyc.*" are parts of "cyc"
-    peak, peak_kind = load_peaks()
-    ab = algorithmic_bytes(dom, work)
-    achieved = ab / (stage_ms[dom] / 1000) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic_for(dom, args.workload),
-                "traffic_source": "ncu capture at the default tuning (profiles/traffic.json)",
-                "kernel": dom, "kernel_ms": stage_ms[dom], "algorithmic_bytes": ab,
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                else "fallback 6.8 TB/s"}
+    roofline = roofline_of(stage_ms, work, args.workload)
     value = job_value(g.m, world, ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -554,12 +758,16 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_batched:
         line["batched"] = bench_batched(fg, torch, dev)
     if args.serving_full:
-        line["serving"] = bench_serving(fg, torch, dev, num_requests=5000, pool_size=48, loads=(1.0, 2.0),
+        line["serving"] = bench_serving(fg, torch, dev, num_requests=5000, pool_size=48, loads=(1.0, 2.0, 4.0),
                                         max_edges=2e7)
     elif not args.no_serving:
         line["serving"] = bench_serving(fg, torch, dev)
+    if not args.no_extras and rank == 0:
+        line["extras"] = {w: bench_extra_workload(fg, torch, dev, w, flush, args)
+                          for w in EXTRA_WORKLOADS if w != args.workload}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        gh = g.to_host() if isinstance(g, gg.DeviceGraph) else g
+        line["cpu_baseline"] = cpu_baseline(gh)
     print(json.dumps(line), flush=True)
     h.close()
     return 0
@@ -571,12 +779,15 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat-s20-ef16", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-extras", action="store_true", help="skip the extra workloads (R-MAT s20) of the line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="autotune even on graphs above 2^22 vertices (minutes at R-MAT s24)")
     ap.add_argument("--no-extensions", action="store_true",
                     help="skip timing the Sigma5 transform, edge-list ingest and relabelling")
     ap.add_argument("--set", action="append", metavar="NAME=VALUE",

@@ -142,6 +142,12 @@ typedef struct {
      * degrees, p2 and the triangle counts c3. Applies to every entry point of
      * the handle (fglt_transform_noalloc always computes Sigma16). */
     unsigned int dictionary_mask;
+    /* batch_small_max: fglt_transform_batched computes a batch whose graphs
+     *   all have at most this many vertices with one fused launch, one thread
+     *   block per graph, the graph's adjacency bitmap in shared memory (at
+     *   most 512; 0 selects 512; -1 always runs the stage sequence). Batches
+     *   with a larger graph run the stage sequence. */
+    int batch_small_max;
 } fglt_options;
 
 /* dictionary_mask of Sigma5 = {sigma_0 .. sigma_4}. */
@@ -316,9 +322,13 @@ fglt_status fglt_work_counters(fglt_t handle, int64_t* counters, int max_counter
  *   be NULL (the legacy default stream). Returns after the work completed.
  *   Scratch: one file-scope device array of FGLT_NOALLOC_SCRATCH_BYTES held by
  *   every device that loads the library until exit. Limits: n <=
- *   FGLT_NOALLOC_MAX_VERTICES, rowptr[n] <= FGLT_NOALLOC_MAX_ENTRIES, and a
- *   largest out-degree in the degree order of about 1000 (the triangle pass's
- *   shared-memory bitmap); larger inputs return FGLT_ERR_UNSUPPORTED.
+ *   FGLT_NOALLOC_MAX_VERTICES and rowptr[n] <= FGLT_NOALLOC_MAX_ENTRIES;
+ *   larger inputs return FGLT_ERR_UNSUPPORTED before any device work. Every
+ *   buffer of an input within both limits fits the array (the out-degree
+ *   classes that would need more, above 1024, need more entries than the
+ *   limit); each piece is still checked, and one that did not fit would
+ *   also return FGLT_ERR_UNSUPPORTED. An error return has waited for the
+ *   call's queued work.
  *   The first call on each device looks up the array's address; make it before
  *   any stream capture. All calls share the array and each leaves its data
  *   there: calls whose device work overlaps race — serialise them.

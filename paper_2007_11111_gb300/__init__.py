@@ -74,6 +74,7 @@ class fglt_options(ctypes.Structure):
         ("cyc_long_segment", ctypes.c_int),
         ("cyc_spill_bits", ctypes.c_int),
         ("dictionary_mask", ctypes.c_uint),
+        ("batch_small_max", ctypes.c_int),
     ]
 
     def tuning(self) -> dict:
@@ -339,7 +340,7 @@ class Handle:
                  cyc_mid_threads=(0, 0, 0), cyc_heavy_threads: int = 0, dictionary: int = 0,
                  tri_probe_loads: int = 0, tri_hash_factor: int = 0, cyc_dense_min: int = 0,
                  tri_group_lanes: int = 0, cyc_long_segment: int = 0, tri_warp_max: int = 0,
-                 cyc_spill_bits: int = 0):
+                 cyc_spill_bits: int = 0, batch_small_max: int = 0):
         """dictionary: sub-dictionary bit mask (0 = Sigma16; DICT_SIGMA5 = Sigma5)."""
         opt = fglt_options_default()
         opt.dictionary_mask = int(dictionary)
@@ -357,6 +358,7 @@ class Handle:
         opt.cyc_long_segment = int(cyc_long_segment)
         opt.tri_warp_max = int(tri_warp_max)
         opt.cyc_spill_bits = int(cyc_spill_bits)
+        opt.batch_small_max = int(batch_small_max)
         opt.validate = int(validate)
         opt.profile_stages = int(profile_stages)
         opt.serve_memory_budget = int(serve_memory_budget)

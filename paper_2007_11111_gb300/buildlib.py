@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfglt.so")
 
-SOURCES = ["k_prep.cu", "k_tri.cu", "k_cyc.cu", "k_ingest.cu", "fglt_pipeline.cu", "fglt_capi.cu", "fglt_serve.cu", "fglt_noalloc.cu"]
+SOURCES = ["k_prep.cu", "k_tri.cu", "k_cyc.cu", "k_ingest.cu", "k_small.cu", "fglt_pipeline.cu", "fglt_capi.cu", "fglt_serve.cu", "fglt_noalloc.cu"]
 HEADERS = ["fglt_device.cuh", "fglt_kernels.h", "fglt_pipeline.h", "fglt_serve.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -22,7 +22,7 @@ namespace {
 enum HandleBufId {
   X_H_ROWPTR = B_PIPELINE_COUNT, X_H_COLIDX, X_H_RAW, X_H_NET, X_BATCH_OFF,
   X_IN_DEG0, X_IN_RP0, X_IN_CUR, X_IN_TMP, X_IN_DEG, X_IN_SCAN, X_IN_CNT, X_IN_SORT,
-  X_RL_D, X_RL_HIST, X_RL_BASE, X_RL_CURSOR, X_RL_RANK, X_RL_INV, X_RL_NDEG,
+  X_RL_D, X_RL_HIST, X_RL_BASE, X_RL_CURSOR, X_RL_RANK, X_RL_INV, X_RL_NDEG, X_SMALL_ORDER, X_SMALL_CNT,
   X_COUNT
 };
 
@@ -62,6 +62,8 @@ struct fglt_handle {
     int64_t* net = nullptr;
     int rp64 = 0;
     int64_t n = 0, nnz = 0, maxg = 0;
+    bool small = false;     // the fused small-graph launch (else the stage sequence)
+    uint64_t off_hash = 0;  // fused launch: hash of the graph offsets it was set up for
     cudaGraphExec_t exec = nullptr;
   } batch;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -361,6 +363,101 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
   return FGLT_OK;
 }
 
+// Batched transform of graphs of at most SMALL_N_MAX vertices: one fused
+// launch (k_small_fglt), captured as a CUDA graph and replayed while the
+// buffers and the graph offsets stay the same. The device copies of the
+// offsets and of the work order (largest graphs first) are made when they
+// change. Called with h->mu held; runs on cs.
+fglt_status batched_small(fglt_t h, const void* rowptr, int rp64, const int32_t* colidx, const int64_t* off,
+                          int64_t num_graphs, int64_t* out_raw, int64_t* out_net, cudaStream_t cs) {
+  const int64_t n = off[num_graphs];
+  SubDict sd;
+  fglt_status s = make_subdict(h->opt.dictionary_mask, &sd);
+  if (s != FGLT_OK) return s;
+  int64_t nnz = 0;
+  {
+    HandleWs ws(h, cs);
+    int32_t v32 = 0;
+    s = rp64 ? ws.read(&nnz, static_cast<const int64_t*>(rowptr) + n, 8, cs)
+             : ws.read(&v32, static_cast<const int32_t*>(rowptr) + n, 4, cs);
+    if (s != FGLT_OK) return s;
+    if (!rp64) nnz = v32;
+  }
+  if (nnz < 0) return FGLT_ERR_INVALID_GRAPH;
+  if (nnz > 0 && !colidx) return FGLT_ERR_INVALID_ARG;
+  const bool full = sd.k == 16;
+  uint64_t hash = 1469598103934665603ull;  // FNV-1a over the offsets
+  for (int64_t i = 0; i <= num_graphs; ++i) hash = (hash ^ (uint64_t)off[i]) * 1099511628211ull;
+  auto& bc = h->batch;
+  void *doff = nullptr, *dorder = nullptr, *dcnt = nullptr;
+  if ((s = need(h, X_BATCH_OFF, (size_t)(num_graphs + 1) * 8, &doff, cs)) != FGLT_OK) return s;
+  if ((s = need(h, X_SMALL_ORDER, (size_t)std::max<int64_t>(num_graphs, 1) * 4, &dorder, cs)) != FGLT_OK) return s;
+  if ((s = need(h, X_SMALL_CNT, 16, &dcnt, cs)) != FGLT_OK) return s;
+  int* cnt = static_cast<int*>(dcnt);  // [0] work queue, [1] error word
+  const bool same = bc.valid && bc.small && bc.rowptr == rowptr && bc.colidx == colidx && bc.raw == out_raw &&
+                    bc.net == out_net && bc.rp64 == rp64 && bc.n == n && bc.nnz == nnz && bc.maxg == num_graphs &&
+                    bc.off_hash == hash;
+  if (!same) {
+    std::vector<int32_t> order((size_t)num_graphs);
+    for (int64_t i = 0; i < num_graphs; ++i) order[(size_t)i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return off[a + 1] - off[a] > off[b + 1] - off[b];
+    });
+    CK(cudaMemcpyAsync(doff, off, (size_t)(num_graphs + 1) * 8, cudaMemcpyHostToDevice, cs));
+    CK(cudaMemcpyAsync(dorder, order.data(), (size_t)num_graphs * 4, cudaMemcpyHostToDevice, cs));
+    CK(cudaStreamSynchronize(cs));  // the host order vector goes out of scope
+    if (bc.exec) {
+      cudaGraphExecDestroy(bc.exec);
+      bc.exec = nullptr;
+    }
+    bc.valid = false;
+    Csr g{rowptr, rp64 != 0, colidx, n, nnz};
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t e = cudaMemsetAsync(cnt, 0, 16, cs);
+      if (e == cudaSuccess)
+        e = launch_small_fglt(g, static_cast<const int64_t*>(doff), static_cast<const int32_t*>(dorder),
+                              num_graphs, cnt, out_raw, out_net, sd, full, cnt + 1, cs);
+      const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+      if (e == cudaSuccess && ee == cudaSuccess && graph && cudaGraphInstantiate(&bc.exec, graph, 0) == cudaSuccess) {
+        bc.valid = true;
+        bc.small = true;
+        bc.rowptr = rowptr;
+        bc.colidx = colidx;
+        bc.raw = out_raw;
+        bc.net = out_net;
+        bc.rp64 = rp64;
+        bc.n = n;
+        bc.nnz = nnz;
+        bc.maxg = num_graphs;
+        bc.off_hash = hash;
+      }
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+    if (!bc.valid) {  // capture unavailable: launch directly
+      Csr g2{rowptr, rp64 != 0, colidx, n, nnz};
+      CK(cudaMemsetAsync(cnt, 0, 16, cs));
+      CK(launch_small_fglt(g2, static_cast<const int64_t*>(doff), static_cast<const int32_t*>(dorder), num_graphs,
+                           cnt, out_raw, out_net, sd, full, cnt + 1, cs));
+    }
+  }
+  if (bc.valid) {
+    CK(cudaGraphLaunch(bc.exec, cs));
+    ++h->batch_replays;
+  }
+  int e = 0;
+  {
+    HandleWs ws(h, cs);
+    s = ws.read(&e, cnt + 1, sizeof e, cs);
+  }
+  if (s != FGLT_OK) return s;
+  h->work_valid = false;
+  h->stages_valid = false;
+  if (e & (ERR_BAD_GRAPH | ERR_BAD_ROWPTR)) return FGLT_ERR_INVALID_GRAPH;
+  return e ? FGLT_ERR_INTERNAL : FGLT_OK;
+}
+
 extern "C" {
 
 fglt_status fglt_options_default(fglt_options* opt) {
@@ -519,6 +616,9 @@ fglt_status fglt_transform_batched(fglt_t h, const void* rowptr, int rowptr_is_6
     }
     return st;
   };
+  const int small_max = h->opt.batch_small_max == 0 ? SMALL_N_MAX : std::min(h->opt.batch_small_max, SMALL_N_MAX);
+  if (small_max > 0 && maxg <= small_max)
+    return finish(batched_small(h, rowptr, rowptr_is_64bit, colidx, graph_offsets, num_graphs, out_raw, out_net, cs));
   int64_t nnz = 0;
   {
     HandleWs ws(h, cs);
@@ -540,7 +640,7 @@ fglt_status fglt_transform_batched(fglt_t h, const void* rowptr, int rowptr_is_6
   Bounds b{nnz, (int32_t)std::max<int64_t>(maxg - 1, 0), std::max<int64_t>(maxg - 1, 1), off_dev, num_graphs};
   Csr g{rowptr, rowptr_is_64bit != 0, colidx, n, nnz};
   auto& bc = h->batch;
-  const bool same = bc.valid && bc.rowptr == rowptr && bc.colidx == colidx && bc.raw == out_raw &&
+  const bool same = bc.valid && !bc.small && bc.rowptr == rowptr && bc.colidx == colidx && bc.raw == out_raw &&
                     bc.net == out_net && bc.rp64 == rowptr_is_64bit && bc.n == n && bc.nnz == nnz &&
                     bc.maxg == maxg;
   if (same && !h->opt.validate && !h->opt.profile_stages) {
@@ -573,6 +673,7 @@ fglt_status fglt_transform_batched(fglt_t h, const void* rowptr, int rowptr_is_6
     if (cap == FGLT_OK && ee == cudaSuccess && graph &&
         cudaGraphInstantiate(&bc.exec, graph, 0) == cudaSuccess) {
       bc.valid = true;
+      bc.small = false;
       bc.rowptr = rowptr;
       bc.colidx = colidx;
       bc.raw = out_raw;

@@ -67,6 +67,50 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
   return s;  // valid in warp 0
 }
 
+// Table I of one vertex from its per-vertex quantities: degree d = p1, p2, p3,
+// c3, and the SpMV / listing sums d^7, d^9, d^10, d^12 .. d^15 (Sec. 4).
+__device__ __forceinline__ void table1_row(long long d, long long p2, long long p3, long long c3, long long r7,
+                                           long long r9, long long r10, long long r12, long long r13, long long r14,
+                                           long long r15, long long f[16]) {
+  f[0] = 1;
+  f[1] = d;
+  f[2] = p2;
+  f[3] = d * (d - 1) / 2;
+  f[4] = c3;
+  f[5] = p3;
+  f[6] = p2 * (d - 1) - 2 * c3;
+  f[7] = r7;
+  f[8] = (d * (d - 1) / 2) * (d - 2) / 3;
+  f[9] = r9;
+  f[10] = r10;
+  f[11] = (d - 2) * c3;
+  f[12] = r12;
+  f[13] = r13;
+  f[14] = r14;
+  f[15] = r15;
+}
+
+// Net frequencies g = U16^{-1} f (Table II), the inverse written out; exact
+// in int64.
+__device__ __forceinline__ void u16_inverse(const long long f[16], long long g[16]) {
+  g[0] = f[0];
+  g[1] = f[1];
+  g[2] = f[2] - 2 * f[4];
+  g[3] = f[3] - f[4];
+  g[4] = f[4];
+  g[5] = f[5] - 2 * f[9] - f[10] - 2 * f[12] + 4 * f[13] + 2 * f[14] - 6 * f[15];
+  g[6] = f[6] - f[10] - 2 * f[11] - 2 * f[12] + 2 * f[13] + 4 * f[14] - 6 * f[15];
+  g[7] = f[7] - f[9] - f[10] + 2 * f[13] + f[14] - 3 * f[15];
+  g[8] = f[8] - f[11] + f[14] - f[15];
+  g[9] = f[9] - 2 * f[13] + 3 * f[15];
+  g[10] = f[10] - 2 * f[13] - 2 * f[14] + 6 * f[15];
+  g[11] = f[11] - 2 * f[14] + 3 * f[15];
+  g[12] = f[12] - f[13] - f[14] + 3 * f[15];
+  g[13] = f[13] - 3 * f[15];
+  g[14] = f[14] - 3 * f[15];
+  g[15] = f[15];
+}
+
 // Lets fn use the device's full opt-in shared memory per block. Every caller
 // sets the same value, so concurrent host threads launching the kernel with
 // different dynamic sizes cannot shrink the limit under one another.

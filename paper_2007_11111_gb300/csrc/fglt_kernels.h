@@ -204,6 +204,18 @@ cudaError_t launch_relabel_fill(const void* rowptr, bool rp64, const int32_t* co
                                 const int32_t* inv, int64_t n, const int64_t* out_rowptr, int32_t* out_colidx,
                                 int* err, cudaStream_t st);
 
+// --- batched small graphs (k_small.cu) ------------------------------------------
+// Largest graph (vertices) of the fused small-graph launch.
+constexpr int SMALL_N_MAX = 512;
+struct SubDict;
+// One block per graph of a block-diagonal batch (graph g owns vertices
+// [off[g], off[g+1]), at most SMALL_N_MAX of them; blocks take the graphs in
+// the given order): the whole transform in shared memory, Table I and
+// U16^{-1} (or the sub-dictionary sd when !full) into raw / net. *next (zeroed)
+// is the work queue; structural violations set ERR_BAD_GRAPH in *err.
+cudaError_t launch_small_fglt(const Csr& g, const int64_t* off, const int32_t* order, int64_t num_graphs, int* next,
+                              int64_t* raw, int64_t* net, const SubDict& sd, bool full, int* err, cudaStream_t st);
+
 // --- epilogue ------------------------------------------------------------------
 struct EpilogueIn {
   const int32_t* d;

@@ -113,12 +113,17 @@ extern "C" fglt_status fglt_transform_noalloc(const void* rowptr, int rowptr_is_
     CK(cudaStreamSynchronize(st));
     nnz = v;
   }
-  CK(cudaStreamSynchronize(st));
+  if (rowptr_is_64bit) CK(cudaStreamSynchronize(st));
   if (nnz < 0) return FGLT_ERR_INVALID_GRAPH;
   if (nnz > FGLT_NOALLOC_MAX_ENTRIES) return FGLT_ERR_UNSUPPORTED;
   if (nnz > 0 && !colidx) return FGLT_ERR_INVALID_ARG;
   Csr g{rowptr, rowptr_is_64bit != 0, colidx, n, nnz};
   CarverWs ws(scratch);
   RunOptions ro;  // default tuning, no validation, no profiling
-  return run_pipeline(ws, g, out_raw, out_net, st, ro);
+  const fglt_status s = run_pipeline(ws, g, out_raw, out_net, st, ro);
+  // An error can leave work of this call queued on st (a buffer that did not
+  // fit stops the sequence midway); wait for it, so that no later call, on
+  // any stream, meets it still writing the shared array.
+  if (s != FGLT_OK) cudaStreamSynchronize(st);
+  return s;
 }

@@ -17,6 +17,8 @@
 #include <cstring>
 #include <initializer_list>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fglt_device.cuh"
 
 namespace fglt {
@@ -40,6 +42,20 @@ enum CounterId {
 // 64-bit work counters: triangle-pass scanned entries, triangles, 4-cliques,
 // max and total wedges of the 4-cycle stage, largest global table need.
 enum Counter64Id { W_PROBES, W_TRIANGLES, W_K4, W_WMAX, W_WSUM, W_GCAP, W_CLS, W_NUM = W_CLS + CYC_CLASSES };
+
+// One NVTX range per stage of a transform (named as in fglt_stage_times),
+// for timeline tools; at most one is open, and the last closes on return.
+struct StageRange {
+  bool open = false;
+  void to(int i) {
+    if (open) nvtxRangePop();
+    open = i < NUM_STAGES;
+    if (open) nvtxRangePushA(STAGE_NAMES[i]);
+  }
+  ~StageRange() {
+    if (open) nvtxRangePop();
+  }
+};
 
 int bits_for(int64_t cap) {
   int hb = 5;
@@ -178,8 +194,10 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   Csr g = in;
   const int64_t n = g.n;
   const int64_t launches0 = g_launches;
+  StageRange range;
   auto mark = [&](int i) {
     if (ro.stage_events && !capturing) cudaEventRecord(ro.stage_events[i], st);
+    range.to(i);
   };
   auto sub = [&](int i, int edge) {  // sub-stage i: edge 0 = start, 1 = stop
     if (!ro.sub_events || capturing) return;
@@ -316,7 +334,8 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   // The last class holds the vertices whose adjacency bitmap of the first
   // pass only fits in global memory.
   const int HF = tu.tri_hash_factor;
-  const int T2 = std::max(T1, tri1_smem_bitmap_max(HF));
+  // (at most 1024: above it the probe tables of the classes double in size)
+  const int T2 = std::max(T1, std::min(1024, tri1_smem_bitmap_max(HF)));
   // The first class (out-degree up to TW) runs one warp per vertex.
   const int TW = std::min(tu.tri_warp, tri_warp_max());
   int32_t* twork;

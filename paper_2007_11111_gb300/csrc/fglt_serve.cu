@@ -45,6 +45,7 @@ struct Request {
   double latency_us = 0;
   State state = QUEUED;
   fglt_status status = FGLT_OK;
+  int passed = 0;  // times a later request was admitted ahead of this one
 };
 
 // Device bytes a request occupies while on the device: the packed input and
@@ -110,8 +111,9 @@ struct Lane {
   std::thread th;
   HostBuf<int64_t> h_rowptr, h_raw, h_net;
   HostBuf<int32_t> h_colidx;
-  DevBuf<int64_t> d_rowptr, d_raw, d_net;
+  DevBuf<int64_t> d_rowptr, d_raw, d_net, d_parts;
   DevBuf<int32_t> d_colidx;
+  HostBuf<int64_t> h_parts;
 };
 
 struct Server {
@@ -132,6 +134,23 @@ namespace {
 
 constexpr int64_t BOUNDED_MAX_GRAPH = 4096;      // packs whose graphs are all this small skip read-backs
 constexpr int64_t PACK_MAX_ENTRIES = 1LL << 22;  // a pack stops growing past this many CSR entries
+constexpr int ADMIT_LOOKAHEAD = 64;  // queued requests scanned per admission
+constexpr int MAX_PASSED = 8;        // a request overtaken this often stops later ones from passing it
+
+// Block-diagonal packing on the device: the parts' rows and columns were
+// copied with their own (local) ids; part p = (vertex offset, entry offset,
+// n, nnz) at parts[4p..4p+3]. Adds the vertex offset to its columns and the
+// entry offset to its row pointers rowptr[vo+1 .. vo+n].
+__global__ void k_rebase_pack(int64_t* __restrict__ rowptr, int32_t* __restrict__ colidx,
+                              const int64_t* __restrict__ parts, int np) {
+  const int p = blockIdx.y;
+  if (p >= np) return;
+  const int64_t vo = parts[4 * p], eo = parts[4 * p + 1], n = parts[4 * p + 2], nnz = parts[4 * p + 3];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += stride)
+    colidx[eo + k] += (int32_t)vo;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) rowptr[vo + 1 + v] += eo;
+}
 
 // Runs one pack on a lane. Returns the status of the whole pack.
 fglt_status run_pack(Server* S, Lane* L, const std::vector<Request*>& pack) {
@@ -143,24 +162,45 @@ fglt_status run_pack(Server* S, Lane* L, const std::vector<Request*>& pack) {
   if (!L->h_rowptr.reserve(n + 1) || !L->h_colidx.reserve(std::max<int64_t>(nnz, 1)) ||
       !L->h_raw.reserve(n * columns_of(L->h)) || !L->h_net.reserve(n * columns_of(L->h)))
     return FGLT_ERR_OOM;
-  // Block-diagonal packing with global vertex ids.
+  // Block-diagonal packing: each part is copied as it is (local ids) and the
+  // device adds its offsets (k_rebase_pack).
+  const int np = (int)pack.size();
+  if (!L->h_parts.reserve(4 * (size_t)np)) return FGLT_ERR_OOM;
   int64_t vo = 0, eo = 0;
   L->h_rowptr.p[0] = 0;
-  for (Request* r : pack) {
-    for (int64_t i = 0; i < r->n; ++i) L->h_rowptr.p[vo + i + 1] = r->rowptr[i + 1] + eo;
-    for (int64_t k = 0; k < r->nnz; ++k) L->h_colidx.p[eo + k] = r->colidx[k] + (int32_t)vo;
+  for (int p = 0; p < np; ++p) {
+    const Request* r = pack[p];
+    std::memcpy(L->h_rowptr.p + vo + 1, r->rowptr.data() + 1, (size_t)r->n * 8);
+    if (r->nnz) std::memcpy(L->h_colidx.p + eo, r->colidx.data(), (size_t)r->nnz * 4);
+    int64_t* q = L->h_parts.p + 4 * p;
+    q[0] = vo;
+    q[1] = eo;
+    q[2] = r->n;
+    q[3] = r->nnz;
     vo += r->n;
     eo += r->nnz;
   }
   cudaStream_t st = handle_stream(L->h);
   if (!L->d_rowptr.reserve(n + 1, st) || !L->d_colidx.reserve(std::max<int64_t>(nnz, 1), st) ||
-      !L->d_raw.reserve(n * columns_of(L->h), st) || !L->d_net.reserve(n * columns_of(L->h), st))
+      !L->d_raw.reserve(n * columns_of(L->h), st) || !L->d_net.reserve(n * columns_of(L->h), st) ||
+      !L->d_parts.reserve(4 * (size_t)np, st))
     return FGLT_ERR_OOM;
   if (cudaMemcpyAsync(L->d_rowptr.p, L->h_rowptr.p, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return FGLT_ERR_CUDA;
   if (nnz > 0 &&
       cudaMemcpyAsync(L->d_colidx.p, L->h_colidx.p, (size_t)nnz * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return FGLT_ERR_CUDA;
+  if (np > 1) {
+    if (cudaMemcpyAsync(L->d_parts.p, L->h_parts.p, (size_t)np * 32, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return FGLT_ERR_CUDA;
+    const int64_t biggest = std::max_element(pack.begin(), pack.end(), [](const Request* a, const Request* b) {
+                              return a->nnz < b->nnz;
+                            })[0]->nnz;
+    const unsigned gx = (unsigned)std::min<int64_t>(std::max<int64_t>((biggest + 255) / 256, 1), 1024);
+    k_rebase_pack<<<dim3(gx, (unsigned)np), 256, 0, st>>>(L->d_rowptr.p, L->d_colidx.p, L->d_parts.p, np);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) return FGLT_ERR_CUDA;
+  }
   Csr g{L->d_rowptr.p, true, L->d_colidx.p, n, nnz};
   // Packs of small graphs run the stage sequence without host read-backs:
   // the largest request bounds every degree and every per-vertex table.
@@ -198,15 +238,25 @@ void lane_loop(Server* S, Lane* L) {
       for (;;) {
         if (S->stop && S->queue.empty()) return;
         if (!S->queue.empty()) {
-          // Admit from the front while the pack fits this lane's share of the budget.
+          // Admit in arrival order while the pack fits this lane's share of
+          // the budget. A request that does not fit (memory, or a pack already
+          // near its size limit) may be overtaken by later ones within the
+          // first ADMIT_LOOKAHEAD of the queue, until it has been passed
+          // MAX_PASSED times; then nothing passes it.
           int64_t pack_nnz = 0;
-          while (!S->queue.empty() && (int)pack.size() < S->max_batch) {
-            Request* r = S->queue.front();
-            if (pack_est + r->est > S->lane_cap || S->reserved + r->est > S->budget) break;
-            // a large request runs alone rather than holding small ones back
-            if (!pack.empty() && pack_nnz + r->nnz > PACK_MAX_ENTRIES) break;
+          size_t i = 0;
+          while (i < S->queue.size() && i < (size_t)ADMIT_LOOKAHEAD && (int)pack.size() < S->max_batch) {
+            Request* r = S->queue[i];
+            const bool fits = pack_est + r->est <= S->lane_cap && S->reserved + r->est <= S->budget &&
+                              (pack.empty() || pack_nnz + r->nnz <= PACK_MAX_ENTRIES);
+            if (!fits) {
+              if (r->passed >= MAX_PASSED) break;
+              ++i;
+              continue;
+            }
+            for (size_t k = 0; k < i; ++k) ++S->queue[k]->passed;
             pack_nnz += r->nnz;
-            S->queue.pop_front();
+            S->queue.erase(S->queue.begin() + (std::ptrdiff_t)i);
             r->state = RUNNING;
             pack.push_back(r);
             pack_est += r->est;
@@ -308,6 +358,8 @@ void destroy(Server* S) {
     L->d_colidx.release();
     L->d_raw.release();
     L->d_net.release();
+    L->d_parts.release();
+    L->h_parts.release();
     if (L->h) fglt_destroy(L->h);
     delete L;
   }

@@ -32,8 +32,10 @@
 //  - the dense window with the other tops in a per-block global-memory hash
 //    table (heavy vertices with many tops outside the window),
 //  - or a global-memory hash table alone (fallback).
-// Wedges are walked cooperatively: the segments of N+(v) of many middles v are
-// concatenated and split evenly over the lanes of a warp or a block.
+// Wedges are walked cooperatively: in the warp class the segments of N+(v) of
+// many middles v are concatenated and split evenly over the lanes; in the block
+// classes long segments are walked one warp each and short ones one group of
+// lanes each.
 #include "fglt_device.cuh"
 #include "fglt_kernels.h"
 
@@ -313,9 +315,8 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const int64_t* __restrict__
 // ---------------------------------------------------------------------------
 // Larger vertices: one block per w. N(w) is taken CH middles at a time;
 // the non-empty segments of the chunk are compacted into shared memory with
-// their exclusive wedge prefix, and the chunk's wedges are split evenly over
-// the block's warps, 32 consecutive wedges per warp step (the owner of each
-// lane follows from the segment starts that fall inside the step).
+// their exclusive wedge prefix; long segments are walked one warp each, short
+// ones one group of SHORT_LANES lanes each.
 //
 // MODE 0: hash table in shared memory sized per w (at most 2^13 slots)
 // MODE 1: dense 16-bit counters for tops >= hub_lo + 2^12-slot shared hash
@@ -323,9 +324,10 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const int64_t* __restrict__
 // MODE 3: hash table in global memory sized per w (fallback)
 // ---------------------------------------------------------------------------
 constexpr int CHUNK_MAX = 512;  // middles per chunk: min(block size, 512)
+constexpr int SHORT_LANES = 8;  // lanes per short segment
 
 // Segments at least long_seg long are walked warp-per-segment (coalesced, one
-// owner); shorter ones are concatenated and split evenly over the lanes.
+// owner); shorter ones by lane groups (walk_short).
 
 struct Segs {
   int64_t* st;      // [chunk] short segments: start in ocol
@@ -370,7 +372,7 @@ __device__ __forceinline__ long long block_excl_scan(long long x, long long* scr
 
 // Segments of the middles c0 .. c0 + chunk of w: long ones listed for
 // warp-per-segment walks, short non-empty ones compacted with their wedge
-// prefix for the flattened walk (one packed block scan).
+// prefix for the group walk (one packed block scan).
 __device__ __forceinline__ void build_chunk(const Segs& S, const Mids& M, int64_t c0, int64_t n, int chunk,
                                             int long_seg) {
   const int64_t k = c0 + threadIdx.x;
@@ -433,63 +435,31 @@ __device__ __forceinline__ void walk_long(const Segs& S, const int32_t* __restri
   }
 }
 
-// Walks the current chunk's wedges. Warp k takes the contiguous range
-// [k*per, (k+1)*per) of the chunk's wedge space, 32 wedges per step; the
-// owner segment of each lane follows from the segment starts inside the step
-// (segments are non-empty, so starts are distinct). f(u, j, valid) is called
-// by every lane (valid = false past the end) so that it may use warp
-// collectives.
-template <typename F>
-__device__ __forceinline__ void walk_chunk(const Segs& S, const int32_t* __restrict__ ocol, F f) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+// Short segments: groups of SG lanes take them round-robin over the block's
+// groups; a group's lanes stride over one segment, two list loads in flight
+// per lane. g(u) per wedge; with SUM, done(j, s) is called by the group's
+// first lane with the group's sum s of g over segment j.
+template <int SG, bool SUM, typename G, typename D>
+__device__ __forceinline__ void walk_short(const Segs& S, const int32_t* __restrict__ ocol, G g, D done) {
+  const int lane = threadIdx.x & 31, gl = lane % SG;
+  const unsigned gmask = (SG == 32 ? 0xffffffffu : ((1u << SG) - 1u)) << (lane & ~(SG - 1));
+  const int ngrp = blockDim.x / SG;
   const int ns = S.misc[0];
-  const int total = S.pre[ns];
-  const int per = ((total + nwarps - 1) / nwarps + 31) & ~31;
-  const int w0 = warp * per;
-  const int w1 = min(w0 + per, total);
-  if (w0 >= w1) return;
-  int lo = 0, hi = ns - 1;  // segment containing w0
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (S.pre[mid] <= w0) lo = mid; else hi = mid - 1;
-  }
-  const uint32_t upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-  // Step t0: this lane's owner segment j and its list entry u. The next
-  // step's load is issued before f runs on the current one (two loads in
-  // flight per lane).
-  int base = lo;  // owner of wedge t0
-  auto locate = [&](int t0, int& j, uint32_t& u, bool& valid, int& nbase) {
-    const int jb = base + 1 + lane;
-    uint32_t bit = 0;
-    if (jb < ns) {
-      const int r = S.pre[jb] - t0;
-      if (r < 32) bit = 1u << r;
+  for (int j = threadIdx.x / SG; j < ns; j += ngrp) {
+    const int32_t* p = ocol + S.st[j];
+    const int len = S.pre[j + 1] - S.pre[j];
+    u64 sum = 0;
+    for (int k = gl; k < len; k += 2 * SG) {
+      const uint32_t u0 = (uint32_t)__ldg(p + k);
+      const uint32_t u1 = k + SG < len ? (uint32_t)__ldg(p + k + SG) : 0u;
+      sum += g(u0);
+      if (k + SG < len) sum += g(u1);
     }
-    const uint32_t M = __reduce_or_sync(0xffffffffu, bit);
-    j = base + __popc(M & upto);
-    const int t = t0 + lane;
-    valid = t < w1;
-    u = 0;
-    if (valid) u = (uint32_t)__ldg(ocol + S.st[j] + (t - S.pre[j]));
-    // owner of t0 + 32
-    nbase = base + __popc(M);
-    if (nbase + 1 < ns && S.pre[nbase + 1] == t0 + 32) ++nbase;
-  };
-  int j, nbase;
-  uint32_t u;
-  bool valid;
-  locate(w0, j, u, valid, nbase);
-  for (int t0 = w0; t0 < w1; t0 += 32) {
-    base = nbase;
-    int j2 = 0, nb2 = nbase;
-    uint32_t u2 = 0;
-    bool v2 = false;
-    if (t0 + 32 < w1) locate(t0 + 32, j2, u2, v2, nb2);
-    f(u, j, valid);
-    j = j2;
-    u = u2;
-    valid = v2;
-    nbase = nb2;
+    if (SUM) {
+#pragma unroll
+      for (int o = SG / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(gmask, sum, o, SG);
+      if (gl == 0) done(j, sum);
+    }
   }
 }
 
@@ -590,9 +560,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
     for (int64_t c0 = 0; c0 < M.K; c0 += CH) {
       build_chunk(S, M, c0, n, CH, long_seg);
       walk_long(S, ocol, [&](uint32_t u) -> u64 { count(u); return 0; }, [](int32_t, u64) {});
-      walk_chunk(S, ocol, [&](uint32_t u, int, bool valid) {
-        if (valid) count(u);
-      });
+      walk_short<SHORT_LANES, false>(S, ocol, [&](uint32_t u) -> u64 { count(u); return 0; }, [](int, u64) {});
       __syncthreads();
     }
     // Pass B: each middle gains cnt[u] - 1 per wedge.
@@ -607,11 +575,8 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
         sum = warp_sum_u64(sum);
         if ((tid & 31) == 0 && sum) atomicAdd(&r12r[rv], sum);
       });
-      walk_chunk(S, ocol, [&](uint32_t u, int j, bool valid) {
-        const u64 c = valid ? credit(u) : 0;
-        bool head;
-        const uint32_t sum = run_sum((uint32_t)c, valid ? j : -1, head);
-        if (head && valid && sum) atomicAdd(&S.acc[j], (u64)sum);
+      walk_short<SHORT_LANES, true>(S, ocol, credit, [&](int j, u64 sum) {
+        if (sum) S.acc[j] += sum;  // one group per segment
       });
       __syncthreads();
       const int ns = S.misc[0];

@@ -607,44 +607,11 @@ __global__ void k_unrank_u64(const u64* __restrict__ src, const int32_t* __restr
 template <bool VEC>
 __global__ void k_epilogue(EpilogueIn in, int64_t n, int64_t* __restrict__ raw, int64_t* __restrict__ net) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const long long d = in.d[v];
     const int32_t r = in.rank[v];
-    const long long c3 = (long long)in.c3r[r];
-    const long long p2 = in.p2[v];
-    long long f[16];
-    f[0] = 1;
-    f[1] = d;
-    f[2] = p2;
-    f[3] = d * (d - 1) / 2;
-    f[4] = c3;
-    f[5] = in.p3[v];
-    f[6] = p2 * (d - 1) - 2 * c3;
-    f[7] = in.r7[v];
-    f[8] = (d * (d - 1) / 2) * (d - 2) / 3;
-    f[9] = in.r9[v];
-    f[10] = (long long)in.r10r[r];
-    f[11] = (d - 2) * c3;
-    f[12] = (long long)in.r12r[r];
-    f[13] = (long long)in.r13r[r];
-    f[14] = (long long)in.r14r[r];
-    f[15] = (long long)in.r15r[r];
-    long long g[16];
-    g[0] = f[0];
-    g[1] = f[1];
-    g[2] = f[2] - 2 * f[4];
-    g[3] = f[3] - f[4];
-    g[4] = f[4];
-    g[5] = f[5] - 2 * f[9] - f[10] - 2 * f[12] + 4 * f[13] + 2 * f[14] - 6 * f[15];
-    g[6] = f[6] - f[10] - 2 * f[11] - 2 * f[12] + 2 * f[13] + 4 * f[14] - 6 * f[15];
-    g[7] = f[7] - f[9] - f[10] + 2 * f[13] + f[14] - 3 * f[15];
-    g[8] = f[8] - f[11] + f[14] - f[15];
-    g[9] = f[9] - 2 * f[13] + 3 * f[15];
-    g[10] = f[10] - 2 * f[13] - 2 * f[14] + 6 * f[15];
-    g[11] = f[11] - 2 * f[14] + 3 * f[15];
-    g[12] = f[12] - f[13] - f[14] + 3 * f[15];
-    g[13] = f[13] - 3 * f[15];
-    g[14] = f[14] - 3 * f[15];
-    g[15] = f[15];
+    long long f[16], g[16];
+    table1_row(in.d[v], in.p2[v], in.p3[v], (long long)in.c3r[r], in.r7[v], in.r9[v], (long long)in.r10r[r],
+               (long long)in.r12r[r], (long long)in.r13r[r], (long long)in.r14r[r], (long long)in.r15r[r], f);
+    u16_inverse(f, g);
     if (VEC) {  // both outputs 16-byte aligned
       if (raw) {
         longlong2* o = reinterpret_cast<longlong2*>(raw + v * 16);
@@ -672,27 +639,10 @@ __global__ void k_epilogue(EpilogueIn in, int64_t n, int64_t* __restrict__ raw, 
 __global__ void k_epilogue_sub(EpilogueIn in, SubDict sd, int64_t n, int64_t* __restrict__ raw,
                                int64_t* __restrict__ net) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const long long d = in.d[v];
     const int32_t r = in.rank[v];
-    const long long c3 = (long long)in.c3r[r];
-    const long long p2 = in.p2[v];
     long long f[16];
-    f[0] = 1;
-    f[1] = d;
-    f[2] = p2;
-    f[3] = d * (d - 1) / 2;
-    f[4] = c3;
-    f[5] = in.p3[v];
-    f[6] = p2 * (d - 1) - 2 * c3;
-    f[7] = in.r7[v];
-    f[8] = (d * (d - 1) / 2) * (d - 2) / 3;
-    f[9] = in.r9[v];
-    f[10] = (long long)in.r10r[r];
-    f[11] = (d - 2) * c3;
-    f[12] = (long long)in.r12r[r];
-    f[13] = (long long)in.r13r[r];
-    f[14] = (long long)in.r14r[r];
-    f[15] = (long long)in.r15r[r];
+    table1_row(in.d[v], in.p2[v], in.p3[v], (long long)in.c3r[r], in.r7[v], in.r9[v], (long long)in.r10r[r],
+               (long long)in.r12r[r], (long long)in.r13r[r], (long long)in.r14r[r], (long long)in.r15r[r], f);
     long long fs[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {

@@ -100,6 +100,35 @@ def test_served_results_equal_alone(fg):
         assert all(x > 0 for x in lat)
         st, _ = fg.fglt_stream_poll(h.h, ids[0], 0)
         assert st == fg.FGLT_ERR_NOT_FOUND  # collected ids are retired
+    # and the served rows against the oracle directly
+    for k, g in enumerate(graphs):
+        oraw, onet = oracle.fglt(g)
+        np.testing.assert_array_equal(outs[k][0], oraw, err_msg=f"request {k} raw vs oracle")
+        np.testing.assert_array_equal(outs[k][1], onet, err_msg=f"request {k} net vs oracle")
+
+
+def test_served_small_requests_overtake_a_large_one(fg):
+    """A large request that does not fit the memory budget while others run
+    does not hold back the small ones queued behind it (they may overtake it),
+    and every result equals the oracle's."""
+    big = gg.rmat(16, 16, seed=9)
+    smalls = [gg.erdos_renyi(300, 6, seed=s) for s in range(40)]
+    est_big = big.n * 512 + big.nnz * 24 + (4 << 20)
+    with fg.Handle(device=0, serve_memory_budget=3 * est_big) as h:
+        reqs = []
+        for g in [big, big] + smalls:
+            raw = np.full((g.n, 16), -1, np.int64)
+            net = np.full((g.n, 16), -1, np.int64)
+            rp = np.ascontiguousarray(g.rowptr, dtype=np.int64)
+            ci = np.ascontiguousarray(g.colidx, dtype=np.int32)
+            reqs.append((g, raw, net, rp, ci, fg.fglt_stream_submit(h.h, g.n, rp, ci, raw, net)))
+        for g, raw, net, _, _, rid in reqs:
+            st, _ = fg.fglt_stream_poll(h.h, rid, 120000)
+            assert st == fg.FGLT_OK
+        for g, raw, net, _, _, _ in reqs[2:7] + reqs[-3:]:
+            oraw, onet = oracle.fglt(g)
+            np.testing.assert_array_equal(raw, oraw)
+            np.testing.assert_array_equal(net, onet)
 
 
 def test_served_bad_request_is_isolated(fg):
@@ -168,3 +197,87 @@ def test_batched_with_a_4096_vertex_member(fg, hash_factor):
             raw, net = h.transform_batched(rp, ci, batch.offsets)
             np.testing.assert_array_equal(raw.cpu().numpy(), oraw)
             np.testing.assert_array_equal(net.cpu().numpy(), onet)
+
+
+def _dev(g):
+    dev = torch.device("cuda:0")
+    return torch.from_numpy(g.rowptr).to(dev), torch.from_numpy(g.colidx if g.colidx.size else
+                                                                 np.zeros(1, np.int32)).to(dev)
+
+
+def test_fused_batch_20000_graphs_vs_oracle_and_sequence(fg):
+    """The benchmark's batch (20,000 BA and random-geometric graphs of 10..500
+    vertices) through the fused one-block-per-graph launch, element by element
+    against the oracle, then against the stage sequence (batch_small_max=-1),
+    and once more as a replay."""
+    batch = gg.small_graph_batch(20000, seed=0, n_lo=10, n_hi=500)
+    oraw, onet = oracle.fglt(batch.graph)
+    rp, ci = _dev(batch.graph)
+    with fg.Handle(device=0) as h:
+        for _ in range(2):
+            raw, net = h.transform_batched(rp, ci, batch.offsets)
+            np.testing.assert_array_equal(raw.cpu().numpy(), oraw)
+            np.testing.assert_array_equal(net.cpu().numpy(), onet)
+    with fg.Handle(device=0, batch_small_max=-1) as h:
+        raw, net = h.transform_batched(rp, ci, batch.offsets)
+        np.testing.assert_array_equal(net.cpu().numpy(), onet)
+
+
+def test_fused_batch_limits_and_special_graphs(fg):
+    """Graphs at the fused launch's size limit (512 vertices), complete graphs,
+    stars, empty and single-vertex graphs; with a 513-vertex member the batch
+    runs the stage sequence. Both against the oracle."""
+    parts = [gg.complete(1), gg.empty(3), gg.complete(40), gg.star(300), gg.erdos_renyi(512, 30, seed=2),
+             gg.barabasi_albert(512, 5, seed=4), gg.cycle(7), gg.path(2), gg.complete(64)]
+    for extra in ([], [gg.erdos_renyi(513, 8, seed=5)]):
+        batch = gg.pack_block_diagonal(parts + extra)
+        oraw, onet = oracle.fglt(batch.graph)
+        rp, ci = _dev(batch.graph)
+        with fg.Handle(device=0) as h:
+            raw, net = h.transform_batched(rp, ci, batch.offsets)
+            np.testing.assert_array_equal(raw.cpu().numpy(), oraw)
+            np.testing.assert_array_equal(net.cpu().numpy(), onet)
+
+
+def test_fused_batch_sub_dictionary(fg):
+    """A sub-dictionary through the fused launch: Sigma5, and a closed index
+    set, equal the oracle's sub-dictionary conversion."""
+    batch = gg.small_graph_batch(300, seed=3, n_lo=10, n_hi=300)
+    oraw16, _ = oracle.fglt(batch.graph)
+    rp, ci = _dev(batch.graph)
+    for mask in (fg.DICT_SIGMA5, 0b1001000000011111):
+        sraw, snet = oracle.sub_dictionary(oraw16, mask)
+        with fg.Handle(device=0, dictionary=mask) as h:
+            raw, net = h.transform_batched(rp, ci, batch.offsets)
+            np.testing.assert_array_equal(raw.cpu().numpy(), sraw)
+            np.testing.assert_array_equal(net.cpu().numpy(), snet)
+
+
+def test_fused_batch_rejects_malformed_members(fg):
+    """Without the validate option the fused launch still refuses an edge
+    joining two graphs, a self-loop, a repeated entry and an asymmetric
+    pattern; the handle then transforms a good batch."""
+    base = gg.pack_block_diagonal([gg.complete(4), gg.cycle(6)])
+    rows = np.repeat(np.arange(base.graph.n), np.diff(base.graph.rowptr))
+    cols = base.graph.colidx.astype(np.int64)
+
+    def raw_csr(r, c):  # rows as given, no symmetrisation or deduplication
+        order = np.lexsort((c, r))
+        r, c = r[order], c[order]
+        rp = np.zeros(base.graph.n + 1, np.int64)
+        np.cumsum(np.bincount(r, minlength=base.graph.n), out=rp[1:])
+        return gg.Graph(base.graph.n, rp, c.astype(np.int32))
+
+    bad = [raw_csr(np.concatenate([rows, [0, 4]]), np.concatenate([cols, [4, 0]])),  # cross edge
+           raw_csr(np.concatenate([rows, [5]]), np.concatenate([cols, [5]])),        # self-loop
+           raw_csr(np.concatenate([rows, [0]]), np.concatenate([cols, [1]])),        # repeated entry
+           raw_csr(np.concatenate([rows, [4]]), np.concatenate([cols, [6]]))]        # asymmetric
+    with fg.Handle(device=0) as h:
+        for g in bad:
+            rp, ci = _dev(g)
+            with pytest.raises(fg.FgltError) as e:
+                h.transform_batched(rp, ci, base.offsets)
+            assert e.value.status == fg.FGLT_ERR_INVALID_GRAPH
+        rp, ci = _dev(base.graph)
+        _, net = h.transform_batched(rp, ci, base.offsets)
+        np.testing.assert_array_equal(net.cpu().numpy(), oracle.fglt(base.graph)[1])

@@ -67,3 +67,21 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     with pytest.raises(fg.FgltError) as e:
         _noalloc(big)
     assert e.value.status == fg.FGLT_ERR_UNSUPPORTED
+
+
+def test_noalloc_at_both_limits_then_a_normal_call():
+    """The largest inputs the limits admit (32768 vertices with about 1.05
+    million stored entries; K_1024 with 1,047,552 entries, whose degree-order
+    out-degrees reach the largest shared-memory triangle class) fit the
+    scratch array and equal fglt_transform; a normal call after them too."""
+    import paper_2007_11111_gb300 as fg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    graphs = [gg.erdos_renyi(32768, 31.9, seed=7), gg.complete(1024), gg.rmat(12, 8, seed=3)]
+    assert graphs[0].nnz <= 1048576 and graphs[1].nnz <= 1048576
+    with fg.Handle(device=0) as h:
+        for g in graphs:
+            want_raw, want_net = _reference(h, g)
+            got_raw, got_net = _noalloc(g)
+            np.testing.assert_array_equal(got_raw, want_raw)
+            np.testing.assert_array_equal(got_net, want_net)
