@@ -107,7 +107,11 @@ struct DevBuf {  // device, grow-only
 }  // namespace
 
 struct Lane {
-  fglt_t h = nullptr;  // private handle: workspace and stream
+  fglt_t h = nullptr;  // private handle: workspace
+  // Packs holding a large request run on the high-priority stream, so that
+  // packs of small requests on the other lanes fill the SMs it leaves idle
+  // rather than slow it down; the others run on the low-priority one.
+  cudaStream_t hi = nullptr, lo = nullptr;
   std::thread th;
   HostBuf<int64_t> h_rowptr, h_raw, h_net;
   HostBuf<int32_t> h_colidx;
@@ -135,6 +139,7 @@ namespace {
 constexpr int64_t BOUNDED_MAX_GRAPH = 4096;      // packs whose graphs are all this small skip read-backs
 constexpr int64_t PACK_MAX_ENTRIES = 1LL << 22;  // a pack stops growing past this many CSR entries
 constexpr int ADMIT_LOOKAHEAD = 64;  // queued requests scanned per admission
+constexpr int64_t LARGE_REQUEST_ENTRIES = 1LL << 20;  // packs with a request this large take the high-priority stream
 constexpr int MAX_PASSED = 8;        // a request overtaken this often stops later ones from passing it
 
 // Block-diagonal packing on the device: the parts' rows and columns were
@@ -180,7 +185,9 @@ fglt_status run_pack(Server* S, Lane* L, const std::vector<Request*>& pack) {
     vo += r->n;
     eo += r->nnz;
   }
-  cudaStream_t st = handle_stream(L->h);
+  int64_t biggest = 0;
+  for (Request* r : pack) biggest = std::max(biggest, r->nnz);
+  cudaStream_t st = biggest >= LARGE_REQUEST_ENTRIES ? L->hi : L->lo;
   if (!L->d_rowptr.reserve(n + 1, st) || !L->d_colidx.reserve(std::max<int64_t>(nnz, 1), st) ||
       !L->d_raw.reserve(n * columns_of(L->h), st) || !L->d_net.reserve(n * columns_of(L->h), st) ||
       !L->d_parts.reserve(4 * (size_t)np, st))
@@ -193,9 +200,6 @@ fglt_status run_pack(Server* S, Lane* L, const std::vector<Request*>& pack) {
   if (np > 1) {
     if (cudaMemcpyAsync(L->d_parts.p, L->h_parts.p, (size_t)np * 32, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return FGLT_ERR_CUDA;
-    const int64_t biggest = std::max_element(pack.begin(), pack.end(), [](const Request* a, const Request* b) {
-                              return a->nnz < b->nnz;
-                            })[0]->nnz;
     const unsigned gx = (unsigned)std::min<int64_t>(std::max<int64_t>((biggest + 255) / 256, 1), 1024);
     k_rebase_pack<<<dim3(gx, (unsigned)np), 256, 0, st>>>(L->d_rowptr.p, L->d_colidx.p, L->d_parts.p, np);
     note_launch();
@@ -321,7 +325,14 @@ fglt_status start(fglt_t owner, Server** out) {
   lo.profile_stages = 0;
   for (int i = 0; i < NUM_LANES; ++i) {
     Lane* L = new (std::nothrow) Lane();
-    if (!L || fglt_create(&L->h, &lo, S->device) != FGLT_OK) {
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (!L || fglt_create(&L->h, &lo, S->device) != FGLT_OK ||
+        cudaStreamCreateWithPriority(&L->hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&L->lo, cudaStreamNonBlocking, prio_lo) != cudaSuccess) {
+      if (L && L->h) fglt_destroy(L->h);
+      if (L && L->hi) cudaStreamDestroy(L->hi);
+      if (L && L->lo) cudaStreamDestroy(L->lo);
       delete L;
       destroy(S);
       return FGLT_ERR_CUDA;
@@ -361,6 +372,8 @@ void destroy(Server* S) {
     L->d_parts.release();
     L->h_parts.release();
     if (L->h) fglt_destroy(L->h);
+    if (L->hi) cudaStreamDestroy(L->hi);
+    if (L->lo) cudaStreamDestroy(L->lo);
     delete L;
   }
   for (auto& kv : S->all) delete kv.second;

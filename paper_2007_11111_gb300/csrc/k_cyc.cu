@@ -402,6 +402,7 @@ __device__ __forceinline__ void build_chunk(const Segs& S, const Mids& M, int64_
     S.misc[0] = ns;
     S.misc[1] = (int)(tot & 0xFFFF);
     S.misc[2] = 0;
+    S.misc[3] = 0;
     S.pre[ns] = (int32_t)(tot >> 32);
   }
   __syncthreads();
@@ -435,17 +436,20 @@ __device__ __forceinline__ void walk_long(const Segs& S, const int32_t* __restri
   }
 }
 
-// Short segments: groups of SG lanes take them round-robin over the block's
-// groups; a group's lanes stride over one segment, two list loads in flight
-// per lane. g(u) per wedge; with SUM, done(j, s) is called by the group's
-// first lane with the group's sum s of g over segment j.
+// Short segments: groups of SG lanes take them one at a time from the
+// chunk's queue (S.misc[3]); a group's lanes stride over one segment, two
+// list loads in flight per lane. g(u) per wedge; with SUM, done(j, s) is
+// called by the group's first lane with the group's sum s of g over segment j.
 template <int SG, bool SUM, typename G, typename D>
 __device__ __forceinline__ void walk_short(const Segs& S, const int32_t* __restrict__ ocol, G g, D done) {
   const int lane = threadIdx.x & 31, gl = lane % SG;
   const unsigned gmask = (SG == 32 ? 0xffffffffu : ((1u << SG) - 1u)) << (lane & ~(SG - 1));
-  const int ngrp = blockDim.x / SG;
   const int ns = S.misc[0];
-  for (int j = threadIdx.x / SG; j < ns; j += ngrp) {
+  for (;;) {
+    int j = 0;
+    if (gl == 0) j = atomicAdd(&S.misc[3], 1);
+    j = __shfl_sync(gmask, j, lane & ~(SG - 1));
+    if (j >= ns) break;
     const int32_t* p = ocol + S.st[j];
     const int len = S.pre[j + 1] - S.pre[j];
     u64 sum = 0;
@@ -568,7 +572,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
       if (!single) {
         build_chunk(S, M, c0, n, CH, long_seg);
       } else {
-        if (tid == 0) S.misc[2] = 0;
+        if (tid == 0) S.misc[2] = S.misc[3] = 0;
         __syncthreads();
       }
       walk_long(S, ocol, credit, [&](int32_t rv, u64 sum) {
