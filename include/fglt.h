@@ -148,6 +148,12 @@ typedef struct {
      *   most 512; 0 selects 512; -1 always runs the stage sequence). Batches
      *   with a larger graph run the stage sequence. */
     int batch_small_max;
+    /* tri_pass2_from: the vertex from which the second triangle pass lists each
+     *   triangle: 1 = its lowest vertex in the degree order (like the first
+     *   pass: N+(b) scanned for every b in N+(a)), 2 = its middle vertex (the
+     *   tail of N+(a) after b scanned for every in-entry a of b: at most
+     *   sum_a binom(d+(a), 2) entries), 0 = the default, 2. */
+    int tri_pass2_from;
 } fglt_options;
 
 /* dictionary_mask of Sigma5 = {sigma_0 .. sigma_4}. */

@@ -75,6 +75,7 @@ class fglt_options(ctypes.Structure):
         ("cyc_spill_bits", ctypes.c_int),
         ("dictionary_mask", ctypes.c_uint),
         ("batch_small_max", ctypes.c_int),
+        ("tri_pass2_from", ctypes.c_int),
     ]
 
     def tuning(self) -> dict:
@@ -84,7 +85,8 @@ class fglt_options(ctypes.Structure):
                 "tri_group_lanes": self.tri_group_lanes, "tri_warp_max": self.tri_warp_max,
                 "cyc_warp_bits": self.cyc_warp_bits, "cyc_mid_threads": list(self.cyc_mid_threads),
                 "cyc_heavy_threads": self.cyc_heavy_threads, "cyc_dense_min": self.cyc_dense_min,
-                "cyc_long_segment": self.cyc_long_segment, "cyc_spill_bits": self.cyc_spill_bits}
+                "cyc_long_segment": self.cyc_long_segment, "cyc_spill_bits": self.cyc_spill_bits,
+                "tri_pass2_from": self.tri_pass2_from}
 
 
 class fglt_graph_host(ctypes.Structure):
@@ -340,7 +342,7 @@ class Handle:
                  cyc_mid_threads=(0, 0, 0), cyc_heavy_threads: int = 0, dictionary: int = 0,
                  tri_probe_loads: int = 0, tri_hash_factor: int = 0, cyc_dense_min: int = 0,
                  tri_group_lanes: int = 0, cyc_long_segment: int = 0, tri_warp_max: int = 0,
-                 cyc_spill_bits: int = 0, batch_small_max: int = 0):
+                 cyc_spill_bits: int = 0, batch_small_max: int = 0, tri_pass2_from: int = 0):
         """dictionary: sub-dictionary bit mask (0 = Sigma16; DICT_SIGMA5 = Sigma5)."""
         opt = fglt_options_default()
         opt.dictionary_mask = int(dictionary)
@@ -359,6 +361,7 @@ class Handle:
         opt.tri_warp_max = int(tri_warp_max)
         opt.cyc_spill_bits = int(cyc_spill_bits)
         opt.batch_small_max = int(batch_small_max)
+        opt.tri_pass2_from = int(tri_pass2_from)
         opt.validate = int(validate)
         opt.profile_stages = int(profile_stages)
         opt.serve_memory_budget = int(serve_memory_budget)

@@ -198,8 +198,8 @@ fglt_status time_once(fglt_t h, const Csr& g, cudaStream_t st, const Tuning& t, 
   for (int r = 0; r < reps; ++r) {
     fglt_status s = run_on_handle(h, g, nullptr, nullptr, st, nullptr, false, &t, true);
     if (s != FGLT_OK) return s;
-    float tri = h->stage_ms[5] + h->stage_ms[8];
-    float cyc = h->stage_ms[9] + h->stage_ms[10];
+    float tri = h->stage_ms[5] + h->stage_ms[9];
+    float cyc = h->stage_ms[8] + h->stage_ms[10];
     float tot = 0;
     for (int i = 0; i < NUM_STAGES; ++i) tot += h->stage_ms[i];
     best.tri = std::min(best.tri, tri);
@@ -219,11 +219,13 @@ void copy_tri(Tuning& dst, const Tuning& src) {
   dst.tri_hash_factor = src.tri_hash_factor;
   dst.tri_group = src.tri_group;
   dst.tri_warp = src.tri_warp;
+  dst.tri_pass2 = src.tri_pass2;
 }
 
 bool same_tri(const Tuning& a, const Tuning& b) {
   return a.tri_t0 == b.tri_t0 && a.tri_t1 == b.tri_t1 && a.tri_loads == b.tri_loads &&
-         a.tri_hash_factor == b.tri_hash_factor && a.tri_group == b.tri_group && a.tri_warp == b.tri_warp;
+         a.tri_hash_factor == b.tri_hash_factor && a.tri_group == b.tri_group && a.tri_warp == b.tri_warp &&
+         a.tri_pass2 == b.tri_pass2;
 }
 
 }  // namespace
@@ -247,10 +249,12 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
     if ((s = time_once(h, g, st, start, reps, &base)) != FGLT_OK) return s;
     // Candidate values per parameter, tried one parameter at a time.
     // triangle candidates: class bounds t0, t1, loads in flight, hash slots per element, group lanes,
-    // warp-per-vertex bound
-    const int t_bounds[][6] = {{128, 512, 4, 4, 32, 32}, {128, 512, 4, 4, 32, 16}, {128, 512, 4, 4, 8, 32},
-                               {64, 256, 4, 4, 32, 32},  {256, 768, 4, 4, 32, 32}, {128, 512, 2, 4, 32, 32},
-                               {128, 512, 4, 4, 16, -1}, {64, 256, 4, 4, 32, -1},  {128, 384, 4, 2, 32, 32}};
+    // warp-per-vertex bound, vertex pass 2 lists from (0 automatic, 1 lowest, 2 middle)
+    const int t_bounds[][7] = {{128, 512, 4, 4, 32, 32, 0}, {128, 512, 4, 4, 32, 16, 0}, {128, 512, 4, 4, 8, 32, 0},
+                               {64, 256, 4, 4, 32, 32, 0},  {256, 768, 4, 4, 32, 32, 0}, {128, 512, 2, 4, 32, 32, 0},
+                               {128, 512, 4, 4, 16, -1, 0}, {64, 256, 4, 4, 32, -1, 0},  {128, 384, 4, 2, 32, 32, 0},
+                               {128, 512, 4, 4, 32, 32, 1}, {128, 512, 4, 4, 32, 32, 2}, {128, 384, 4, 2, 32, 32, 1},
+                               {128, 384, 4, 2, 32, 32, 2}};
     const int wbits[] = {8, 9, 10};
     const int spans[] = {0, 16384, 32768, 65536, 90112};
     const int threads[] = {128, 256, 512, 1024};
@@ -263,6 +267,7 @@ extern "C" fglt_status fglt_autotune(fglt_t h, const void* rowptr, int rowptr_is
       t.tri_hash_factor = tb[3];
       t.tri_group = tb[4];
       t.tri_warp = tb[5] < 0 ? 0 : tb[5];
+      t.tri_pass2 = tb[6];
       if (!same_tri(t, start)) tri_c.push_back(t);
     }
     TuneScore cur = base;

@@ -66,9 +66,12 @@ cudaError_t launch_sort_rows(const int64_t* orp, int64_t n, int32_t dpmax, int64
 cudaError_t launch_worklist_outdeg(const int32_t* opc, int64_t n, int min_out, int32_t* list,
                                    int32_t* count, cudaStream_t st);
 // The same split into five lists by out-degree: [min_out, tw], (tw, t0],
-// (t0, t1], (t1, t2], (t2, ...) at lists + c * stride, sizes in counts[0..4].
+// (t0, t1], (t1, t2], (t2, ...) at lists + c * stride, sizes in counts[0..4]
+// (zeroed beforehand). With indeg, a vertex of the first list whose
+// in-degree is above promote goes to the second.
 cudaError_t launch_worklist_outdeg5(const int32_t* opc, int64_t n, int min_out, int tw, int t0, int t1, int t2,
-                                    int32_t* lists, int64_t stride, int32_t* counts, cudaStream_t st);
+                                    int32_t* lists, int64_t stride, int32_t* counts, cudaStream_t st,
+                                    const int32_t* indeg = nullptr, int promote = 0);
 
 // --- scans -----------------------------------------------------------------
 // out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
@@ -101,12 +104,16 @@ int tri_warp_max();
 cudaError_t launch_tri1_warp(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                              int* next, int32_t* C3o, u64* c3r, u64* k4r, u64* work_ctr, int* err, cudaStream_t st,
                              bool cliques, int loads);
-cudaError_t launch_tri2_warp(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
-                             int* next, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st, int loads);
-// d^13 (diamond, off-cord) per vertex from the final C3.
-cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
-                        int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st,
-                        int loads = 2, int hf = 2, int group = 32);
+cudaError_t launch_tri2_warp(const int64_t* orp, const int32_t* ocol, const int64_t* irp, const int2* iin,
+                             const int32_t* work, const int32_t* nwork, int* next, const int32_t* C3o, u64* r13r,
+                             int* err, cudaStream_t st, int loads, bool middle);
+// d^13 (diamond, off-cord) per vertex from the final C3, listing each
+// triangle from its middle vertex b (middle = true; work = the b of one
+// out-degree class; irp/iin = in-lists, see launch_in_lists) or from its
+// lowest vertex a like pass 1 (middle = false; irp/iin unused).
+cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int64_t* irp, const int2* iin,
+                        const int32_t* work, const int32_t* nwork, int* next, int dpmax, const int32_t* C3o,
+                        u64* r13r, int* err, cudaStream_t st, int loads, int hf, int group, bool middle);
 // d^10 = C3 (p1 - 2) and d^14 = D4,3 e / 2 from the final C3 (rank space).
 cudaError_t launch_c3_edge_terms(const int64_t* orp, const int32_t* ocol, const int32_t* C3o,
                                  const int32_t* dr, int64_t n, u64* r10r, u64* r14r, cudaStream_t st);

@@ -7,8 +7,8 @@
 //   tri1              C3 = A o A^2 per edge, c3, 4-cliques T     (Lemma 2, Sec. 4.3)
 //   c3_edges          d^10 = C3 (p1 - 2), d^14 = D4,3 e / 2      (Sec. 4.2, 4.3)
 //   spmv2             p3 = A p2 - p1 o (p1-1) - 2 c3, d^9        (Sec. 4.1, 4.2)
+//   wedges            in-lists, wedge counts of the 4-cycle stage
 //   tri2              d^13 = D4,c e / 2                          (Sec. 4.3)
-//   wedges            in-lists and wedge counts of the 4-cycle stage
 //   cyc               c4 = C4,2 e / 2                            (Lemma on c4)
 //   epilogue          Table I, then f = U16^{-1} f^              (Table II)
 #include "fglt_pipeline.h"
@@ -24,7 +24,7 @@
 namespace fglt {
 
 const char* const STAGE_NAMES[NUM_STAGES] = {"degree", "spmv1", "rank", "orient", "sort", "tri1", "c3_edges",
-                                             "spmv2", "tri2", "wedges", "cyc", "epilogue"};
+                                             "spmv2", "wedges", "tri2", "cyc", "epilogue"};
 const char* const SUB_NAMES[NUM_SUB] = {"cyc.warp",   "cyc.hash11", "cyc.hash12", "cyc.hash13", "cyc.dense",
                                         "cyc.dense_spill", "cyc.global", "tri1.w", "tri1.c0",  "tri1.c1",
                                         "tri1.c2",    "tri1.c3",    "tri2.w",     "tri2.c0",    "tri2.c1",
@@ -33,6 +33,7 @@ const char* const SUB_NAMES[NUM_SUB] = {"cyc.warp",   "cyc.hash11", "cyc.hash12"
 namespace {
 
 constexpr int64_t MAX_DEGREE_EXACT = 2097151;  // binom(d,3) products stay inside int64
+constexpr int TRI2_WARP_IN = 256;  // pass 2 from the middle vertex: in-entries one warp takes at most
 
 // Small device counters, one int slot each.
 enum CounterId {
@@ -146,6 +147,8 @@ fglt_status tuning_from_options(const fglt_options& o, Tuning* t) {
   if (x.cyc_dense_min < 0 || x.cyc_dense_min > 4096) return FGLT_ERR_INVALID_ARG;
   if (o.cyc_heavy_threads) x.cyc_heavy_threads = o.cyc_heavy_threads;
   if (!pow2_threads(x.cyc_heavy_threads)) return FGLT_ERR_INVALID_ARG;
+  if (o.tri_pass2_from < 0 || o.tri_pass2_from > 2) return FGLT_ERR_INVALID_ARG;
+  x.tri_pass2 = o.tri_pass2_from;
   *t = x;
   return FGLT_OK;
 }
@@ -164,6 +167,7 @@ void tuning_to_options(const Tuning& t, fglt_options* o) {
   o->cyc_dense_min = t.cyc_dense_min;
   o->cyc_long_segment = t.cyc_long_segment;
   o->cyc_spill_bits = t.cyc_spill_bits;
+  o->tri_pass2_from = t.tri_pass2;
 }
 
 fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t* out_net, cudaStream_t st,
@@ -340,11 +344,13 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   const int TW = std::min(tu.tri_warp, tri_warp_max());
   int32_t* twork;
   NEED(B_TWORK, (int64_t)TRI_CLASSES * n, twork);
-  CK(launch_worklist_outdeg5(opc, n, 2, std::max(TW, 1), T0, T1, T2, twork, n, cnt + C_NTRI0, st));
+  // Out-degree 1 is kept: pass 2 lists a triangle from its middle vertex,
+  // which needs one out-neighbour only.
+  CK(launch_worklist_outdeg5(opc, n, 1, TW, T0, T1, T2, twork, n, cnt + C_NTRI0, st));
   const int tri_cap[TRI_CLASSES] = {std::min(dpmax, TW), std::min(dpmax, T0), std::min(dpmax, T1),
                                     std::min(dpmax, T2), dpmax};
-  const bool tri_on[TRI_CLASSES] = {TW >= 2 && dpmax >= 2, dpmax > std::max(TW, 1) && T0 > TW, dpmax > T0,
-                                    dpmax > T1, dpmax > T2};
+  const bool tri_on[TRI_CLASSES] = {TW >= 1 && dpmax >= 1, dpmax > TW && T0 > TW, dpmax > T0, dpmax > T1,
+                                    dpmax > T2};
 
   // Triangle pass 1: C3, c3, 4-cliques.
   mark(5);
@@ -414,37 +420,20 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
     CK(cudaMemsetAsync(r9, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(int64_t), st));
   }
 
-  // Triangle pass 2: diamonds at the off-cord vertices.
+  // In-lists of the oriented graph: pass 2 lists each triangle from its
+  // middle vertex, and the 4-cycle stage walks the middles of each vertex.
+  // The same pass counts the 4-cycle stage's wedges.
   mark(8);
-  u64* r13r;
-  NEED(B_R13R, n, r13r);
-  CK(cudaMemsetAsync(r13r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
-  for (int c = 0; c < TRI_CLASSES; ++c)
-    if (tri_on[c] && need_tri2) {
-      sub(CYC_CLASSES + TRI_CLASSES + c, 0);
-      if (c == 0)
-        CK(launch_tri2_warp(orp, ocol, twork, cnt + C_NTRI0, cnt + C_NEXT2_0, C3o, r13r, err, st, tu.tri_loads));
-      else
-        CK(launch_tri2(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT2_0 + c, tri_cap[c], C3o, r13r, err,
-                       st, tu.tri_loads, tri_hf[c], tu.tri_group));
-      sub(CYC_CLASSES + TRI_CLASSES + c, 1);
-    }
-
-  // 4-cycles: in-lists and wedge counts, vertex classes, then the class kernels.
-  mark(9);
-  u64* r12r;
-  NEED(B_R12R, n, r12r);
-  CK(cudaMemsetAsync(r12r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
-  if (!need_cyc) mark(10);
-  if (need_cyc) {
-    // Dense window of top ranks: 32768 by default, 65536 for graphs above
-    // 2^21 vertices (their wedge tops spread over more hubs).
-    int64_t span = tu.cyc_hub_span > 0 ? tu.cyc_hub_span : (n > (1 << 22) ? 65536 : 32768);
-    const int32_t hub_lo = (int32_t)std::max<int64_t>(0, n - span);
-    const int spill_bits = cyc_fit_spill_bits((int)std::min<int64_t>(span, n), tu.cyc_spill_bits, tu.cyc_heavy_threads);
-    int64_t *wc, *wcn, *irp;
-    int32_t *hc, *indeg, *icur;
-    int2* iin;
+  // Dense window of top ranks: 32768 by default, 65536 for graphs above
+  // 2^21 vertices (their wedge tops spread over more hubs).
+  const int64_t span = tu.cyc_hub_span > 0 ? tu.cyc_hub_span : (n > (1 << 22) ? 65536 : 32768);
+  const int32_t hub_lo = (int32_t)std::max<int64_t>(0, n - span);
+  int64_t *wc = nullptr, *wcn = nullptr, *irp = nullptr;
+  int32_t *hc, *indeg, *icur;
+  int2* iin = nullptr;
+  // Pass 2 from the middle vertex unless the lowest is requested.
+  const bool tri2_mid = tu.tri_pass2 != 1;
+  if ((need_tri2 && tri2_mid) || need_cyc) {
     NEED(B_WC, n, wc);
     NEED(B_WCN, n, wcn);
     NEED(B_HC, n, hc);
@@ -457,6 +446,45 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
     CK(cudaMemsetAsync(icur, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(int32_t), st));
     CK(cudaMemsetAsync(iin, 0xFF, (size_t)std::max<int64_t>(m_or, 1) * sizeof(int2), st));
     CK(launch_in_lists(orp, ocol, dr, opc, n, hub_lo, hc, indeg, irp, scan_tmp, icur, iin, wc, wcn, st));
+  }
+
+  // Triangle pass 2: diamonds at the off-cord vertices.
+  mark(9);
+  u64* r13r;
+  NEED(B_R13R, n, r13r);
+  CK(cudaMemsetAsync(r13r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
+  if (need_tri2 && tri2_mid) {
+    // Listed from the middle vertex, a vertex's work grows with its
+    // in-degree: the out-degree classes are rebuilt (pass 1 is done with
+    // them) with every vertex of more than TRI2_WARP_IN in-entries moved from
+    // the warp class to the first block class.
+    // (only where the first block class can hold a warp-class vertex)
+    CK(cudaMemsetAsync(cnt + C_NTRI0, 0, TRI_CLASSES * sizeof(int32_t), st));
+    CK(launch_worklist_outdeg5(opc, n, 1, TW, T0, T1, T2, twork, n, cnt + C_NTRI0, st, indeg,
+                               T0 >= TW ? TRI2_WARP_IN : 0x7fffffff));
+  }
+  bool tri2_on[TRI_CLASSES];
+  for (int c = 0; c < TRI_CLASSES; ++c) tri2_on[c] = tri_on[c];
+  if (tri2_mid && T0 >= TW && TW >= 1 && dpmax >= 1) tri2_on[1] = true;  // may hold promoted vertices
+  for (int c = 0; c < TRI_CLASSES; ++c)
+    if (tri2_on[c] && need_tri2) {
+      sub(CYC_CLASSES + TRI_CLASSES + c, 0);
+      if (c == 0)
+        CK(launch_tri2_warp(orp, ocol, irp, iin, twork, cnt + C_NTRI0, cnt + C_NEXT2_0, C3o, r13r, err, st,
+                            tu.tri_loads, tri2_mid));
+      else
+        CK(launch_tri2(orp, ocol, irp, iin, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT2_0 + c, tri_cap[c], C3o,
+                       r13r, err, st, tu.tri_loads, tri_hf[c], tu.tri_group, tri2_mid));
+      sub(CYC_CLASSES + TRI_CLASSES + c, 1);
+    }
+
+  // 4-cycles: vertex classes, then the class kernels.
+  mark(10);
+  u64* r12r;
+  NEED(B_R12R, n, r12r);
+  CK(cudaMemsetAsync(r12r, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(u64), st));
+  if (need_cyc) {
+    const int spill_bits = cyc_fit_spill_bits((int)std::min<int64_t>(span, n), tu.cyc_spill_bits, tu.cyc_heavy_threads);
     int32_t* lists;
     NEED(B_LS, (int64_t)CYC_CLASSES * n, lists);
     const int64_t cap_bound = b ? std::min<int64_t>(b->cap, n) : n;
@@ -478,7 +506,6 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
       n_gmem = ng[0] + ng[1];
       READ(ctr + W_GCAP, &gcap);
     }
-    mark(10);
     {
       CycArgs ca{};
       ca.n = n;

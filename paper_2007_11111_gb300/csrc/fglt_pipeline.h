@@ -55,6 +55,7 @@ struct Tuning {
   int cyc_dense_min = 2048;
   int cyc_long_segment = 32;
   int cyc_spill_bits = 11;
+  int tri_pass2 = 0;  // 0 automatic, 1 lowest vertex, 2 middle vertex
 };
 
 // Fills t from the options (0 fields keep the defaults) and checks ranges.

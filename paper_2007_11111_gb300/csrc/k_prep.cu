@@ -458,13 +458,15 @@ __global__ void k_worklist_outdeg(const int32_t* __restrict__ opc, int64_t n, in
 
 // Five lists by out-degree: [min_out, tw], (tw, t0], (t0, t1], (t1, t2], (t2, ...).
 __global__ void k_worklist_outdeg5(const int32_t* __restrict__ opc, int64_t n, int min_out, int tw, int t0, int t1,
-                                   int t2, int32_t* lists, int64_t stride, int32_t* counts) {
+                                   int t2, int32_t* lists, int64_t stride, int32_t* counts,
+                                   const int32_t* __restrict__ indeg, int promote) {
   const int lane = threadIdx.x & 31;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < n; r0 += step) {
     const int64_t r = r0 + lane;
     const int d = r < n ? opc[r] : 0;
-    const int cls = d < min_out ? -1 : (d <= tw ? 0 : (d <= t0 ? 1 : (d <= t1 ? 2 : (d <= t2 ? 3 : 4))));
+    int cls = d < min_out ? -1 : (d <= tw ? 0 : (d <= t0 ? 1 : (d <= t1 ? 2 : (d <= t2 ? 3 : 4))));
+    if (cls == 0 && indeg && r < n && indeg[r] > promote) cls = 1;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       const unsigned m = __ballot_sync(0xffffffffu, cls == c);
@@ -806,9 +808,11 @@ cudaError_t launch_worklist_outdeg(const int32_t* opc, int64_t n, int min_out, i
 }
 
 cudaError_t launch_worklist_outdeg5(const int32_t* opc, int64_t n, int min_out, int tw, int t0, int t1, int t2,
-                                    int32_t* lists, int64_t stride, int32_t* counts, cudaStream_t st) {
+                                    int32_t* lists, int64_t stride, int32_t* counts, cudaStream_t st,
+                                    const int32_t* indeg, int promote) {
   if (n <= 0) return cudaSuccess;
-  k_worklist_outdeg5<<<grid_for(n, 256), 256, 0, st>>>(opc, n, min_out, tw, t0, t1, t2, lists, stride, counts);
+  k_worklist_outdeg5<<<grid_for(n, 256), 256, 0, st>>>(opc, n, min_out, tw, t0, t1, t2, lists, stride, counts,
+                                                       indeg, promote);
   note_launch();
   return cudaGetLastError();
 }

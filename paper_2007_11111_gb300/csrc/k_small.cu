@@ -9,8 +9,8 @@
 //   1. the bitmap, the degrees, and checks of the structure the kernel relies
 //      on (every neighbour inside its graph, no self-loop, no repeated entry,
 //      a symmetric pattern; a violation sets ERR_BAD_GRAPH);
-//   2. one warp per vertex i: the row P2(i, .) = sum_{k in N(i)} A(k, .) by
-//      column counts (lane l counts bit l of the neighbours' rows), giving
+//   2. one warp per vertex i: the row P2(i, .) = sum_{k in N(i)} A(k, .) by a
+//      walk over the neighbours' rows (each set bit adds one), giving
 //        c4(i)   = sum_{l != i} binom(P2(i,l), 2)            (Lemma on c4)
 //        C3(i,j) = P2(i,j) on the edges, c3(i) = sum_j C3(i,j) / 2 (Lemma 2)
 //        d^7, d^10, d^14, p2 as sums over the edges of i    (Sec. 3.1-4.3)

@@ -13,8 +13,9 @@
 //   d^15(i) = 4-cliques at i = T e / 6, T(i,j) = q_ij^T A q_ij (Sec. 4.3):
 //             the 4-cliques {a, x, y, z} with a lowest are the triangles
 //             {x, y, z} of G_a, counted per vertex by popcounts of row ANDs.
-// Pass 2 re-lists the triangles once C3 is final and adds, for a triangle
-// {i,j,k}, C3(j,k) - 1 to i (and likewise for j and k):
+// Pass 2 re-lists the triangles once C3 is final, from their middle vertex
+// (in-lists of the oriented graph), and adds, for a triangle {i,j,k},
+// C3(j,k) - 1 to i (and likewise for j and k):
 //   d^13 = D4,c e / 2 with D4,c = A o (A (C3 - A))       (Sec. 4.3)
 #include "fglt_device.cuh"
 #include "fglt_kernels.h"
@@ -425,10 +426,301 @@ __global__ void __launch_bounds__(BT)
 }
 
 // ---------------------------------------------------------------------------
-// Pass 2
+// Pass 2, listed from the middle vertex: a block takes a vertex b and holds
+// N+(b) in a shared hash table, with C3(b, c) beside each entry. For every
+// in-entry (a, j) of b (b = N+(a)[j], so C3(a, b) = C3o[orp[a] + j]) a lane
+// group scans the tail of N+(a) after position j up to max N+(b); a hit c
+// closes the triangle {a, b, c} with a < b < c, found once. Its three
+// corners gain the opposite edge's C3 - 1: a gains C3(b, c) - 1 (summed per
+// scan), b gains C3(a, c) - 1 (C3o at the scanned position, summed per
+// block), c gains C3(a, b) - 1 (shared tally per entry of N+(b)). The scans
+// cover sum_a binom(d+(a), 2) entries at most, against the per-a listing of
+// pass 1, which scans N+(b) for every b in N+(a).
 // ---------------------------------------------------------------------------
 template <int PL, int BT, int G>
 __global__ void __launch_bounds__(BT) k_tri2(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                                const int64_t* __restrict__ irp, const int2* __restrict__ iin,
+                                                const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
+                                                int* next, int Dmax, int Hbits, int hf,
+                                                const int32_t* __restrict__ C3o, u64* r13r, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  __shared__ u64 red[32];
+  const int Hmax = 1 << Hbits;
+  u64* acc = reinterpret_cast<u64*>(smem);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(acc + Dmax);
+  int32_t* vals = reinterpret_cast<int32_t*>(keys + Hmax);
+  int32_t* tv = vals + Hmax;
+  uint32_t* filt = reinterpret_cast<uint32_t*>(tv + Dmax);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int total = *nwork;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    const int b = work[total - 1 - item];  // lists run in rising rank: the largest vertices first
+    const int64_t base = orp[b];
+    const int D = (int)(orp[b + 1] - base);
+    int hb = 5;
+    while ((1 << hb) < hf * D) ++hb;
+    const int fb = filter_bits_for(D);
+
+    for (int i = tid; i < (1 << hb); i += blockDim.x) keys[i] = EMPTY_KEY;
+    for (int i = tid; i < (1 << (fb - 5)); i += blockDim.x) filt[i] = 0u;
+    for (int i = tid; i < D; i += blockDim.x) { acc[i] = 0; tv[i] = C3o[base + i]; }
+    __syncthreads();
+    for (int x = tid; x < D; x += blockDim.x) {
+      const uint32_t key = (uint32_t)ocol[base + x];
+      table_insert(keys, vals, key, x, hb, err);
+      filter_set(filt, key, fb);
+    }
+    __syncthreads();
+
+    const int32_t lastB = ocol[base + D - 1];
+    const int64_t ib0 = irp[b], nin = irp[b + 1] - ib0;
+    long long acc_b = 0;
+    const Groups<G> grp(warp, nwarps, lane);
+    for (int64_t e = grp.first; e < nin; e += grp.stride) {
+      const int2 ent = __ldg(iin + ib0 + e);
+      const int32_t a = ent.x;
+      if (a < 0) continue;  // never-written slot (malformed graph only)
+      const int64_t ab = orp[a], ae = orp[a + 1];
+      const long long tab = C3o[ab + ent.y];  // C3(a, b)
+      long long acca = 0;
+      auto probe = [&](int32_t c, int64_t k) {
+        if (c <= lastB && filter_test(filt, (uint32_t)c, fb)) {
+          const int32_t c3ac = C3o[k];  // issued before the table probe so that the two overlap
+          const int ic = table_find(keys, vals, (uint32_t)c, hb);
+          if (ic >= 0) {
+            acca += (long long)tv[ic] - 1;   // a: opposite edge b-c
+            acc_b += (long long)c3ac - 1;    // b: opposite edge a-c
+            if (tab > 1) atomicAdd(&acc[ic], (u64)(tab - 1));  // c: opposite edge a-b
+          }
+        }
+      };
+      scan_sorted<PL, G>(ocol, ab + ent.y + 1, ae, lastB, grp.gl, grp.mask, probe);
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acca += __shfl_xor_sync(grp.mask, acca, o, G);
+      if (grp.gl == 0 && acca) atomicAdd(&r13r[a], (u64)acca);
+    }
+    __syncthreads();
+    for (int x = tid; x < D; x += blockDim.x)
+      if (acc[x]) atomicAdd(&r13r[ocol[base + x]], acc[x]);
+    const u64 sb = block_sum((u64)acc_b, red);
+    if (tid == 0 && sb) atomicAdd(&r13r[b], sb);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small out-degree (|N+(a)| <= 32): one warp per vertex a, no block barriers.
+// Each bitmap row of G_a is one word, so the 4-clique tallies are per-lane
+// popcounts. Per warp: a 128-slot hash table of N+(a) (at most 4 slots per
+// element), a 512-bit filter, the bitmap rows and the tallies.
+// ---------------------------------------------------------------------------
+constexpr int TW_MAX = 32;      // largest out-degree of the warp class
+constexpr int TW_HBITS = 7;     // 128 slots
+constexpr int TW_FBITS = 9;     // 512-bit filter
+constexpr int TW_T = 256;       // 8 warps per block
+struct WarpTri {                // per-warp shared memory
+  uint32_t keys[1 << TW_HBITS];
+  int32_t vals[1 << TW_HBITS];
+  uint32_t filt[(1 << TW_FBITS) / 32];
+  uint32_t S[TW_MAX];
+  uint32_t k2[TW_MAX];
+  u64 acc[TW_MAX];
+  int32_t tv[TW_MAX];
+};
+
+// Loads N+(a) into the warp's table and filter; returns the lane's element
+// (or 0x7fffffff past D) and sets *D, *base.
+__device__ __forceinline__ int32_t warp_load_out(WarpTri& w, const int64_t* __restrict__ orp,
+                                                 const int32_t* __restrict__ ocol, int32_t a, int lane, int* D,
+                                                 int64_t* base, int* hb, int* err) {
+  *base = orp[a];
+  *D = (int)(orp[a + 1] - *base);
+  if (*D > TW_MAX || *D < 1) {  // outside the class (a sizing bug): flag it, skip the vertex
+    if (lane == 0) atomicOr(err, ERR_INTERNAL);
+    *D = 0;
+    return 0x7fffffff;
+  }
+  int b = 5;
+  while ((1 << b) < 4 * *D) ++b;
+  *hb = b;
+  for (int i = lane; i < (1 << b); i += 32) w.keys[i] = EMPTY_KEY;
+  if (lane < (1 << TW_FBITS) / 32) w.filt[lane] = 0u;
+  __syncwarp();
+  const int32_t x = lane < *D ? ocol[*base + lane] : 0x7fffffff;
+  if (lane < *D) {
+    table_insert(w.keys, w.vals, (uint32_t)x, lane, b, err);
+    filter_set(w.filt, (uint32_t)x, TW_FBITS);
+  }
+  __syncwarp();
+  return x;
+}
+
+template <int PL, bool K4>
+__global__ void __launch_bounds__(TW_T) k_tri1_warp(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                                    const int32_t* __restrict__ work,
+                                                    const int32_t* __restrict__ nwork, int* next, int32_t* C3o,
+                                                    u64* c3r, u64* k4r, u64* work_ctr, int* err) {
+  __shared__ WarpTri sw[TW_T / 32];
+  const int lane = threadIdx.x & 31;
+  WarpTri& w = sw[threadIdx.x >> 5];
+  const int total = *nwork;
+  u64 probes = 0, tri_total = 0, k4_total = 0;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(next, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    const int32_t a = work[total - 1 - item];  // the largest vertices first
+    int D, hb;
+    int64_t base;
+    const int32_t x = warp_load_out(w, orp, ocol, a, lane, &D, &base, &hb, err);
+    if (D < 2) continue;  // a single out-neighbour closes no triangle with a lowest
+    w.S[lane] = 0u;
+    w.k2[lane] = 0u;
+    __syncwarp();
+    const int32_t lastA = __shfl_sync(0xffffffffu, x, D - 1);
+    for (int ib = 0; ib < D; ++ib) {
+      const int32_t b = __shfl_sync(0xffffffffu, x, ib);
+      const int64_t bb = orp[b], be = orp[b + 1];
+      auto probe = [&](int32_t c, int64_t k) {
+        if (c <= lastA) {
+          ++probes;
+          if (filter_test(w.filt, (uint32_t)c, TW_FBITS)) {
+            const int ic = table_find(w.keys, w.vals, (uint32_t)c, hb);
+            if (ic >= 0) {
+              atomicOr(&w.S[ib], 1u << ic);
+              atomicOr(&w.S[ic], 1u << ib);
+              atomicAdd(&C3o[k], 1);  // edge b -> c
+            }
+          }
+        }
+      };
+      scan_sorted<PL, 32>(ocol, bb, be, lastA, lane, 0xffffffffu, probe);
+    }
+    __syncwarp();
+    const uint32_t Sx = lane < D ? w.S[lane] : 0u;
+    const int deg = __popc(Sx);
+    if (deg) {
+      atomicAdd(&C3o[base + lane], deg);
+      atomicAdd(&c3r[x], (u64)deg);
+    }
+    const u64 tri_a = (u64)warp_sum_i32(deg) / 2;
+    if (K4) {
+      // per edge x-y of G_a with y > x: t = |S_x ∩ S_y|, added to both ends
+      uint32_t up = lane < 31 ? (Sx & ~((2u << lane) - 1u)) : 0u;
+      uint32_t kx = 0;
+      while (up) {
+        const int y = __ffs(up) - 1;
+        up &= up - 1;
+        const uint32_t t = __popc(Sx & w.S[y]);
+        if (t) {
+          atomicAdd(&w.k2[y], t);
+          kx += t;
+        }
+      }
+      if (kx) atomicAdd(&w.k2[lane], kx);
+      __syncwarp();
+      const uint32_t k2 = lane < D ? w.k2[lane] : 0u;
+      if (k2) atomicAdd(&k4r[x], (u64)(k2 / 2));
+      const u64 k4_a = (u64)warp_sum_i32((int)k2) / 6;
+      if (lane == 0 && k4_a) atomicAdd(&k4r[a], k4_a);
+      k4_total += k4_a;
+    }
+    if (lane == 0 && tri_a) atomicAdd(&c3r[a], tri_a);
+    tri_total += tri_a;
+    __syncwarp();
+  }
+  probes = warp_sum_u64(probes);
+  if (lane == 0) {
+    if (probes) atomicAdd(&work_ctr[0], probes);
+    if (tri_total) atomicAdd(&work_ctr[1], tri_total);
+    if (k4_total) atomicAdd(&work_ctr[2], k4_total);
+  }
+}
+
+// Pass 2 for out-degrees up to 32, from the middle vertex (see k_tri2): one
+// warp per b, groups of 8 lanes per in-entry of b.
+template <int PL>
+__global__ void __launch_bounds__(TW_T) k_tri2_warp(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+                                                    const int64_t* __restrict__ irp, const int2* __restrict__ iin,
+                                                    const int32_t* __restrict__ work,
+                                                    const int32_t* __restrict__ nwork, int* next,
+                                                    const int32_t* __restrict__ C3o, u64* r13r, int* err) {
+  constexpr int G = 8;
+  __shared__ WarpTri sw[TW_T / 32];
+  const int lane = threadIdx.x & 31;
+  WarpTri& w = sw[threadIdx.x >> 5];
+  const int total = *nwork;
+  const Groups<G> grp(0, 1, lane);
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(next, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    const int32_t b = work[total - 1 - item];  // the largest vertices first
+    int D, hb;
+    int64_t base;
+    const int32_t x = warp_load_out(w, orp, ocol, b, lane, &D, &base, &hb, err);
+    if (D == 0) continue;
+    w.acc[lane] = 0;
+    w.tv[lane] = lane < D ? C3o[base + lane] : 0;
+    __syncwarp();
+    const int32_t lastB = __shfl_sync(0xffffffffu, x, D - 1);
+    const int64_t ib0 = irp[b], nin = irp[b + 1] - ib0;
+    long long acc_b = 0;
+    for (int64_t e0 = 0; e0 < nin; e0 += 32 / G) {
+      const int64_t e = e0 + grp.first;
+      int32_t a = -1;
+      int64_t ab = 0, ae = 0;
+      long long tab = 0;
+      if (e < nin) {
+        const int2 ent = __ldg(iin + ib0 + e);
+        a = ent.x;
+        if (a >= 0) {
+          ab = orp[a] + ent.y + 1;
+          ae = orp[a + 1];
+          tab = C3o[ab - 1];  // C3(a, b)
+        }
+      }
+      long long acca = 0;
+      auto probe = [&](int32_t c, int64_t k) {
+        if (c <= lastB && filter_test(w.filt, (uint32_t)c, TW_FBITS)) {
+          const int32_t c3ac = C3o[k];  // issued before the table probe so that the two overlap
+          const int ic = table_find(w.keys, w.vals, (uint32_t)c, hb);
+          if (ic >= 0) {
+            acca += (long long)w.tv[ic] - 1;  // a: opposite edge b-c
+            acc_b += (long long)c3ac - 1;     // b: opposite edge a-c
+            if (tab > 1) atomicAdd(&w.acc[ic], (u64)(tab - 1));  // c: opposite edge a-b
+          }
+        }
+      };
+      scan_sorted<PL, G>(ocol, ab, ae, lastB, grp.gl, grp.mask, probe);
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acca += __shfl_xor_sync(grp.mask, acca, o, G);
+      if (grp.gl == 0 && acca) atomicAdd(&r13r[a], (u64)acca);
+    }
+    __syncwarp();
+    if (lane < D && w.acc[lane]) atomicAdd(&r13r[x], w.acc[lane]);
+    const u64 sb = (u64)warp_sum_i64(acc_b);
+    if (lane == 0 && sb) atomicAdd(&r13r[b], sb);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2, listed from the lowest vertex a like pass 1 (the scans of N+(b) for
+// every b in N+(a)); on graphs whose out-lists mostly stay in L2 this costs
+// less than the listing from the middle vertex, whose scans are shorter but
+// each needs an in-entry and two row pointers.
+// ---------------------------------------------------------------------------
+template <int PL, int BT, int G>
+__global__ void __launch_bounds__(BT) k_tri2_low(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
                                                 const int32_t* __restrict__ work, const int32_t* __restrict__ nwork,
                                                 int* next, int Dmax, int Hbits, int hf,
                                                 const int32_t* __restrict__ C3o,
@@ -501,138 +793,9 @@ __global__ void __launch_bounds__(BT) k_tri2(const int64_t* __restrict__ orp, co
   }
 }
 
-// ---------------------------------------------------------------------------
-// Small out-degree (|N+(a)| <= 32): one warp per vertex a, no block barriers.
-// Each bitmap row of G_a is one word, so the 4-clique tallies are per-lane
-// popcounts. Per warp: a 128-slot hash table of N+(a) (at most 4 slots per
-// element), a 512-bit filter, the bitmap rows and the tallies.
-// ---------------------------------------------------------------------------
-constexpr int TW_MAX = 32;      // largest out-degree of the warp class
-constexpr int TW_HBITS = 7;     // 128 slots
-constexpr int TW_FBITS = 9;     // 512-bit filter
-constexpr int TW_T = 256;       // 8 warps per block
-struct WarpTri {                // per-warp shared memory
-  uint32_t keys[1 << TW_HBITS];
-  int32_t vals[1 << TW_HBITS];
-  uint32_t filt[(1 << TW_FBITS) / 32];
-  uint32_t S[TW_MAX];
-  uint32_t k2[TW_MAX];
-  u64 acc[TW_MAX];
-  int32_t tv[TW_MAX];
-};
-
-// Loads N+(a) into the warp's table and filter; returns the lane's element
-// (or 0x7fffffff past D) and sets *D, *base.
-__device__ __forceinline__ int32_t warp_load_out(WarpTri& w, const int64_t* __restrict__ orp,
-                                                 const int32_t* __restrict__ ocol, int32_t a, int lane, int* D,
-                                                 int64_t* base, int* hb, int* err) {
-  *base = orp[a];
-  *D = (int)(orp[a + 1] - *base);
-  if (*D > TW_MAX || *D < 2) {  // outside the class (a sizing bug): flag it, skip the vertex
-    if (lane == 0) atomicOr(err, ERR_INTERNAL);
-    *D = 0;
-    return 0x7fffffff;
-  }
-  int b = 5;
-  while ((1 << b) < 4 * *D) ++b;
-  *hb = b;
-  for (int i = lane; i < (1 << b); i += 32) w.keys[i] = EMPTY_KEY;
-  if (lane < (1 << TW_FBITS) / 32) w.filt[lane] = 0u;
-  __syncwarp();
-  const int32_t x = lane < *D ? ocol[*base + lane] : 0x7fffffff;
-  if (lane < *D) {
-    table_insert(w.keys, w.vals, (uint32_t)x, lane, b, err);
-    filter_set(w.filt, (uint32_t)x, TW_FBITS);
-  }
-  __syncwarp();
-  return x;
-}
-
-template <int PL, bool K4>
-__global__ void __launch_bounds__(TW_T) k_tri1_warp(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
-                                                    const int32_t* __restrict__ work,
-                                                    const int32_t* __restrict__ nwork, int* next, int32_t* C3o,
-                                                    u64* c3r, u64* k4r, u64* work_ctr, int* err) {
-  __shared__ WarpTri sw[TW_T / 32];
-  const int lane = threadIdx.x & 31;
-  WarpTri& w = sw[threadIdx.x >> 5];
-  const int total = *nwork;
-  u64 probes = 0, tri_total = 0, k4_total = 0;
-  for (;;) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(next, 1);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= total) break;
-    const int32_t a = work[total - 1 - item];  // the largest vertices first
-    int D, hb;
-    int64_t base;
-    const int32_t x = warp_load_out(w, orp, ocol, a, lane, &D, &base, &hb, err);
-    if (D == 0) continue;
-    w.S[lane] = 0u;
-    w.k2[lane] = 0u;
-    __syncwarp();
-    const int32_t lastA = __shfl_sync(0xffffffffu, x, D - 1);
-    for (int ib = 0; ib < D; ++ib) {
-      const int32_t b = __shfl_sync(0xffffffffu, x, ib);
-      const int64_t bb = orp[b], be = orp[b + 1];
-      auto probe = [&](int32_t c, int64_t k) {
-        if (c <= lastA) {
-          ++probes;
-          if (filter_test(w.filt, (uint32_t)c, TW_FBITS)) {
-            const int ic = table_find(w.keys, w.vals, (uint32_t)c, hb);
-            if (ic >= 0) {
-              atomicOr(&w.S[ib], 1u << ic);
-              atomicOr(&w.S[ic], 1u << ib);
-              atomicAdd(&C3o[k], 1);  // edge b -> c
-            }
-          }
-        }
-      };
-      scan_sorted<PL, 32>(ocol, bb, be, lastA, lane, 0xffffffffu, probe);
-    }
-    __syncwarp();
-    const uint32_t Sx = lane < D ? w.S[lane] : 0u;
-    const int deg = __popc(Sx);
-    if (deg) {
-      atomicAdd(&C3o[base + lane], deg);
-      atomicAdd(&c3r[x], (u64)deg);
-    }
-    const u64 tri_a = (u64)warp_sum_i32(deg) / 2;
-    if (K4) {
-      // per edge x-y of G_a with y > x: t = |S_x ∩ S_y|, added to both ends
-      uint32_t up = lane < 31 ? (Sx & ~((2u << lane) - 1u)) : 0u;
-      uint32_t kx = 0;
-      while (up) {
-        const int y = __ffs(up) - 1;
-        up &= up - 1;
-        const uint32_t t = __popc(Sx & w.S[y]);
-        if (t) {
-          atomicAdd(&w.k2[y], t);
-          kx += t;
-        }
-      }
-      if (kx) atomicAdd(&w.k2[lane], kx);
-      __syncwarp();
-      const uint32_t k2 = lane < D ? w.k2[lane] : 0u;
-      if (k2) atomicAdd(&k4r[x], (u64)(k2 / 2));
-      const u64 k4_a = (u64)warp_sum_i32((int)k2) / 6;
-      if (lane == 0 && k4_a) atomicAdd(&k4r[a], k4_a);
-      k4_total += k4_a;
-    }
-    if (lane == 0 && tri_a) atomicAdd(&c3r[a], tri_a);
-    tri_total += tri_a;
-    __syncwarp();
-  }
-  probes = warp_sum_u64(probes);
-  if (lane == 0) {
-    if (probes) atomicAdd(&work_ctr[0], probes);
-    if (tri_total) atomicAdd(&work_ctr[1], tri_total);
-    if (k4_total) atomicAdd(&work_ctr[2], k4_total);
-  }
-}
-
+// Pass 2 from the lowest vertex for out-degrees up to 32 (see k_tri2_low).
 template <int PL>
-__global__ void __launch_bounds__(TW_T) k_tri2_warp(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
+__global__ void __launch_bounds__(TW_T) k_tri2_warp_low(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol,
                                                     const int32_t* __restrict__ work,
                                                     const int32_t* __restrict__ nwork, int* next,
                                                     const int32_t* __restrict__ C3o, u64* r13r, int* err) {
@@ -821,24 +984,35 @@ cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
-                        int* next, int dpmax, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st, int loads,
-                        int hf, int group) {
+cudaError_t launch_tri2(const int64_t* orp, const int32_t* ocol, const int64_t* irp, const int2* iin,
+                        const int32_t* work, const int32_t* nwork, int* next, int dpmax, const int32_t* C3o, u64* r13r,
+                        int* err, cudaStream_t st, int loads, int hf, int group, bool middle) {
   if (dpmax < 2) return cudaSuccess;
   const size_t smem = tri2_smem_bytes(dpmax, hf);
   if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
   // the out-degree class beyond the shared-memory bitmap of pass 1 runs with
   // 1024-thread blocks (its tables allow one block per SM)
   const bool big = !tri1_bitmap_fits_smem(dpmax, hf);
-  auto pick = [&](auto f8, auto f16, auto f32) { return group >= 32 ? f32 : (group >= 16 ? f16 : f8); };
-  auto* fn = big ? (loads >= 4 ? pick(k_tri2<4, TRI_T_BIG, 8>, k_tri2<4, TRI_T_BIG, 16>, k_tri2<4, TRI_T_BIG, 32>)
-                               : pick(k_tri2<2, TRI_T_BIG, 8>, k_tri2<2, TRI_T_BIG, 16>, k_tri2<2, TRI_T_BIG, 32>))
-                 : (loads >= 4 ? pick(k_tri2<4, TRI_T, 8>, k_tri2<4, TRI_T, 16>, k_tri2<4, TRI_T, 32>)
-                               : pick(k_tri2<2, TRI_T, 8>, k_tri2<2, TRI_T, 16>, k_tri2<2, TRI_T, 32>));
-  allow_max_smem(fn);
   const int threads = big ? TRI_T_BIG : TRI_T;
-  const int grid = occupancy_grid((const void*)fn, smem, threads);
-  fn<<<grid, threads, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hash_bits_for(dpmax, hf), hf, C3o, r13r, err);
+  const int hb = hash_bits_for(dpmax, hf);
+  auto pick = [&](auto f8, auto f16, auto f32) { return group >= 32 ? f32 : (group >= 16 ? f16 : f8); };
+  if (middle) {  // the scanned tails are short: 8 lanes per in-entry, except for the largest out-degrees
+    auto* fn = big ? (loads >= 4 ? pick(k_tri2<4, TRI_T_BIG, 8>, k_tri2<4, TRI_T_BIG, 16>, k_tri2<4, TRI_T_BIG, 32>)
+                                 : pick(k_tri2<2, TRI_T_BIG, 8>, k_tri2<2, TRI_T_BIG, 16>, k_tri2<2, TRI_T_BIG, 32>))
+                   : (loads >= 4 ? k_tri2<4, TRI_T, 8> : k_tri2<2, TRI_T, 8>);
+    allow_max_smem(fn);
+    const int grid = occupancy_grid((const void*)fn, smem, threads);
+    fn<<<grid, threads, smem, st>>>(orp, ocol, irp, iin, work, nwork, next, dpmax, hb, hf, C3o, r13r, err);
+  } else {
+    auto* fn =
+        big ? (loads >= 4 ? pick(k_tri2_low<4, TRI_T_BIG, 8>, k_tri2_low<4, TRI_T_BIG, 16>, k_tri2_low<4, TRI_T_BIG, 32>)
+                          : pick(k_tri2_low<2, TRI_T_BIG, 8>, k_tri2_low<2, TRI_T_BIG, 16>, k_tri2_low<2, TRI_T_BIG, 32>))
+            : (loads >= 4 ? pick(k_tri2_low<4, TRI_T, 8>, k_tri2_low<4, TRI_T, 16>, k_tri2_low<4, TRI_T, 32>)
+                          : pick(k_tri2_low<2, TRI_T, 8>, k_tri2_low<2, TRI_T, 16>, k_tri2_low<2, TRI_T, 32>));
+    allow_max_smem(fn);
+    const int grid = occupancy_grid((const void*)fn, smem, threads);
+    fn<<<grid, threads, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, hf, C3o, r13r, err);
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -856,11 +1030,18 @@ cudaError_t launch_tri1_warp(const int64_t* orp, const int32_t* ocol, const int3
   return cudaGetLastError();
 }
 
-cudaError_t launch_tri2_warp(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
-                             int* next, const int32_t* C3o, u64* r13r, int* err, cudaStream_t st, int loads) {
-  auto* fn = loads >= 4 ? k_tri2_warp<4> : k_tri2_warp<2>;
-  const int grid = occupancy_grid((const void*)fn, 0, TW_T);
-  fn<<<grid, TW_T, 0, st>>>(orp, ocol, work, nwork, next, C3o, r13r, err);
+cudaError_t launch_tri2_warp(const int64_t* orp, const int32_t* ocol, const int64_t* irp, const int2* iin,
+                             const int32_t* work, const int32_t* nwork, int* next, const int32_t* C3o, u64* r13r,
+                             int* err, cudaStream_t st, int loads, bool middle) {
+  if (middle) {
+    auto* fn = loads >= 4 ? k_tri2_warp<4> : k_tri2_warp<2>;
+    const int grid = occupancy_grid((const void*)fn, 0, TW_T);
+    fn<<<grid, TW_T, 0, st>>>(orp, ocol, irp, iin, work, nwork, next, C3o, r13r, err);
+  } else {
+    auto* fn = loads >= 4 ? k_tri2_warp_low<4> : k_tri2_warp_low<2>;
+    const int grid = occupancy_grid((const void*)fn, 0, TW_T);
+    fn<<<grid, TW_T, 0, st>>>(orp, ocol, work, nwork, next, C3o, r13r, err);
+  }
   note_launch();
   return cudaGetLastError();
 }

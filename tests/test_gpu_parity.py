@@ -279,6 +279,20 @@ def test_rmat_s20_top_hubs_vs_stored_oracle_rows(s20):
         assert_same(net[v:v + 1], onet[None, :], f"hub {v} net")
 
 
+@pytest.mark.parametrize("pass2_from", [1, 2])
+def test_pass2_listing_vertex(pass2_from):
+    """The second triangle pass listed from each triangle's lowest vertex and
+    from its middle vertex (through the in-lists) gives the oracle's counts,
+    on R-MAT, BA, dense neighbourhoods and complete graphs."""
+    import paper_2007_11111_gb300 as fg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    with fg.Handle(device=0, tri_pass2_from=pass2_from) as h:
+        for g in (gg.rmat(12, 16, seed=4), gg.barabasi_albert(3000, 7, seed=8), gg.complete(40), gg.star(50),
+                  gg.dense_neighbourhoods(300, 0.4, (1.0, 0.7), 120, 0.8, seed=6)):
+            check_vs_oracle(h, g, f"pass 2 from {pass2_from}, n={g.n}")
+
+
 def test_rmat_s20_full_size_sampled(s20):
     """R-MAT scale 20, edge factor 16, seed 0, in the benchmark's launch
     configuration: every row checked against the invariants that hold at any

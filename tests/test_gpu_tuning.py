@@ -30,6 +30,11 @@ SETTINGS = [
     dict(cyc_long_segment=512, cyc_heavy_threads=512, cyc_spill_bits=13),
     dict(cyc_spill_bits=12, cyc_hub_span=64, cyc_dense_min=1),
     dict(cyc_hub_span=1, cyc_warp_bits=7, tri_class_bounds=(16, 32)),
+    dict(tri_pass2_from=1),
+    dict(tri_pass2_from=2),
+    dict(tri_pass2_from=2, tri_warp_max=-1, tri_class_bounds=(64, 256)),
+    dict(tri_pass2_from=2, tri_class_bounds=(2, 3), tri_group_lanes=8, tri_probe_loads=2),
+    dict(tri_pass2_from=2, tri_class_bounds=(3, 2000), tri_hash_factor=2),
 ]
 
 
@@ -76,7 +81,7 @@ def test_invalid_settings_rejected():
                 dict(cyc_hub_span=-1), dict(cyc_hub_span=90113), dict(tri_probe_loads=3),
                 dict(tri_hash_factor=3), dict(cyc_mid_threads=(64, 256, 256)), dict(cyc_dense_min=5000),
                 dict(tri_group_lanes=4), dict(cyc_long_segment=1), dict(tri_warp_max=33), dict(cyc_spill_bits=14),
-                dict(tri_warp_max=-2)):
+                dict(tri_warp_max=-2), dict(tri_pass2_from=3), dict(tri_pass2_from=-1)):
         with pytest.raises(fg.FgltError) as e:
             fg.Handle(device=0, **bad)
         assert e.value.status == fg.FGLT_ERR_INVALID_ARG
@@ -110,7 +115,8 @@ def test_autotune_installs_setting_and_keeps_results(cases):
                   tri_group_lanes=chosen["tri_group_lanes"], tri_warp_max=chosen["tri_warp_max"],
                   cyc_mid_threads=tuple(chosen["cyc_mid_threads"]), cyc_heavy_threads=chosen["cyc_heavy_threads"],
                   cyc_hub_span=chosen["cyc_hub_span"], cyc_dense_min=chosen["cyc_dense_min"],
-                  cyc_long_segment=chosen["cyc_long_segment"], cyc_spill_bits=chosen["cyc_spill_bits"])
+                  cyc_long_segment=chosen["cyc_long_segment"], cyc_spill_bits=chosen["cyc_spill_bits"],
+                  tri_pass2_from=chosen["tri_pass2_from"])
         with fg.Handle(device=0, **kw) as h2:
             raw, net = _run(h2, g)
             np.testing.assert_array_equal(net, onet)
