@@ -51,3 +51,26 @@ def test_reference_arm_nonzero_rank_exits_without_work():
                         "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_oracle_sampler_extrapolation():
+    """The CPU baseline's sampler: every bin below the degree cap that has an
+    affordable vertex is sampled, the per-row timers are positive where the
+    oracle computed rows, the estimate covers the sampled bins' vertices, and
+    the all-core throughput is at least the one-core one."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    import graphgen as gg
+    g = gg.rmat(12, 16, seed=2)
+    s = bench.OracleSampler(g, per_bin=2, threads=2, seed=1)
+    deg = np.diff(g.rowptr)
+    assert s.nb_cap >= 1 << 12
+    for b, cand in s.cands.items():
+        assert (np.floor(np.log2(np.maximum(deg[cand], 1))).astype(int)[deg[cand] > 0] == b).all()
+        assert (deg[cand] < s.deg_cap).all()
+    wall, est = s.step()
+    assert wall > 0 and est > 0
+    v_all, v_one = s.values(est)
+    assert v_all >= v_one > 0
+    assert "thread-seconds" in s.describe(1, est)
