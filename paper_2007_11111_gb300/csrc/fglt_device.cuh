@@ -14,6 +14,7 @@ enum : int {
   ERR_BAD_GRAPH = 2,      // validation found a non-simple / asymmetric CSR
   ERR_INTERNAL = 4,       // a consistency check failed
   ERR_BAD_ROWPTR = 8,     // row pointers not monotone / outside [0, nnz]
+  ERR_TIMEOUT = 16,       // a bounded device wait ran out
 };
 
 constexpr uint32_t EMPTY_KEY = 0xFFFFFFFFu;

@@ -552,6 +552,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   int e = 0;
   READ(err, &e);
   if (e & (ERR_BAD_GRAPH | ERR_BAD_ROWPTR)) return FGLT_ERR_INVALID_GRAPH;
+  if (e & ERR_TIMEOUT) return FGLT_ERR_TIMEOUT;
   if (e) return FGLT_ERR_INTERNAL;
   if (ro.work) {
     u64 w[W_NUM];

@@ -326,8 +326,13 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const int64_t* __restrict__
 constexpr int CHUNK_MAX = 512;  // middles per chunk: min(block size, 512)
 constexpr int SHORT_LANES = 8;  // lanes per short segment
 
-// Segments at least long_seg long are walked warp-per-segment (coalesced, one
-// owner); shorter ones by lane groups (walk_short).
+// Segments at least long_seg long are cut into pieces of PIECE wedges, walked
+// warp-per-piece (coalesced, one owner per piece), so one long segment is
+// shared by several warps; shorter ones are walked by lane groups
+// (walk_short). Measured at R-MAT s24: pieces of 256 wedges suit the
+// shared-hash classes, 512 the dense window with a shared spill table, 2048
+// the dense window with a global one (per-piece costs against the imbalance
+// of whole segments).
 
 struct Segs {
   int64_t* st;      // [chunk] short segments: start in ocol
@@ -338,7 +343,8 @@ struct Segs {
   int64_t* lst;     // [chunk] long segments: start in ocol
   int32_t* llen;    // [chunk] long segments: length
   int32_t* lrv;     // [chunk] long segments: rank of the middle
-  int* misc;        // [0] short count, [1] long count, [2] long cursor
+  int32_t* lpp;     // [chunk + 1] long segments: exclusive piece prefix
+  int* misc;        // [0] short count, [1] piece count, [2] piece cursor, [3] short cursor, [4] long count
 };
 
 // Block-wide exclusive scan; *total = sum.
@@ -373,6 +379,7 @@ __device__ __forceinline__ long long block_excl_scan(long long x, long long* scr
 // Segments of the middles c0 .. c0 + chunk of w: long ones listed for
 // warp-per-segment walks, short non-empty ones compacted with their wedge
 // prefix for the group walk (one packed block scan).
+template <int PIECE>
 __device__ __forceinline__ void build_chunk(const Segs& S, const Mids& M, int64_t c0, int64_t n, int chunk,
                                             int long_seg) {
   const int64_t k = c0 + threadIdx.x;
@@ -381,49 +388,66 @@ __device__ __forceinline__ void build_chunk(const Segs& S, const Mids& M, int64_
   if ((int)threadIdx.x < chunk && k < M.K) middle_seg(M, k, n, rv, st, len);
   const bool is_long = len >= long_seg;
   const bool is_short = len > 0 && !is_long;
-  // packed: [short wedge sum : 32 | short count : 16 | long count : 16]
-  const long long packed = ((is_short ? len : 0LL) << 32) | ((long long)is_short << 16) | (long long)is_long;
+  // A segment lies in one out-list of the degree order, so len <= sqrt(2 nnz)
+  // < 2^16 and a chunk holds fewer than 2^17 pieces and 2^18 short wedges.
+  // packed: [short wedge sum : 20 | short count : 11 | long count : 11 | pieces : 22]
+  const long long pieces = is_long ? (len + PIECE - 1) / PIECE : 0;
+  const long long packed = ((is_short ? len : 0LL) << 44) | ((long long)is_short << 33) |
+                           ((long long)is_long << 22) | pieces;
   long long tot;
   const long long ex = block_excl_scan(packed, S.scan, &tot);
   if (is_short) {
-    const int pos = (int)((ex >> 16) & 0xFFFF);
+    const int pos = (int)((ex >> 33) & 0x7FF);
     S.st[pos] = st;
-    S.pre[pos] = (int32_t)(ex >> 32);
+    S.pre[pos] = (int32_t)(ex >> 44);
     S.rv[pos] = rv;
     S.acc[pos] = 0;
   } else if (is_long) {
-    const int pos = (int)(ex & 0xFFFF);
+    const int pos = (int)((ex >> 22) & 0x7FF);
     S.lst[pos] = st;
     S.llen[pos] = (int32_t)len;
     S.lrv[pos] = rv;
+    S.lpp[pos] = (int32_t)(ex & 0x3FFFFF);
   }
   if (threadIdx.x == 0) {
-    const int ns = (int)((tot >> 16) & 0xFFFF);
+    const int ns = (int)((tot >> 33) & 0x7FF);
+    const int nl = (int)((tot >> 22) & 0x7FF);
     S.misc[0] = ns;
-    S.misc[1] = (int)(tot & 0xFFFF);
+    S.misc[1] = (int)(tot & 0x3FFFFF);
     S.misc[2] = 0;
     S.misc[3] = 0;
-    S.pre[ns] = (int32_t)(tot >> 32);
+    S.misc[4] = nl;
+    S.pre[ns] = (int32_t)(tot >> 44);
+    S.lpp[nl] = (int32_t)(tot & 0x3FFFFF);
   }
   __syncthreads();
 }
 
-// Long segments: warps take them one at a time; lanes stride over the
-// segment (coalesced, one owner). g(u) per wedge; done(rv, lane_sum) after
-// each segment with the warp's sum of g's return values.
-template <typename G, typename D>
+// Long segments: warps take pieces one at a time from the chunk's queue
+// (S.misc[2]); the piece's segment is the last one whose piece prefix is at
+// most the piece index (a two-level ballot search over at most 2^10
+// prefixes). Lanes stride over the piece (coalesced, four loads in flight).
+// g(u) per wedge; done(rv, lane_sum) after each piece with the warp's sum of
+// g's return values.
+template <int PIECE, typename G, typename D>
 __device__ __forceinline__ void walk_long(const Segs& S, const int32_t* __restrict__ ocol, G g, D done) {
   const int lane = threadIdx.x & 31;
-  const int nl = S.misc[1];
+  const int np = S.misc[1], nl = S.misc[4];
   for (;;) {
     int i = 0;
     if (lane == 0) i = atomicAdd(&S.misc[2], 1);
     i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= nl) break;
-    const int32_t* p = ocol + S.lst[i];
-    const int len = S.llen[i];
+    if (i >= np) break;
+    // coarse: lanes test every 32nd prefix; fine: the 32 prefixes after it
+    const int c = lane * 32;
+    const unsigned mc = __ballot_sync(0xffffffffu, c < nl && S.lpp[c] <= i);
+    const int base = (31 - __clz(mc)) * 32;
+    const unsigned mf = __ballot_sync(0xffffffffu, base + lane < nl && S.lpp[base + lane] <= i);
+    const int sg = base + 31 - __clz(mf);
+    const int off = (i - S.lpp[sg]) * PIECE;
+    const int32_t* p = ocol + S.lst[sg] + off;
+    const int len = min(PIECE, S.llen[sg] - off);
     u64 sum = 0;
-    // four coalesced loads in flight before the first update
     for (int q = lane; q < len; q += 128) {
       uint32_t x[4];
 #pragma unroll
@@ -432,7 +456,7 @@ __device__ __forceinline__ void walk_long(const Segs& S, const int32_t* __restri
       for (int r = 0; r < 4; ++r)
         if (q + 32 * r < len) sum += g(x[r]);
     }
-    done(S.lrv[i], sum);
+    done(S.lrv[sg], sum);
   }
 }
 
@@ -468,7 +492,7 @@ __device__ __forceinline__ void walk_short(const Segs& S, const int32_t* __restr
 }
 
 size_t seg_bytes(int ch) {
-  return (size_t)ch * 8 * 3 + 64 * 8 + (size_t)(ch + 1) * 4 + (size_t)ch * 4 * 3 + 16;
+  return (size_t)ch * 8 * 3 + 64 * 8 + (size_t)(ch + 1) * 4 * 2 + (size_t)ch * 4 * 3 + 32;
 }
 
 template <int MODE, int BT>
@@ -482,6 +506,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
   constexpr bool DENSE = MODE == 1 || MODE == 4;
   constexpr bool GMEM = MODE == 3 || MODE == 4;
   constexpr int CH = BT < CHUNK_MAX ? BT : CHUNK_MAX;
+  constexpr int PIECE = MODE == 0 ? 256 : (MODE == 4 ? 2048 : 512);
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ u64 red[32];
@@ -495,8 +520,9 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
   S.rv = S.pre + CH + 1;
   S.llen = S.rv + CH;
   S.lrv = S.llen + CH;
-  S.misc = S.lrv + CH;
-  uint32_t* after = reinterpret_cast<uint32_t*>(S.misc + 4);
+  S.lpp = S.lrv + CH;
+  S.misc = S.lpp + CH + 1;
+  uint32_t* after = reinterpret_cast<uint32_t*>(S.misc + 8);
   uint32_t* dense = after;
   uint32_t* hbase = DENSE ? after + dense_words : after;
   __shared__ int s_ntouched;
@@ -562,20 +588,20 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
     };
     // Pass A: count the wedges per top u.
     for (int64_t c0 = 0; c0 < M.K; c0 += CH) {
-      build_chunk(S, M, c0, n, CH, long_seg);
-      walk_long(S, ocol, [&](uint32_t u) -> u64 { count(u); return 0; }, [](int32_t, u64) {});
+      build_chunk<PIECE>(S, M, c0, n, CH, long_seg);
+      walk_long<PIECE>(S, ocol, [&](uint32_t u) -> u64 { count(u); return 0; }, [](int32_t, u64) {});
       walk_short<SHORT_LANES, false>(S, ocol, [&](uint32_t u) -> u64 { count(u); return 0; }, [](int, u64) {});
       __syncthreads();
     }
     // Pass B: each middle gains cnt[u] - 1 per wedge.
     for (int64_t c0 = 0; c0 < M.K; c0 += CH) {
       if (!single) {
-        build_chunk(S, M, c0, n, CH, long_seg);
+        build_chunk<PIECE>(S, M, c0, n, CH, long_seg);
       } else {
         if (tid == 0) S.misc[2] = S.misc[3] = 0;
         __syncthreads();
       }
-      walk_long(S, ocol, credit, [&](int32_t rv, u64 sum) {
+      walk_long<PIECE>(S, ocol, credit, [&](int32_t rv, u64 sum) {
         sum = warp_sum_u64(sum);
         if ((tid & 31) == 0 && sum) atomicAdd(&r12r[rv], sum);
       });

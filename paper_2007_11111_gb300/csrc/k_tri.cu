@@ -19,6 +19,7 @@
 //   d^13 = D4,c e / 2 with D4,c = A o (A (C3 - A))       (Sec. 4.3)
 #include "fglt_device.cuh"
 #include "fglt_kernels.h"
+#include "tcgen05.cuh"
 
 namespace fglt {
 
@@ -203,6 +204,126 @@ __device__ __forceinline__ void hub_cliques(const uint32_t* __restrict__ bm, int
   }
 }
 
+// Tensor-core clique phase of the global-bitmap class (tcgen05, E4M3 inputs,
+// f32 accumulators in tensor memory). With S the 0/1 adjacency matrix of G_a,
+// k2loc[x] gains sum_y S_xy (S S)_xy: over the edges x-y of G_a, the
+// triangles of G_a on each, the same tallies as the row-AND popcounts. S is
+// symmetric, so the block of S S for a row band X (128 rows) and a column
+// span Y (512 columns) is S_X S_Y^T, both operands K-major rows of S. Per
+// chunk of 128 columns of K both bands are expanded from the bitmap to bytes
+// (0 or 1.0 in E4M3) in shared memory, in core matrices of 8 rows x 16 bytes;
+// one thread issues 8 MMAs (two 128 x 256 accumulators, four K steps of 32)
+// and commits them to the stage's barrier while the block expands the next
+// chunk into the other stage. The accumulators are read out (and restarted)
+// after at most 4096 columns of K, so every f32 sum is an integer below 2^12
+// and exact even for an adder that keeps only 14 mantissa bits. Needs 32
+// warps (the epilogue reads the 128 x 512 accumulators as 4 lane quarters x
+// 8 column blocks).
+constexpr int TC_M = 128, TC_N = 256, TC_SPAN = 2 * TC_N, TC_KC = 128;
+constexpr int TC_A_BYTES = TC_M * TC_KC, TC_B_BYTES = TC_SPAN * TC_KC;
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_REGION_WORDS = 2 * TC_STAGE_BYTES / 4;
+constexpr uint32_t TC_COLS = 512;                     // tensor-memory columns: two f32 accumulators of 256
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;        // limit of one barrier wait (2 s)
+constexpr uint32_t TC_IDESC = tc::idesc_e4m3_f32(TC_M, TC_N);
+constexpr int TC_SEG_CHUNKS = 4096 / TC_KC;            // K chunks per accumulator read-out
+
+struct TcState {
+  uint64_t* bar;  // [2] stage barriers (one phase per committed chunk)
+  uint32_t tmem;  // accumulator base address in tensor memory
+  uint32_t g;     // chunks committed by this block so far
+  int* abort;     // shared: a barrier wait ran out
+};
+
+// 16 bits of a bitmap row -> 16 bytes, bit b -> byte b (0 or 0x38 = 1.0 in E4M3).
+__device__ __forceinline__ void expand16(uint32_t bits, uint4* dst) {
+  auto nib = [](uint32_t n) { return ((n * 0x00204081u) & 0x01010101u) * 0x38u; };
+  uint4 v;
+  v.x = nib(bits & 15u);
+  v.y = nib((bits >> 4) & 15u);
+  v.z = nib((bits >> 8) & 15u);
+  v.w = nib((bits >> 12) & 15u);
+  *dst = v;
+}
+
+// False if a barrier wait ran out (all threads return together).
+__device__ __forceinline__ bool hub_cliques_tc(const uint32_t* __restrict__ bm, int D, int W, int WS,
+                                               uint32_t* k2loc, unsigned char* smem, TcState& T) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nk = (D + TC_KC - 1) / TC_KC;
+  const uint32_t sbase = tc::smem_addr(smem);
+  for (int x0 = 0; x0 < D; x0 += TC_M) {
+    for (int y0 = 0; y0 < D; y0 += TC_SPAN) {
+     for (int c0 = 0; c0 < nk; c0 += TC_SEG_CHUNKS) {
+      const int c1 = min(nk, c0 + TC_SEG_CHUNKS);
+      for (int c = c0; c < c1; ++c, ++T.g) {
+        const int s = T.g & 1;
+        // the stage's previous chunk must be consumed before it is overwritten
+        if (T.g >= 2 && !tc::mbar_wait(&T.bar[s], ((T.g - 2) >> 1) & 1u, TC_WAIT_NS)) *T.abort = 1;
+        unsigned char* A = smem + s * TC_STAGE_BYTES;
+        unsigned char* B = A + TC_A_BYTES;
+        const int kw0 = c * (TC_KC / 32);
+        // item = (operand row, bitmap word of the chunk); 4 lanes per row
+        for (int i = tid; i < (TC_M + TC_SPAN) * (TC_KC / 32); i += blockDim.x) {
+          const int r = i >> 2, j = i & 3;
+          const bool isA = r < TC_M;
+          const int rr = isA ? r : r - TC_M;
+          const int row = isA ? x0 + rr : y0 + rr;
+          const int kw = kw0 + j;
+          const uint32_t v = (row < D && kw < W) ? __ldcg(bm + (size_t)row * WS + kw) : 0u;
+          unsigned char* op = (isA ? A : B) + (rr >> 3) * (8 * TC_KC) + (rr & 7) * 16 + (2 * j) * 128;
+          expand16(v & 0xFFFFu, reinterpret_cast<uint4*>(op));
+          expand16(v >> 16, reinterpret_cast<uint4*>(op + 128));
+        }
+        tc::fence_async_smem();
+        __syncthreads();
+        if (*T.abort) return false;
+        if (tid == 0) {
+          tc::fence_after_sync();
+          const uint32_t a0 = sbase + s * TC_STAGE_BYTES, b0 = a0 + TC_A_BYTES;
+#pragma unroll
+          for (int ks = 0; ks < TC_KC / 32; ++ks) {
+            // a K step of 32 bytes spans two core matrices along K (128 bytes apart)
+            const uint64_t ad = tc::smem_desc(a0 + ks * 256, 128, 8 * TC_KC);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint64_t bd = tc::smem_desc(b0 + h * (TC_N * TC_KC) + ks * 256, 128, 8 * TC_KC);
+              tc::mma_e4m3(T.tmem + h * TC_N, ad, bd, TC_IDESC, (c > c0 || ks > 0) ? 1u : 0u);
+            }
+          }
+          tc::mma_commit(&T.bar[s]);
+        }
+      }
+      // the last commit completes after every MMA of the segment
+      const uint32_t gl = T.g - 1;
+      if (!tc::mbar_wait(&T.bar[gl & 1], (gl >> 1) & 1u, TC_WAIT_NS)) *T.abort = 1;
+      tc::fence_after_sync();
+      const int q = warp & 3, cb = warp >> 2;
+      const int x = x0 + 32 * q + lane;
+      uint32_t kx = 0;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int col = cb * 64 + hh * 32;
+        uint32_t r[32];
+        tc::tmem_ld32(T.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, r);
+        tc::tmem_ld_wait();
+        const int yw = (y0 + col) >> 5;
+        const uint32_t bits = (x < D && yw < W) ? __ldcg(bm + (size_t)x * WS + yw) : 0u;
+        float sum = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sum += ((bits >> j) & 1u) ? __uint_as_float(r[j]) : 0.f;
+        kx += (uint32_t)sum;
+      }
+      if (x < D && kx) atomicAdd(&k2loc[x], kx);
+      tc::fence_before_sync();
+      __syncthreads();
+      if (*T.abort) return false;
+     }
+    }
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // Pass 1
 //
@@ -220,7 +341,8 @@ __device__ __forceinline__ void hub_cliques(const uint32_t* __restrict__ bm, int
 __host__ __device__ __forceinline__ size_t hub_region_words(int Hbits, int fwords, int Wmax, int TB, int nwarps) {
   const size_t table = 2 * ((size_t)1 << Hbits) + (size_t)fwords;
   const size_t bands = 2 * (size_t)TB * (size_t)(Wmax | 1) + (size_t)nwarps * TB;
-  return table > bands ? table : bands;
+  const size_t r = table > bands ? table : bands;
+  return r > (size_t)TC_REGION_WORDS ? r : (size_t)TC_REGION_WORDS;
 }
 
 constexpr int TRI_YL = 256;  // y-list entries per warp in the clique phase of the shared-memory classes
@@ -257,6 +379,30 @@ __global__ void __launch_bounds__(BT)
   int32_t* wlist = SMEM_BM ? ylist + TRI_YL : nullptr;
   const int total = *nwork;
   const unsigned below = (1u << lane) - 1u;
+
+  // Global-bitmap class with cliques: tensor memory for the accumulators and
+  // the two stage barriers of the tensor-core clique phase.
+  constexpr bool TCP = !SMEM_BM && K4;
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  TcState T{s_bar, 0u, 0u, &s_abort};
+  if (TCP) {
+    if (tid == 0) {
+      tc::mbar_init(&s_bar[0], 1);
+      tc::mbar_init(&s_bar[1], 1);
+      tc::mbar_init_fence();
+      s_abort = 0;
+    }
+    if (warp == 0) {
+      tc::tmem_alloc(&s_tmem, TC_COLS);
+      tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    T.tmem = s_tmem;
+  }
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(next, 1);
@@ -331,7 +477,7 @@ __global__ void __launch_bounds__(BT)
           tri2x += (u64)deg;
         }
       }
-      if (K4) hub_cliques(bm, D, W, WS, Wmax, TB, k2loc, smem);
+      if (TCP && !hub_cliques_tc(bm, D, W, WS, k2loc, smem, T)) break;
     }
     for (int x = warp; SMEM_BM && x < D; x += nwarps) {
       const uint32_t* Sx = bm + (size_t)x * WS;
@@ -422,6 +568,20 @@ __global__ void __launch_bounds__(BT)
       atomicAdd(&work_ctr[2], k4_sum);
     }
     __syncthreads();
+  }
+  if (TCP) {
+    // after a wait ran out: wait (bounded) for the block's last MMAs before
+    // the tensor memory is released
+    if (s_abort) {
+      if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+      if (T.g > 0) tc::mbar_wait(&s_bar[(T.g - 1) & 1], ((T.g - 1) >> 1) & 1u, TC_WAIT_NS);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+      tc::fence_after_sync();
+      tc::tmem_dealloc(T.tmem, TC_COLS);
+    }
   }
 }
 
