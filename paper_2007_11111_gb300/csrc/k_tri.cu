@@ -209,16 +209,20 @@ __device__ __forceinline__ void hub_cliques(const uint32_t* __restrict__ bm, int
 // k2loc[x] gains sum_y S_xy (S S)_xy: over the edges x-y of G_a, the
 // triangles of G_a on each, the same tallies as the row-AND popcounts. S is
 // symmetric, so the block of S S for a row band X (128 rows) and a column
-// span Y (512 columns) is S_X S_Y^T, both operands K-major rows of S. Per
-// chunk of 128 columns of K both bands are expanded from the bitmap to bytes
-// (0 or 1.0 in E4M3) in shared memory, in core matrices of 8 rows x 16 bytes;
-// one thread issues 8 MMAs (two 128 x 256 accumulators, four K steps of 32)
-// and commits them to the stage's barrier while the block expands the next
-// chunk into the other stage. The accumulators are read out (and restarted)
-// after at most 4096 columns of K, so every f32 sum is an integer below 2^12
-// and exact even for an adder that keeps only 14 mantissa bits. Needs 32
-// warps (the epilogue reads the 128 x 512 accumulators as 4 lane quarters x
-// 8 column blocks).
+// span Y (512 columns) is S_X S_Y^T, both operands K-major rows of S, and
+// only the blocks on or above the diagonal are formed: spans start at the
+// band's first row; a pair (x, y) with y in a later 128-row block adds its
+// count to the row tally of x and (by a cross-lane column reduction) to the
+// tally of y, a pair in the band's own square block to the row tally only.
+// Per chunk of 128 columns of K both bands are expanded from the bitmap to
+// bytes (0 or 1.0 in E4M3) in shared memory, in core matrices of 8 rows x 16
+// bytes; one thread issues 8 MMAs (two 128 x 256 accumulators, four K steps
+// of 32) and commits them to the stage's barrier while the block expands the
+// next chunk into the other stage (its bitmap words loaded a chunk ahead).
+// The accumulators are read out (and restarted) after at most 4096 columns
+// of K, so every f32 sum is an integer below 2^12, exact even for an adder
+// that keeps only 14 mantissa bits. The epilogue reads the 128 x 512
+// accumulators as 4 lane quarters x 8 column blocks: 32 warps.
 constexpr int TC_M = 128, TC_N = 256, TC_SPAN = 2 * TC_N, TC_KC = 128;
 constexpr int TC_A_BYTES = TC_M * TC_KC, TC_B_BYTES = TC_SPAN * TC_KC;
 constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
@@ -227,6 +231,7 @@ constexpr uint32_t TC_COLS = 512;                     // tensor-memory columns: 
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;        // limit of one barrier wait (2 s)
 constexpr uint32_t TC_IDESC = tc::idesc_e4m3_f32(TC_M, TC_N);
 constexpr int TC_SEG_CHUNKS = 4096 / TC_KC;            // K chunks per accumulator read-out
+constexpr int TC_ITEMS = (TC_M + TC_SPAN) * (TC_KC / 32);  // (operand row, bitmap word) pairs per chunk
 
 struct TcState {
   uint64_t* bar;  // [2] stage barriers (one phase per committed chunk)
@@ -246,79 +251,118 @@ __device__ __forceinline__ void expand16(uint32_t bits, uint4* dst) {
   *dst = v;
 }
 
+// Column sums across the warp (v holds f32 bit patterns): lane L ends with
+// the sum over all 32 lanes of v[L % 16] (recursive halving, 16 shuffles).
+__device__ __forceinline__ float warp_column_sums16(uint32_t (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool upper = lane & o;
+#pragma unroll
+    for (int k = 0; k < o; ++k) {
+      const uint32_t give = upper ? v[k] : v[k + o];
+      const uint32_t keep = upper ? v[k + o] : v[k];
+      v[k] = __float_as_uint(__uint_as_float(keep) + __uint_as_float(__shfl_xor_sync(0xffffffffu, give, o)));
+    }
+  }
+  return __uint_as_float(v[0]) + __uint_as_float(__shfl_xor_sync(0xffffffffu, v[0], 16));
+}
+
 // False if a barrier wait ran out (all threads return together).
+template <int BT>
 __device__ __forceinline__ bool hub_cliques_tc(const uint32_t* __restrict__ bm, int D, int W, int WS,
                                                uint32_t* k2loc, unsigned char* smem, TcState& T) {
+  static_assert(BT == 1024, "the epilogue maps 32 warps onto the accumulators");
+  constexpr int PER = (TC_ITEMS + BT - 1) / BT;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nk = (D + TC_KC - 1) / TC_KC;
   const uint32_t sbase = tc::smem_addr(smem);
+  // item i: operand row i / 4 (A rows, then B rows), word i % 4 of the chunk
+  auto load = [&](uint32_t (&v)[PER], int x0, int y0, int c) {
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int i = tid + t * BT;
+      const int r = i >> 2, kw = c * (TC_KC / 32) + (i & 3);
+      const int row = r < TC_M ? x0 + r : y0 + (r - TC_M);
+      v[t] = (i < TC_ITEMS && row < D && kw < W) ? __ldcg(bm + (size_t)row * WS + kw) : 0u;
+    }
+  };
+  auto store = [&](const uint32_t (&v)[PER], unsigned char* stage) {
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int i = tid + t * BT;
+      if (i < TC_ITEMS) {
+        const int r = i >> 2, j = i & 3;
+        const int rr = r < TC_M ? r : r - TC_M;
+        unsigned char* op = stage + (r < TC_M ? 0 : TC_A_BYTES) + (rr >> 3) * (8 * TC_KC) + (rr & 7) * 16 + j * 256;
+        expand16(v[t] & 0xFFFFu, reinterpret_cast<uint4*>(op));
+        expand16(v[t] >> 16, reinterpret_cast<uint4*>(op + 128));
+      }
+    }
+  };
   for (int x0 = 0; x0 < D; x0 += TC_M) {
-    for (int y0 = 0; y0 < D; y0 += TC_SPAN) {
-     for (int c0 = 0; c0 < nk; c0 += TC_SEG_CHUNKS) {
-      const int c1 = min(nk, c0 + TC_SEG_CHUNKS);
-      for (int c = c0; c < c1; ++c, ++T.g) {
-        const int s = T.g & 1;
-        // the stage's previous chunk must be consumed before it is overwritten
-        if (T.g >= 2 && !tc::mbar_wait(&T.bar[s], ((T.g - 2) >> 1) & 1u, TC_WAIT_NS)) *T.abort = 1;
-        unsigned char* A = smem + s * TC_STAGE_BYTES;
-        unsigned char* B = A + TC_A_BYTES;
-        const int kw0 = c * (TC_KC / 32);
-        // item = (operand row, bitmap word of the chunk); 4 lanes per row
-        for (int i = tid; i < (TC_M + TC_SPAN) * (TC_KC / 32); i += blockDim.x) {
-          const int r = i >> 2, j = i & 3;
-          const bool isA = r < TC_M;
-          const int rr = isA ? r : r - TC_M;
-          const int row = isA ? x0 + rr : y0 + rr;
-          const int kw = kw0 + j;
-          const uint32_t v = (row < D && kw < W) ? __ldcg(bm + (size_t)row * WS + kw) : 0u;
-          unsigned char* op = (isA ? A : B) + (rr >> 3) * (8 * TC_KC) + (rr & 7) * 16 + (2 * j) * 128;
-          expand16(v & 0xFFFFu, reinterpret_cast<uint4*>(op));
-          expand16(v >> 16, reinterpret_cast<uint4*>(op + 128));
+    for (int y0 = x0; y0 < D; y0 += TC_SPAN) {
+      for (int c0 = 0; c0 < nk; c0 += TC_SEG_CHUNKS) {
+        const int c1 = min(nk, c0 + TC_SEG_CHUNKS);
+        uint32_t v[PER];
+        load(v, x0, y0, c0);
+        for (int c = c0; c < c1; ++c, ++T.g) {
+          const int s = T.g & 1;
+          // the stage's previous chunk must be consumed before it is overwritten
+          if (T.g >= 2 && !tc::mbar_wait(&T.bar[s], ((T.g - 2) >> 1) & 1u, TC_WAIT_NS)) *T.abort = 1;
+          store(v, smem + s * TC_STAGE_BYTES);
+          if (c + 1 < c1) load(v, x0, y0, c + 1);
+          tc::fence_async_smem();
+          __syncthreads();
+          if (*T.abort) return false;
+          if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = sbase + s * TC_STAGE_BYTES, b0 = a0 + TC_A_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < TC_KC / 32; ++ks) {
+              // a K step of 32 bytes spans two core matrices along K (128 bytes apart)
+              const uint64_t ad = tc::smem_desc(a0 + ks * 256, 128, 8 * TC_KC);
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const uint64_t bd = tc::smem_desc(b0 + h * (TC_N * TC_KC) + ks * 256, 128, 8 * TC_KC);
+                tc::mma_e4m3(T.tmem + h * TC_N, ad, bd, TC_IDESC, (c > c0 || ks > 0) ? 1u : 0u);
+              }
+            }
+            tc::mma_commit(&T.bar[s]);
+          }
         }
-        tc::fence_async_smem();
+        // the last commit completes after every MMA of the segment
+        const uint32_t gl = T.g - 1;
+        if (!tc::mbar_wait(&T.bar[gl & 1], (gl >> 1) & 1u, TC_WAIT_NS)) *T.abort = 1;
+        tc::fence_after_sync();
+        const int q = warp & 3, cb = warp >> 2;
+        const int x = x0 + 32 * q + lane;
+        float kx = 0.f;
+#pragma unroll
+        for (int hh = 0; hh < 4; ++hh) {
+          const int col = cb * 64 + hh * 16;
+          uint32_t r[16];
+          tc::tmem_ld16(T.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, r);
+          tc::tmem_ld_wait();
+          const int yw = (y0 + col) >> 5;
+          const uint32_t bits = (x < D && yw < W) ? __ldcg(bm + (size_t)x * WS + yw) >> (col & 16) : 0u;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float f = ((bits >> j) & 1u) ? __uint_as_float(r[j]) : 0.f;
+            kx += f;
+            r[j] = __float_as_uint(f);
+          }
+          if (y0 + col >= x0 + TC_M) {  // beyond the band's square block: the pairs (y, x) too
+            const float cy = warp_column_sums16(r);
+            const int y = y0 + col + lane;
+            if (lane < 16 && y < D && cy != 0.f) atomicAdd(&k2loc[y], (uint32_t)cy);
+          }
+        }
+        if (x < D && kx != 0.f) atomicAdd(&k2loc[x], (uint32_t)kx);
+        tc::fence_before_sync();
         __syncthreads();
         if (*T.abort) return false;
-        if (tid == 0) {
-          tc::fence_after_sync();
-          const uint32_t a0 = sbase + s * TC_STAGE_BYTES, b0 = a0 + TC_A_BYTES;
-#pragma unroll
-          for (int ks = 0; ks < TC_KC / 32; ++ks) {
-            // a K step of 32 bytes spans two core matrices along K (128 bytes apart)
-            const uint64_t ad = tc::smem_desc(a0 + ks * 256, 128, 8 * TC_KC);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const uint64_t bd = tc::smem_desc(b0 + h * (TC_N * TC_KC) + ks * 256, 128, 8 * TC_KC);
-              tc::mma_e4m3(T.tmem + h * TC_N, ad, bd, TC_IDESC, (c > c0 || ks > 0) ? 1u : 0u);
-            }
-          }
-          tc::mma_commit(&T.bar[s]);
-        }
       }
-      // the last commit completes after every MMA of the segment
-      const uint32_t gl = T.g - 1;
-      if (!tc::mbar_wait(&T.bar[gl & 1], (gl >> 1) & 1u, TC_WAIT_NS)) *T.abort = 1;
-      tc::fence_after_sync();
-      const int q = warp & 3, cb = warp >> 2;
-      const int x = x0 + 32 * q + lane;
-      uint32_t kx = 0;
-#pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        const int col = cb * 64 + hh * 32;
-        uint32_t r[32];
-        tc::tmem_ld32(T.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, r);
-        tc::tmem_ld_wait();
-        const int yw = (y0 + col) >> 5;
-        const uint32_t bits = (x < D && yw < W) ? __ldcg(bm + (size_t)x * WS + yw) : 0u;
-        float sum = 0.f;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) sum += ((bits >> j) & 1u) ? __uint_as_float(r[j]) : 0.f;
-        kx += (uint32_t)sum;
-      }
-      if (x < D && kx) atomicAdd(&k2loc[x], kx);
-      tc::fence_before_sync();
-      __syncthreads();
-      if (*T.abort) return false;
-     }
     }
   }
   return true;
@@ -477,7 +521,9 @@ __global__ void __launch_bounds__(BT)
           tri2x += (u64)deg;
         }
       }
-      if (TCP && !hub_cliques_tc(bm, D, W, WS, k2loc, smem, T)) break;
+      if constexpr (TCP) {
+        if (!hub_cliques_tc<BT>(bm, D, W, WS, k2loc, smem, T)) break;
+      }
     }
     for (int x = warp; SMEM_BM && x < D; x += nwarps) {
       const uint32_t* Sx = bm + (size_t)x * WS;
