@@ -12,7 +12,9 @@
 //   c3(i)   = triangles at i = C3 e / 2                  (Lemma 2)
 //   d^15(i) = 4-cliques at i = T e / 6, T(i,j) = q_ij^T A q_ij (Sec. 4.3):
 //             the 4-cliques {a, x, y, z} with a lowest are the triangles
-//             {x, y, z} of G_a, counted per vertex by popcounts of row ANDs.
+//             {x, y, z} of G_a, counted per vertex by popcounts of row ANDs
+//             (bitmap in shared memory) or, for the largest out-degrees, from
+//             the product S S of G_a's adjacency matrix on the tensor cores.
 // Pass 2 re-lists the triangles once C3 is final, from their middle vertex
 // (in-lists of the oriented graph), and adds, for a triangle {i,j,k},
 // C3(j,k) - 1 to i (and likewise for j and k):
@@ -123,91 +125,11 @@ struct Groups {
   }
 };
 
-// Clique phase of the global-bitmap class. The bitmap S of G_a (D rows of W
-// words at stride WS, in global memory) is taken in row bands of TB rows: a
-// band X is staged in shared memory, then every band Y at or after it, and
-// for each x in X and each neighbour y > x of x in Y the warp's lanes add
-// t = popc(S_x & S_y) over all W words to the tallies of x and y. G_a of a
-// vertex in this class is dense (rows rarely hold an empty word), so every
-// word is ANDed. Each band pair is read from global memory once, and the
-// popcounts read only shared memory.
-__device__ __forceinline__ void hub_cliques(const uint32_t* __restrict__ bm, int D, int W, int WS, int Wmax, int TB,
-                                            uint32_t* k2loc, unsigned char* smem) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  uint32_t* Xs = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* Ys = Xs + (size_t)TB * (Wmax | 1);
-  int32_t* yl = reinterpret_cast<int32_t*>(Ys + (size_t)TB * (Wmax | 1)) + warp * TB;
-  for (int x0 = 0; x0 < D; x0 += TB) {
-    const int nx = min(TB, D - x0);
-    __syncthreads();  // the previous band's readers (or the probe tables' users) are done
-    for (int i = tid; i < nx * WS; i += blockDim.x) Xs[i] = __ldcg(bm + (size_t)x0 * WS + i);
-    for (int y0 = x0; y0 < D; y0 += TB) {
-      const int ny = min(TB, D - y0);
-      const uint32_t* Yb = Xs;
-      if (y0 != x0) {
-        __syncthreads();  // the previous Y band's readers are done
-        for (int i = tid; i < ny * WS; i += blockDim.x) Ys[i] = __ldcg(bm + (size_t)y0 * WS + i);
-        Yb = Ys;
-      }
-      __syncthreads();
-      const int yw0 = y0 >> 5;  // TB is a multiple of 32
-      const int nyw = (ny + 31) >> 5;
-      for (int xi = warp; xi < nx; xi += nwarps) {
-        const int x = x0 + xi;
-        const uint32_t* xr = Xs + (size_t)xi * WS;
-        uint32_t bits = 0u;
-        if (lane < nyw) {
-          bits = xr[yw0 + lane];
-          const int yb = (yw0 + lane) << 5;
-          if (yb + 31 <= x) bits = 0u;
-          else if (yb <= x) bits &= ~((2u << (x - yb)) - 1u);  // keep y > x
-        }
-        const int c = __popc(bits);
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
-        }
-        int p = incl - c;
-        while (bits) {
-          const int t = __ffs(bits) - 1;
-          bits &= bits - 1;
-          yl[p++] = ((yw0 + lane) << 5) + t - y0;
-        }
-        const int nyl = __shfl_sync(0xffffffffu, incl, 31);
-        __syncwarp();
-        uint32_t kx = 0;
-        for (int i = lane; i < nyl; i += 32) {
-          const int yi = yl[i];
-          const uint32_t* yr = Yb + (size_t)yi * WS;
-          uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0;
-          int w = 0;
-          for (; w + 4 <= W; w += 4) {
-            t0 += __popc(xr[w] & yr[w]);
-            t1 += __popc(xr[w + 1] & yr[w + 1]);
-            t2 += __popc(xr[w + 2] & yr[w + 2]);
-            t3 += __popc(xr[w + 3] & yr[w + 3]);
-          }
-          for (; w < W; ++w) t0 += __popc(xr[w] & yr[w]);
-          const uint32_t t = t0 + t1 + t2 + t3;
-          if (t) {
-            atomicAdd(&k2loc[y0 + yi], t);
-            kx += t;
-          }
-        }
-        kx = (uint32_t)warp_sum_i32((int)kx);
-        if (lane == 0 && kx) atomicAdd(&k2loc[x], kx);
-        __syncwarp();
-      }
-    }
-  }
-}
-
 // Tensor-core clique phase of the global-bitmap class (tcgen05, E4M3 inputs,
 // f32 accumulators in tensor memory). With S the 0/1 adjacency matrix of G_a,
 // k2loc[x] gains sum_y S_xy (S S)_xy: over the edges x-y of G_a, the
-// triangles of G_a on each, the same tallies as the row-AND popcounts. S is
+// triangles of G_a on each (the row-AND popcounts of the shared-memory
+// classes give the same tallies). S is
 // symmetric, so the block of S S for a row band X (128 rows) and a column
 // span Y (512 columns) is S_X S_Y^T, both operands K-major rows of S, and
 // only the blocks on or above the diagonal are formed: spans start at the
@@ -378,15 +300,13 @@ __device__ __forceinline__ bool hub_cliques_tc(const uint32_t* __restrict__ bm, 
 //                                  i.e. twice the 4-cliques {a, x, ., .}
 // and a's own counts are the sums over x divided by 2 and 6.
 // ---------------------------------------------------------------------------
-// Shared-memory words of the region that holds, in turn, the probe tables of
-// N+(a) (hash keys and values, filter) and the two row bands of the clique
-// phase of the global-bitmap class (TB rows each, plus a TB-entry list per
-// warp); the clique tallies follow it.
-__host__ __device__ __forceinline__ size_t hub_region_words(int Hbits, int fwords, int Wmax, int TB, int nwarps) {
+// Shared-memory words of the region of the global-bitmap class that holds,
+// in turn, the probe tables of N+(a) (hash keys and values, filter) and the
+// two operand stages of the tensor-core clique phase; the clique tallies
+// follow it.
+__host__ __device__ __forceinline__ size_t hub_region_words(int Hbits, int fwords) {
   const size_t table = 2 * ((size_t)1 << Hbits) + (size_t)fwords;
-  const size_t bands = 2 * (size_t)TB * (size_t)(Wmax | 1) + (size_t)nwarps * TB;
-  const size_t r = table > bands ? table : bands;
-  return r > (size_t)TC_REGION_WORDS ? r : (size_t)TC_REGION_WORDS;
+  return table > (size_t)TC_REGION_WORDS ? table : (size_t)TC_REGION_WORDS;
 }
 
 constexpr int TRI_YL = 256;  // y-list entries per warp in the clique phase of the shared-memory classes
@@ -395,7 +315,7 @@ template <bool SMEM_BM, bool K4, int PL, int G, int BT>
 __global__ void __launch_bounds__(BT)
     k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol, const int32_t* __restrict__ work,
            const int32_t* __restrict__ nwork, int* next, int Dmax, int Hbits, int hf, int32_t* C3o, u64* c3r,
-           u64* k4r, uint32_t* gbm, u64* work_ctr, int* err, int TB) {
+           u64* k4r, uint32_t* gbm, u64* work_ctr, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ u64 red[32];
@@ -407,7 +327,7 @@ __global__ void __launch_bounds__(BT)
   uint32_t* filt = reinterpret_cast<uint32_t*>(vals + Hmax);
   // Shared-memory bitmap: [per-warp lists][bitmap][tallies] in shared memory.
   // Otherwise the bitmap lives in this block's slot of gbm, and shared memory
-  // holds [probe tables | row bands][tallies].
+  // holds [probe tables | tensor-core operand stages][tallies].
   int32_t* lists_base = nullptr;
   uint32_t* bm;
   uint32_t* k2loc;  // [Dmax] per-vertex 4-clique tallies
@@ -417,7 +337,7 @@ __global__ void __launch_bounds__(BT)
     k2loc = bm + (size_t)Dmax * (Wmax + 1);
   } else {
     bm = gbm + (size_t)blockIdx.x * ((size_t)Dmax * (Wmax + 1));
-    k2loc = reinterpret_cast<uint32_t*>(smem) + hub_region_words(Hbits, FWmax, Wmax, TB, nwarps);
+    k2loc = reinterpret_cast<uint32_t*>(smem) + hub_region_words(Hbits, FWmax);
   }
   int32_t* ylist = SMEM_BM ? lists_base + warp * (TRI_YL + Wmax) : nullptr;
   int32_t* wlist = SMEM_BM ? ylist + TRI_YL : nullptr;
@@ -503,9 +423,10 @@ __global__ void __launch_bounds__(BT)
     __syncthreads();
 
     // Per local vertex x: triangles through edge a-x (popc S_x). Per edge x-y
-    // of G_a with y > x: t = |S_x ∩ S_y| triangles of G_a on that edge, added
-    // to both ends, so k2loc[x] ends as twice the triangles of G_a at x, i.e.
-    // twice the 4-cliques {a, x, ., .}.
+    // of G_a: t = |S_x ∩ S_y| triangles of G_a on that edge, added to both
+    // ends, so k2loc[x] ends as twice the triangles of G_a at x, i.e. twice
+    // the 4-cliques {a, x, ., .} (tensor-core products in the global-bitmap
+    // class, row-AND popcounts over y > x otherwise).
     u64 tri2x = 0;
     if (!SMEM_BM) {
       for (int x = warp; x < D; x += nwarps) {
@@ -1058,24 +979,11 @@ int host_filter_words(int D) {
   return (1 << fb) >> 5;
 }
 
-// Rows per band of the global-bitmap class's clique phase: the largest of
-// 128, 64, 32 whose bands fit next to the tallies.
-int hub_tile_rows(int D, int hf) {
-  const int W = (D + 31) / 32;
-  for (int tb : {128, 64, 32}) {
-    const size_t words = hub_region_words(hash_bits_for(D, hf), host_filter_words(D), W, tb, TRI_T_BIG / 32) + D;
-    if (((words * 4 + 15) & ~(size_t)15) <= SMEM_LIMIT - 1024) return tb;
-  }
-  return 32;
-}
-
 size_t tri1_smem_impl(int D, bool smem_bm, int hf, int bt = TRI_T) {
   const int H = 1 << hash_bits_for(D, hf);
   const size_t W = (size_t)(D + 31) / 32;
-  if (!smem_bm) {  // [probe tables | row bands][tallies]
-    const size_t words =
-        hub_region_words(hash_bits_for(D, hf), host_filter_words(D), (int)W, hub_tile_rows(D, hf), TRI_T_BIG / 32) +
-        (size_t)D;
+  if (!smem_bm) {  // [probe tables | tensor-core operand stages][tallies]
+    const size_t words = hub_region_words(hash_bits_for(D, hf), host_filter_words(D)) + (size_t)D;
     return (words * 4 + 15) & ~(size_t)15;
   }
   size_t bytes = (size_t)H * 8 + (size_t)host_filter_words(D) * 4;
@@ -1185,7 +1093,7 @@ cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* 
                      : (cliques ? tri1_fn<false, true, TRI_T_BIG>(loads, group)
                                 : tri1_fn<false, false, TRI_T_BIG>(loads, group));
   fn<<<grid, bt, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, hf, C3o, c3r, k4r, smem_bm ? nullptr : gbm,
-                             work_ctr, err, smem_bm ? 0 : hub_tile_rows(dpmax, hf));
+                             work_ctr, err);
   note_launch();
   return cudaGetLastError();
 }

@@ -235,7 +235,7 @@ def test_dense_neighbourhoods_hub_classes(handle):
     """Two roots whose higher-ranked neighbours induce a random subgraph of
     density 1/2 (the shape of the largest triangle classes on R-MAT s24):
     out-degree 1100 runs in the class with the bitmap in global memory and its
-    banded clique phase, 991 in the largest shared-memory class. The roots, a
+    tensor-core clique phase, 991 in the largest shared-memory class. The roots, a
     few core and booster vertices against the oracle; every row against the
     invariants."""
     g = gg.dense_neighbourhoods(1100, 0.5, (1.0, 0.9), 900, 0.75, seed=5)

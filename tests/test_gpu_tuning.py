@@ -138,3 +138,29 @@ def test_global_bitmap_in_any_class_closed_form(bounds, lanes):
     want = np.zeros(16, np.int64)
     want[0], want[1], want[4], want[15] = 1, n - 1, comb(n - 1, 2), comb(n - 1, 3)
     np.testing.assert_array_equal(net, np.tile(want, (n, 1)))
+
+
+def test_complete_multipartite_beyond_one_accumulator_segment():
+    """Complete 6-partite graph with parts of 900 (vertex v in part v mod 6):
+    every vertex has degree 4500, so out-degrees in the degree order reach
+    4499 and the global-bitmap class forms S S on the tensor cores over more
+    than 4096 columns of K (two accumulator read-outs), with S zero wherever
+    two vertices share a part. All vertices are alike: triangles
+    binom(5, 2) 900^2 and 4-cliques binom(5, 3) 900^3 at each, equal rows,
+    and raw = U16 net."""
+    import paper_2007_11111_gb300 as fg
+    from math import comb
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    k, s = 6, 900
+    n = k * s
+    i, j = np.triu_indices(n, k=1)
+    keep = (i % k) != (j % k)
+    g = gg.csr_from_pairs(n, i[keep], j[keep])
+    with fg.Handle(device=0) as h:
+        raw, net = _run(h, g)
+    assert (net == net[0]).all(), "all vertices alike"
+    assert net[0, 1] == (k - 1) * s
+    assert net[0, 4] == comb(k - 1, 2) * s ** 2
+    assert net[0, 15] == comb(k - 1, 3) * s ** 3
+    np.testing.assert_array_equal(raw, net @ oracle.u16().T)
