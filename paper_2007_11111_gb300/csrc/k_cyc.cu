@@ -107,6 +107,41 @@ struct Table {
     }
     atomicOr(err, ERR_HASH_FULL);
   }
+  // First level of a two-level table: the key is counted only within the
+  // first `window` slots of its probe sequence; false if they all hold other
+  // keys (the caller then counts it in the next level). Slots are never freed
+  // while the vertex's passes run, so a key that went to the next level never
+  // finds room here later, and no key is counted in both levels.
+  __device__ __forceinline__ bool increment_window(uint32_t key, int hb, int window) const {
+    const uint32_t mask = (1u << hb) - 1;
+    uint32_t h = hash_slot(key, hb);
+    for (int probe = 0; probe < window; ++probe) {
+      uint32_t k = load_key(h);
+      if (k == EMPTY_KEY) {
+        k = atomicCAS(keys + h, EMPTY_KEY, key);
+        if (k == EMPTY_KEY) k = key;
+      }
+      if (k == key) {
+        atomicAdd(cnts + h, 1u);
+        return true;
+      }
+      h = (h + 1) & mask;
+    }
+    return false;
+  }
+  // The key's count in the first level (0 if an empty slot ends its window),
+  // or -1 if its window is full of other keys (the key is in the next level).
+  __device__ __forceinline__ int count_in_window(uint32_t key, int hb, int window) const {
+    const uint32_t mask = (1u << hb) - 1;
+    uint32_t h = hash_slot(key, hb);
+    for (int probe = 0; probe < window; ++probe) {
+      const uint32_t k = load_key(h);
+      if (k == key) return (int)load_cnt(h);
+      if (k == EMPTY_KEY) return 0;
+      h = (h + 1) & mask;
+    }
+    return -1;
+  }
   __device__ __forceinline__ uint32_t count_of(uint32_t key, int hb) const {
     const uint32_t mask = (1u << hb) - 1;
     uint32_t h = hash_slot(key, hb);
@@ -315,16 +350,20 @@ __global__ void __launch_bounds__(WARP_T) k_cyc_warp(const int64_t* __restrict__
 // ---------------------------------------------------------------------------
 // Larger vertices: one block per w. N(w) is taken CH middles at a time;
 // the non-empty segments of the chunk are compacted into shared memory with
-// their exclusive wedge prefix; long segments are walked one warp each, short
-// ones one group of SHORT_LANES lanes each.
+// their exclusive wedge prefix; long segments are cut into pieces walked one
+// warp each, short ones are walked by groups of SHORT_LANES lanes.
 //
 // MODE 0: hash table in shared memory sized per w (at most 2^13 slots)
-// MODE 1: dense 16-bit counters for tops >= hub_lo + 2^12-slot shared hash
-// MODE 2: dense 32-bit counters for tops >= hub_lo + 2^12-slot shared hash
+// MODE 1: dense 16-bit counters for tops >= hub_lo + a shared spill table
+//         (2^sbits slots)
 // MODE 3: hash table in global memory sized per w (fallback)
+// MODE 4: dense 16-bit counters + a two-level spill table: a shared first
+//         level of 2^sbits slots (keys kept within TWO_WINDOW probes), the
+//         block's global table sized per w for the keys that find no room
 // ---------------------------------------------------------------------------
 constexpr int CHUNK_MAX = 512;  // middles per chunk: min(block size, 512)
 constexpr int SHORT_LANES = 8;  // lanes per short segment
+constexpr int TWO_WINDOW = 16;  // probe window of the shared first level (MODE 4)
 
 // Segments at least long_seg long are cut into pieces of PIECE wedges, walked
 // warp-per-piece (coalesced, one owner per piece), so one long segment is
@@ -502,9 +541,10 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
                                                   const int32_t* __restrict__ cnt, int* next, u64* r12r, int64_t n,
                                                   const int64_t* __restrict__ wcn, int32_t hub_lo, int tbits,
                                                   int dense_words, int long_seg, uint32_t* gkeys, uint32_t* gtouch,
-                                                  uint32_t* gcnt, int64_t cap_bound, int* err) {
+                                                  uint32_t* gcnt, int64_t cap_bound, int sbits, int* err) {
   constexpr bool DENSE = MODE == 1 || MODE == 4;
   constexpr bool GMEM = MODE == 3 || MODE == 4;
+  constexpr bool TWO = MODE == 4;
   constexpr int CH = BT < CHUNK_MAX ? BT : CHUNK_MAX;
   constexpr int PIECE = MODE == 0 ? 256 : (MODE == 4 ? 2048 : 512);
   extern __shared__ __align__(16) unsigned char smem[];
@@ -537,6 +577,11 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
     T.keys = hbase;
     T.cnts = hbase + (1 << tbits);
   }
+  Table<false> T1;  // MODE 4: the shared first level of the spill table
+  if (TWO) {
+    T1.keys = hbase;
+    T1.cnts = hbase + (1 << sbits);
+  }
   const int tid = threadIdx.x;
   const int total = *cnt;
   const int hub_n = DENSE ? (int)(n - hub_lo) : 0;
@@ -554,6 +599,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
   // reads (for a global table: the slots listed as claimed), so each vertex
   // finds them empty again.
   for (uint32_t i = tid; i < (1u << tbits); i += blockDim.x) T.clear(i);
+  for (uint32_t i = tid; TWO && i < (1u << sbits); i += blockDim.x) T1.clear(i);
   if (tid == 0) s_ntouched = 0;
   if (DENSE)
     for (int i = tid; i < (hub_n + 1) >> 1; i += blockDim.x) dense[i] = 0u;
@@ -580,10 +626,16 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
     const bool single = M.K <= CH;
     auto count = [&](uint32_t u) {
       if (DENSE && (int32_t)u >= hub_lo) dense_add(u);
-      else T.increment(u, hb, err);
+      else if (!TWO || !T1.increment_window(u, sbits, TWO_WINDOW)) T.increment(u, hb, err);
     };
     auto credit = [&](uint32_t u) -> u64 {
-      const uint32_t c = (DENSE && (int32_t)u >= hub_lo) ? dense_get(u) : T.count_of(u, hb);
+      uint32_t c;
+      if (DENSE && (int32_t)u >= hub_lo) {
+        c = dense_get(u);
+      } else {
+        const int c1 = TWO ? T1.count_in_window(u, sbits, TWO_WINDOW) : -1;
+        c = c1 >= 0 ? (uint32_t)c1 : T.count_of(u, hb);
+      }
       return c > 1 ? (u64)(c - 1) : 0;
     };
     // Pass A: count the wedges per top u.
@@ -630,6 +682,20 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
             }
           }
           dense[i] = 0u;
+        }
+      }
+    }
+    if (TWO) {
+      for (uint32_t i = tid; i < (1u << sbits); i += blockDim.x) {
+        const uint32_t key = T1.load_key(i);
+        if (key != EMPTY_KEY) {
+          const u64 c = T1.load_cnt(i);
+          if (c >= 2) {
+            const u64 v = c * (c - 1) / 2;
+            atomicAdd(&r12r[key], v);
+            accw += v;
+          }
+          T1.clear(i);
         }
       }
     }
@@ -794,22 +860,25 @@ size_t block_smem(int mode, int bt, int tbits, int dense_words) {  // tbits: tab
   const size_t seg = seg_bytes(bt < CHUNK_MAX ? bt : CHUNK_MAX);
   if (mode == 0) return seg + ((size_t)8 << tbits);
   if (mode == 1) return seg + (size_t)dense_words * 4 + ((size_t)8 << tbits);
-  if (mode == 4) return seg + (size_t)dense_words * 4;
   return seg;
+}
+
+size_t block_smem_two(int bt, int sbits, int dense_words) {  // MODE 4: dense window + shared first level
+  return seg_bytes(bt < CHUNK_MAX ? bt : CHUNK_MAX) + (size_t)dense_words * 4 + ((size_t)8 << sbits);
 }
 
 int gmem_blocks() { return num_sms(); }
 
 template <int MODE, int BT>
 void launch_block(const CycArgs& a, int cls, int tbits, int dense_words, cudaStream_t st) {
-  const size_t smem = block_smem(MODE, BT, tbits, dense_words);
+  const size_t smem = MODE == 4 ? block_smem_two(BT, a.spill_bits, dense_words) : block_smem(MODE, BT, tbits, dense_words);
   allow_max_smem(k_cyc_block<MODE, BT>);
   // global-table modes: one table per block, cyc_gmem_blocks() tables
   const int grid = MODE >= 3 ? gmem_blocks() : num_sms() * occupancy((const void*)k_cyc_block<MODE, BT>, BT, smem);
   k_cyc_block<MODE, BT><<<grid, BT, smem, st>>>(a.orp, a.ocol, a.irp, a.iin, a.wc, a.lists + cls * a.list_stride,
                                                 a.counts + cls, a.next + cls, a.r12r, a.n, a.wcn, a.hub_lo, tbits,
                                                 dense_words, a.long_seg, a.gkeys, a.gtouch, a.gcnt, a.cap_bound,
-                                                a.err);
+                                                a.spill_bits, a.err);
   note_launch();
 }
 
