@@ -466,8 +466,8 @@ __device__ __forceinline__ void build_chunk(const Segs& S, const Mids& M, int64_
 // (S.misc[2]); the piece's segment is the last one whose piece prefix is at
 // most the piece index (a two-level ballot search over at most 2^10
 // prefixes). Lanes stride over the piece (coalesced, four loads in flight).
-// g(u) per wedge; done(rv, lane_sum) after each piece with the warp's sum of
-// g's return values.
+// g(u) per wedge; done(rv, lane_sum, len) after each piece of len wedges,
+// lane_sum the lane's 32-bit sum of g's return values (the caller reduces).
 template <int PIECE, typename G, typename D>
 __device__ __forceinline__ void walk_long(const Segs& S, const int32_t* __restrict__ ocol, G g, D done) {
   const int lane = threadIdx.x & 31;
@@ -486,7 +486,7 @@ __device__ __forceinline__ void walk_long(const Segs& S, const int32_t* __restri
     const int off = (i - S.lpp[sg]) * PIECE;
     const int32_t* p = ocol + S.lst[sg] + off;
     const int len = min(PIECE, S.llen[sg] - off);
-    u64 sum = 0;
+    uint32_t sum = 0;
     for (int q = lane; q < len; q += 128) {
       uint32_t x[4];
 #pragma unroll
@@ -495,14 +495,15 @@ __device__ __forceinline__ void walk_long(const Segs& S, const int32_t* __restri
       for (int r = 0; r < 4; ++r)
         if (q + 32 * r < len) sum += g(x[r]);
     }
-    done(S.lrv[sg], sum);
+    done(S.lrv[sg], sum, len);
   }
 }
 
 // Short segments: groups of SG lanes take them one at a time from the
 // chunk's queue (S.misc[3]); a group's lanes stride over one segment, two
-// list loads in flight per lane. g(u) per wedge; with SUM, done(j, s) is
-// called by the group's first lane with the group's sum s of g over segment j.
+// list loads in flight per lane. g(u) per wedge; with SUM, done(j, s, len) is
+// called by the group's first lane with the group's 32-bit sum s of g over
+// segment j of len wedges.
 template <int SG, bool SUM, typename G, typename D>
 __device__ __forceinline__ void walk_short(const Segs& S, const int32_t* __restrict__ ocol, G g, D done) {
   const int lane = threadIdx.x & 31, gl = lane % SG;
@@ -515,7 +516,7 @@ __device__ __forceinline__ void walk_short(const Segs& S, const int32_t* __restr
     if (j >= ns) break;
     const int32_t* p = ocol + S.st[j];
     const int len = S.pre[j + 1] - S.pre[j];
-    u64 sum = 0;
+    uint32_t sum = 0;
     for (int k = gl; k < len; k += 2 * SG) {
       const uint32_t u0 = (uint32_t)__ldg(p + k);
       const uint32_t u1 = k + SG < len ? (uint32_t)__ldg(p + k + SG) : 0u;
@@ -525,7 +526,7 @@ __device__ __forceinline__ void walk_short(const Segs& S, const int32_t* __restr
     if (SUM) {
 #pragma unroll
       for (int o = SG / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(gmask, sum, o, SG);
-      if (gl == 0) done(j, sum);
+      if (gl == 0) done(j, sum, len);
     }
   }
 }
@@ -628,21 +629,22 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
       if (DENSE && (int32_t)u >= hub_lo) dense_add(u);
       else if (!TWO || !T1.increment_window(u, sbits, TWO_WINDOW)) T.increment(u, hb, err);
     };
-    auto credit = [&](uint32_t u) -> u64 {
-      uint32_t c;
-      if (DENSE && (int32_t)u >= hub_lo) {
-        c = dense_get(u);
-      } else {
-        const int c1 = TWO ? T1.count_in_window(u, sbits, TWO_WINDOW) : -1;
-        c = c1 >= 0 ? (uint32_t)c1 : T.count_of(u, hb);
-      }
-      return c > 1 ? (u64)(c - 1) : 0;
+    // Every top of a middle's segment was counted in pass A, so cnt[u] >= 1
+    // and the credits cnt[u] - 1 of a segment sum to sum(cnt) - (its wedges).
+    // The sums stay below 2^30: a piece or short segment has at most 512
+    // wedges (2048 in the spill class, whose counts are below 2^16) and a
+    // count never exceeds the degree of w (below 2^21).
+    auto credit = [&](uint32_t u) -> uint32_t {
+      if (DENSE && (int32_t)u >= hub_lo) return dense_get(u);
+      const int c1 = TWO ? T1.count_in_window(u, sbits, TWO_WINDOW) : -1;
+      return c1 >= 0 ? (uint32_t)c1 : T.count_of(u, hb);
     };
     // Pass A: count the wedges per top u.
     for (int64_t c0 = 0; c0 < M.K; c0 += CH) {
       build_chunk<PIECE>(S, M, c0, n, CH, long_seg);
-      walk_long<PIECE>(S, ocol, [&](uint32_t u) -> u64 { count(u); return 0; }, [](int32_t, u64) {});
-      walk_short<SHORT_LANES, false>(S, ocol, [&](uint32_t u) -> u64 { count(u); return 0; }, [](int, u64) {});
+      walk_long<PIECE>(S, ocol, [&](uint32_t u) -> uint32_t { count(u); return 0u; }, [](int32_t, uint32_t, int) {});
+      walk_short<SHORT_LANES, false>(S, ocol, [&](uint32_t u) -> uint32_t { count(u); return 0u; },
+                                     [](int, uint32_t, int) {});
       __syncthreads();
     }
     // Pass B: each middle gains cnt[u] - 1 per wedge.
@@ -653,12 +655,13 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
         if (tid == 0) S.misc[2] = S.misc[3] = 0;
         __syncthreads();
       }
-      walk_long<PIECE>(S, ocol, credit, [&](int32_t rv, u64 sum) {
-        sum = warp_sum_u64(sum);
-        if ((tid & 31) == 0 && sum) atomicAdd(&r12r[rv], sum);
+      walk_long<PIECE>(S, ocol, credit, [&](int32_t rv, uint32_t sum, int len) {
+        const uint32_t v = (uint32_t)warp_sum_i32((int)sum) - (uint32_t)len;
+        if ((tid & 31) == 0 && v) atomicAdd(&r12r[rv], (u64)v);
       });
-      walk_short<SHORT_LANES, true>(S, ocol, credit, [&](int j, u64 sum) {
-        if (sum) S.acc[j] += sum;  // one group per segment
+      walk_short<SHORT_LANES, true>(S, ocol, credit, [&](int j, uint32_t sum, int len) {
+        const uint32_t v = sum - (uint32_t)len;
+        if (v) S.acc[j] += v;  // one group per segment
       });
       __syncthreads();
       const int ns = S.misc[0];
