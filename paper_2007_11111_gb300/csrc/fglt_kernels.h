@@ -176,9 +176,8 @@ struct CycArgs {
   int heavy_threads;      // block size of the dense and global classes
   int long_seg;           // block classes: segments at least this long are walked warp-per-segment
   int spill_bits;         // dense class: shared spill table of 2^spill_bits slots
-  int gbits;              // global tables: cyc_gmem_blocks() << gbits slots each array
-  uint32_t* gkeys;        // NULL when both global-table classes are empty
-  uint32_t* gcnt;
+  int gbits;              // global tables: cyc_gmem_blocks() << gbits slots each
+  uint32_t* gkeys;        // 2 words (key, count) per slot; NULL when both global-table classes are empty
   uint32_t* gtouch;       // cyc_gmem_blocks() << (gbits - 1) claimed-slot lists
   u64* r12r;
   int* err;

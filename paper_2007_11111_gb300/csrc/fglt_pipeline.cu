@@ -533,8 +533,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
       if (n_gmem > 0) {
         ca.gbits = bits_for((int64_t)gcap);
         const int64_t slots = (int64_t)cyc_gmem_blocks() << ca.gbits;
-        NEED(B_GKEYS, slots, ca.gkeys);
-        NEED(B_GCNT, slots, ca.gcnt);
+        NEED(B_GKEYS, 2 * slots, ca.gkeys);  // (key, count) per slot
         NEED(B_GTOUCH, slots / 2, ca.gtouch);
       }
       CK(launch_cyc(ca, st));

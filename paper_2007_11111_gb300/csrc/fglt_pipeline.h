@@ -24,7 +24,7 @@ namespace fglt {
 enum BufId {
   B_D, B_HEAVY, B_CNT, B_HIST, B_BASE, B_CURSOR, B_RANK, B_PERM, B_DR, B_OPC, B_ORP, B_SCAN, B_OCOL, B_OCUR,
   B_SORT, B_TWORK, B_C3O, B_C3R, B_K4R, B_R10R, B_R14R, B_R13R, B_R12R, B_C3OO, B_P2, B_P3, B_R7, B_R9, B_WC,
-  B_LS, B_WCN, B_GBM, B_GKEYS, B_GCNT, B_GTOUCH, B_HC, B_INDEG, B_IRP, B_ICUR, B_IIN, B_CTR64,
+  B_LS, B_WCN, B_GBM, B_GKEYS, B_GTOUCH, B_HC, B_INDEG, B_IRP, B_ICUR, B_IIN, B_CTR64,
   B_PIPELINE_COUNT
 };
 

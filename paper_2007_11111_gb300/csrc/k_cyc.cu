@@ -57,27 +57,33 @@ int num_sms() {
   return sms > 0 ? sms : 1;
 }
 
+// Hash table of (top, count). In shared memory keys and counts are two
+// arrays; in global memory slot h is one 8-byte word {keys[2h], keys[2h+1]},
+// so that a lookup reads key and count in one access.
 template <bool GMEM>
 struct Table {
   uint32_t* keys;
-  uint32_t* cnts;
+  uint32_t* cnts;  // shared tables only
   // global tables: the slots claimed since the last pass C (so that pass C
   // visits only those), with room for tcap entries
   uint32_t* touched = nullptr;
   int* ntouched = nullptr;
   int tcap = 0;
+  __device__ __forceinline__ uint32_t* key_at(uint32_t h) const { return GMEM ? keys + 2 * (size_t)h : keys + h; }
+  __device__ __forceinline__ uint32_t* cnt_at(uint32_t h) const {
+    return GMEM ? keys + 2 * (size_t)h + 1 : cnts + h;
+  }
   __device__ __forceinline__ uint32_t load_key(uint32_t h) const {
-    if (GMEM) return __ldcg(keys + h);
+    if (GMEM) return __ldcg(key_at(h));
     return *((volatile uint32_t*)keys + h);
   }
   __device__ __forceinline__ uint32_t load_cnt(uint32_t h) const {
-    if (GMEM) return __ldcg(cnts + h);
+    if (GMEM) return __ldcg(cnt_at(h));
     return cnts[h];
   }
   __device__ __forceinline__ void clear(uint32_t h) const {
     if (GMEM) {
-      __stcg(keys + h, EMPTY_KEY);
-      __stcg(cnts + h, 0u);
+      __stcg(reinterpret_cast<uint2*>(keys) + h, make_uint2(EMPTY_KEY, 0u));
     } else {
       keys[h] = EMPTY_KEY;
       cnts[h] = 0u;
@@ -89,7 +95,7 @@ struct Table {
     for (uint32_t probe = 0; probe <= mask; ++probe) {
       uint32_t k = load_key(h);
       if (k == EMPTY_KEY) {
-        k = atomicCAS(keys + h, EMPTY_KEY, key);
+        k = atomicCAS(key_at(h), EMPTY_KEY, key);
         if (k == EMPTY_KEY) {
           k = key;
           if (GMEM) {
@@ -100,7 +106,7 @@ struct Table {
         }
       }
       if (k == key) {
-        atomicAdd(cnts + h, 1u);
+        atomicAdd(cnt_at(h), 1u);
         return;
       }
       h = (h + 1) & mask;
@@ -146,9 +152,15 @@ struct Table {
     const uint32_t mask = (1u << hb) - 1;
     uint32_t h = hash_slot(key, hb);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
-      const uint32_t k = load_key(h);
-      if (k == key) return load_cnt(h);
-      if (k == EMPTY_KEY) return 0u;
+      if (GMEM) {
+        const uint2 e = __ldcg(reinterpret_cast<const uint2*>(keys) + h);
+        if (e.x == key) return e.y;
+        if (e.x == EMPTY_KEY) return 0u;
+      } else {
+        const uint32_t k = load_key(h);
+        if (k == key) return load_cnt(h);
+        if (k == EMPTY_KEY) return 0u;
+      }
       h = (h + 1) & mask;
     }
     return 0u;
@@ -542,7 +554,7 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
                                                   const int32_t* __restrict__ cnt, int* next, u64* r12r, int64_t n,
                                                   const int64_t* __restrict__ wcn, int32_t hub_lo, int tbits,
                                                   int dense_words, int long_seg, uint32_t* gkeys, uint32_t* gtouch,
-                                                  uint32_t* gcnt, int64_t cap_bound, int sbits, int* err) {
+                                                  int64_t cap_bound, int sbits, int* err) {
   constexpr bool DENSE = MODE == 1 || MODE == 4;
   constexpr bool GMEM = MODE == 3 || MODE == 4;
   constexpr bool TWO = MODE == 4;
@@ -569,8 +581,8 @@ __global__ void __launch_bounds__(BT) k_cyc_block(const int64_t* __restrict__ or
   __shared__ int s_ntouched;
   Table<GMEM> T;
   if (GMEM) {
-    T.keys = gkeys + ((size_t)blockIdx.x << tbits);
-    T.cnts = gcnt + ((size_t)blockIdx.x << tbits);
+    T.keys = gkeys + ((size_t)blockIdx.x << (tbits + 1));  // 2^tbits slots of 8 bytes
+    T.cnts = nullptr;
     T.touched = gtouch + ((size_t)blockIdx.x << (tbits - 1));
     T.ntouched = &s_ntouched;
     T.tcap = 1 << (tbits - 1);
@@ -880,7 +892,7 @@ void launch_block(const CycArgs& a, int cls, int tbits, int dense_words, cudaStr
   const int grid = MODE >= 3 ? gmem_blocks() : num_sms() * occupancy((const void*)k_cyc_block<MODE, BT>, BT, smem);
   k_cyc_block<MODE, BT><<<grid, BT, smem, st>>>(a.orp, a.ocol, a.irp, a.iin, a.wc, a.lists + cls * a.list_stride,
                                                 a.counts + cls, a.next + cls, a.r12r, a.n, a.wcn, a.hub_lo, tbits,
-                                                dense_words, a.long_seg, a.gkeys, a.gtouch, a.gcnt, a.cap_bound,
+                                                dense_words, a.long_seg, a.gkeys, a.gtouch, a.cap_bound,
                                                 a.spill_bits, a.err);
   note_launch();
 }
