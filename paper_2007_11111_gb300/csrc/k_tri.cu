@@ -94,21 +94,35 @@ __device__ __forceinline__ bool filter_test(const uint32_t* filt, uint32_t key, 
 
 // Scan of the sorted list ocol[bb, be) by a group of G lanes (gl = lane in
 // the group, gmask = the group's lanes) up to the first entry above last: PL
-// loads per lane in flight per step (G * PL entries), probe(c, k) for each
-// entry c = ocol[k] (entries past the end read as INT_MAX).
+// loads per lane per step (G * PL entries), probe(c, k) for each entry
+// c = ocol[k] (entries past the end read as INT_MAX). The next step's loads
+// are issued before the current step's probes, so two steps' loads are in
+// flight while the probes wait on shared memory.
 template <int PL, int G, typename P>
 __device__ __forceinline__ void scan_sorted(const int32_t* __restrict__ ocol, int64_t bb, int64_t be, int32_t last,
                                             int gl, unsigned gmask, P probe) {
-  for (int64_t k0 = bb; k0 < be; k0 += G * PL) {
-    int32_t c[PL];
+  if (bb >= be) return;
+  int32_t c[PL];
+#pragma unroll
+  for (int t = 0; t < PL; ++t) {
+    const int64_t k = bb + gl + G * t;
+    c[t] = k < be ? ocol[k] : 0x7fffffff;
+  }
+  for (int64_t k0 = bb;; k0 += G * PL) {
+    // the step after this one is needed unless the list ends or this step
+    // already passes last (the group's last entry decides, for all lanes)
+    const bool more = k0 + G * PL < be && __shfl_sync(gmask, c[PL - 1], G - 1, G) <= last;
+    int32_t nx[PL];
 #pragma unroll
     for (int t = 0; t < PL; ++t) {
-      const int64_t k = k0 + gl + G * t;
-      c[t] = k < be ? ocol[k] : 0x7fffffff;
+      const int64_t k = k0 + G * PL + gl + G * t;
+      nx[t] = more && k < be ? ocol[k] : 0x7fffffff;
     }
 #pragma unroll
     for (int t = 0; t < PL; ++t) probe(c[t], k0 + gl + G * t);
-    if (__shfl_sync(gmask, c[PL - 1], G - 1, G) > last) break;
+    if (!more) break;
+#pragma unroll
+    for (int t = 0; t < PL; ++t) c[t] = nx[t];
   }
 }
 
