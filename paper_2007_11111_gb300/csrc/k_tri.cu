@@ -214,23 +214,37 @@ __device__ __forceinline__ bool hub_cliques_tc(const uint32_t* __restrict__ bm, 
   const int nk = (D + TC_KC - 1) / TC_KC;
   const uint32_t sbase = tc::smem_addr(smem);
   // item i: operand row i / 4 (A rows, then B rows), word i % 4 of the chunk
-  auto load = [&](uint32_t (&v)[PER], int x0, int y0, int c) {
+  // This thread's items: operand rows (tid / 4) + 256 t, bitmap word tid % 4
+  // of each chunk. Per span, each item's bitmap row (null past D, or in the
+  // B rows of a second accumulator the span does not need) and its offset in
+  // a stage are fixed.
+  const int jw = tid & 3;
+  const uint32_t* src[PER];
+  uint32_t dst[PER];
+  auto setup = [&](int x0, int y0, bool hi_on) {
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
       const int i = tid + t * BT;
-      const int r = i >> 2, kw = c * (TC_KC / 32) + (i & 3);
-      const int row = r < TC_M ? x0 + r : y0 + (r - TC_M);
-      v[t] = (i < TC_ITEMS && row < D && kw < W) ? __ldcg(bm + (size_t)row * WS + kw) : 0u;
+      const int r = i >> 2;
+      const bool isA = r < TC_M;
+      const int rr = isA ? r : r - TC_M;
+      const int row = isA ? x0 + rr : y0 + rr;
+      const bool need = i < TC_ITEMS && (isA || hi_on || rr < TC_N);
+      src[t] = need && row < D ? bm + (size_t)row * WS + jw : nullptr;
+      dst[t] = need ? (uint32_t)((isA ? 0 : TC_A_BYTES) + (rr >> 3) * (8 * TC_KC) + (rr & 7) * 16 + jw * 256)
+                    : 0xFFFFFFFFu;
     }
+  };
+  auto load = [&](uint32_t (&v)[PER], int c) {
+    const int kw = c * (TC_KC / 32) + jw;
+#pragma unroll
+    for (int t = 0; t < PER; ++t) v[t] = (src[t] && kw < W) ? __ldcg(src[t] + c * (TC_KC / 32)) : 0u;
   };
   auto store = [&](const uint32_t (&v)[PER], unsigned char* stage) {
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
-      const int i = tid + t * BT;
-      if (i < TC_ITEMS) {
-        const int r = i >> 2, j = i & 3;
-        const int rr = r < TC_M ? r : r - TC_M;
-        unsigned char* op = stage + (r < TC_M ? 0 : TC_A_BYTES) + (rr >> 3) * (8 * TC_KC) + (rr & 7) * 16 + j * 256;
+      if (dst[t] != 0xFFFFFFFFu) {
+        unsigned char* op = stage + dst[t];
         expand16(v[t] & 0xFFFFu, reinterpret_cast<uint4*>(op));
         expand16(v[t] >> 16, reinterpret_cast<uint4*>(op + 128));
       }
@@ -238,16 +252,19 @@ __device__ __forceinline__ bool hub_cliques_tc(const uint32_t* __restrict__ bm, 
   };
   for (int x0 = 0; x0 < D; x0 += TC_M) {
     for (int y0 = x0; y0 < D; y0 += TC_SPAN) {
+      // the second accumulator (span rows 256..511) only while they reach into D
+      const bool hi_on = y0 + TC_N < D;
+      setup(x0, y0, hi_on);
       for (int c0 = 0; c0 < nk; c0 += TC_SEG_CHUNKS) {
         const int c1 = min(nk, c0 + TC_SEG_CHUNKS);
         uint32_t v[PER];
-        load(v, x0, y0, c0);
+        load(v, c0);
         for (int c = c0; c < c1; ++c, ++T.g) {
           const int s = T.g & 1;
           // the stage's previous chunk must be consumed before it is overwritten
           if (T.g >= 2 && !tc::mbar_wait(&T.bar[s], ((T.g - 2) >> 1) & 1u, TC_WAIT_NS)) *T.abort = 1;
           store(v, smem + s * TC_STAGE_BYTES);
-          if (c + 1 < c1) load(v, x0, y0, c + 1);
+          if (c + 1 < c1) load(v, c + 1);
           tc::fence_async_smem();
           __syncthreads();
           if (*T.abort) return false;
@@ -260,6 +277,7 @@ __device__ __forceinline__ bool hub_cliques_tc(const uint32_t* __restrict__ bm, 
               const uint64_t ad = tc::smem_desc(a0 + ks * 256, 128, 8 * TC_KC);
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
+                if (h == 1 && !hi_on) break;
                 const uint64_t bd = tc::smem_desc(b0 + h * (TC_N * TC_KC) + ks * 256, 128, 8 * TC_KC);
                 tc::mma_e4m3(T.tmem + h * TC_N, ad, bd, TC_IDESC, (c > c0 || ks > 0) ? 1u : 0u);
               }
@@ -274,9 +292,12 @@ __device__ __forceinline__ bool hub_cliques_tc(const uint32_t* __restrict__ bm, 
         const int q = warp & 3, cb = warp >> 2;
         const int x = x0 + 32 * q + lane;
         float kx = 0.f;
+        // column groups at or past D (and so every column of a second
+        // accumulator the span skipped) hold nothing to read
 #pragma unroll
         for (int hh = 0; hh < 4; ++hh) {
           const int col = cb * 64 + hh * 16;
+          if (y0 + col >= D) break;
           uint32_t r[16];
           tc::tmem_ld16(T.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, r);
           tc::tmem_ld_wait();
