@@ -336,11 +336,13 @@ __device__ __forceinline__ bool hub_cliques_tc(const uint32_t* __restrict__ bm, 
 // and a's own counts are the sums over x divided by 2 and 6.
 // ---------------------------------------------------------------------------
 // Shared-memory words of the region of the global-bitmap class that holds,
-// in turn, the probe tables of N+(a) (hash keys and values, filter) and the
-// two operand stages of the tensor-core clique phase; the clique tallies
-// follow it.
-__host__ __device__ __forceinline__ size_t hub_region_words(int Hbits, int fwords) {
-  const size_t table = 2 * ((size_t)1 << Hbits) + (size_t)fwords;
+// in turn, the probe tables of N+(a) (hash keys and values, filter) with one
+// row of scratch bits per lane group (the class scans with 32-lane groups:
+// one per warp of its 1024-thread blocks), and the two operand stages of the
+// tensor-core clique phase; the clique tallies follow it.
+constexpr int HUB_GROUPS_MAX = TRI_T_BIG / 32;
+__host__ __device__ __forceinline__ size_t hub_region_words(int Hbits, int fwords, int Wmax) {
+  const size_t table = 2 * ((size_t)1 << Hbits) + (size_t)fwords + (size_t)HUB_GROUPS_MAX * (size_t)Wmax;
   return table > (size_t)TC_REGION_WORDS ? table : (size_t)TC_REGION_WORDS;
 }
 
@@ -351,6 +353,7 @@ __global__ void __launch_bounds__(BT)
     k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol, const int32_t* __restrict__ work,
            const int32_t* __restrict__ nwork, int* next, int Dmax, int Hbits, int hf, int32_t* C3o, u64* c3r,
            u64* k4r, uint32_t* gbm, u64* work_ctr, int* err) {
+  static_assert(SMEM_BM || G == 32, "the global-bitmap class keeps one scratch row per warp");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ u64 red[32];
@@ -372,12 +375,19 @@ __global__ void __launch_bounds__(BT)
     k2loc = bm + (size_t)Dmax * (Wmax + 1);
   } else {
     bm = gbm + (size_t)blockIdx.x * ((size_t)Dmax * (Wmax + 1));
-    k2loc = reinterpret_cast<uint32_t*>(smem) + hub_region_words(Hbits, FWmax);
+    k2loc = reinterpret_cast<uint32_t*>(smem) + hub_region_words(Hbits, FWmax, Wmax);
   }
   int32_t* ylist = SMEM_BM ? lists_base + warp * (TRI_YL + Wmax) : nullptr;
   int32_t* wlist = SMEM_BM ? ylist + TRI_YL : nullptr;
   const int total = *nwork;
   const unsigned below = (1u << lane) - 1u;
+
+  // Global-bitmap class: each lane group collects the row of its b in shared
+  // memory (the upper triangle of S: c after b), stores it to the bitmap in
+  // global memory once, and a transpose pass fills the lower triangle. The
+  // scratch rows are cleared per vertex (the clique phase's operand stages
+  // overwrite them) and after each use.
+  uint32_t* gscr = SMEM_BM ? nullptr : filt + FWmax;
 
   // Global-bitmap class with cliques: tensor memory for the accumulators and
   // the two stage barriers of the tensor-core clique phase.
@@ -421,7 +431,8 @@ __global__ void __launch_bounds__(BT)
     // bitmap rows at an odd stride of words: lanes reading different rows
     // at the same word offset hit different shared-memory banks
     const int WS = W | 1;
-    for (int i = tid; i < D * WS; i += blockDim.x) bm[i] = 0u;
+    for (int i = tid; SMEM_BM && i < D * WS; i += blockDim.x) bm[i] = 0u;  // global rows are stored whole
+    for (int i = tid; !SMEM_BM && i < HUB_GROUPS_MAX * W; i += blockDim.x) gscr[(i / W) * Wmax + i % W] = 0u;
     for (int i = tid; K4 && i < D; i += blockDim.x) k2loc[i] = 0u;
     __syncthreads();
     for (int x = tid; x < D; x += blockDim.x) {
@@ -440,22 +451,51 @@ __global__ void __launch_bounds__(BT)
       const int32_t b = ocol[base + ib];
       const int64_t bb = orp[b], be = orp[b + 1];
       uint32_t* row = bm + (size_t)ib * WS;
+      uint32_t* srow = SMEM_BM ? row : gscr + (size_t)grp.first * Wmax;
       auto probe = [&](int32_t c, int64_t k) {
         if (c <= lastA) {
           ++probes;
           if (filter_test(filt, (uint32_t)c, fb)) {
             const int ic = table_find(keys, vals, (uint32_t)c, hb);
             if (ic >= 0) {
-              atomicOr(&row[ic >> 5], 1u << (ic & 31));
-              atomicOr(&bm[(size_t)ic * WS + (ib >> 5)], 1u << (ib & 31));
+              atomicOr(&srow[ic >> 5], 1u << (ic & 31));
+              if (SMEM_BM) atomicOr(&bm[(size_t)ic * WS + (ib >> 5)], 1u << (ib & 31));
               atomicAdd(&C3o[k], 1);  // edge b -> c
             }
           }
         }
       };
       scan_sorted<PL, G>(ocol, bb, be, lastA, grp.gl, grp.mask, probe);
+      if (!SMEM_BM) {  // row ib (upper triangle) to global memory, scratch back to zero
+        __syncwarp(grp.mask);
+        for (int w = grp.gl; w < W; w += G) {
+          __stcg(row + w, srow[w]);
+          srow[w] = 0u;
+        }
+        __syncwarp(grp.mask);
+      }
     }
     __syncthreads();
+    if (!SMEM_BM) {
+      // Lower triangle: the 32 x 32 tile (J, I) of S is the transpose of the
+      // upper tile (I, J), J >= I; a diagonal tile is ORed with its transpose.
+      // Tile row r of (I, J) is lane r's word; ballot b gathers column b.
+      for (int t = warp; t < W * W; t += nwarps) {
+        const int I = t / W, J = t % W;
+        if (J < I) continue;
+        const int r0 = 32 * I + lane;
+        const uint32_t wv = r0 < D ? __ldcg(bm + (size_t)r0 * WS + J) : 0u;
+        uint32_t mine = 0u;
+#pragma unroll
+        for (int b2 = 0; b2 < 32; ++b2) {
+          const uint32_t col = __ballot_sync(0xffffffffu, (wv >> b2) & 1u);
+          if (lane == b2) mine = col;
+        }
+        const int r1 = 32 * J + lane;
+        if (r1 < D) __stcg(bm + (size_t)r1 * WS + I, I == J ? (wv | mine) : mine);
+      }
+      __syncthreads();
+    }
 
     // Per local vertex x: triangles through edge a-x (popc S_x). Per edge x-y
     // of G_a: t = |S_x ∩ S_y| triangles of G_a on that edge, added to both
@@ -1018,7 +1058,7 @@ size_t tri1_smem_impl(int D, bool smem_bm, int hf, int bt = TRI_T) {
   const int H = 1 << hash_bits_for(D, hf);
   const size_t W = (size_t)(D + 31) / 32;
   if (!smem_bm) {  // [probe tables | tensor-core operand stages][tallies]
-    const size_t words = hub_region_words(hash_bits_for(D, hf), host_filter_words(D)) + (size_t)D;
+    const size_t words = hub_region_words(hash_bits_for(D, hf), host_filter_words(D), (int)W) + (size_t)D;
     return (words * 4 + 15) & ~(size_t)15;
   }
   size_t bytes = (size_t)H * 8 + (size_t)host_filter_words(D) * 4;
@@ -1062,11 +1102,16 @@ int tri_grid_blocks() { return num_sms(); }
 // block size).
 template <bool SMEM_BM, bool K4, int BT>
 auto tri1_fn(int loads, int g) {
-  if (loads >= 4)
-    return g >= 32 ? k_tri1<SMEM_BM, K4, 4, 32, BT>
-                   : (g >= 16 ? k_tri1<SMEM_BM, K4, 4, 16, BT> : k_tri1<SMEM_BM, K4, 4, 8, BT>);
-  return g >= 32 ? k_tri1<SMEM_BM, K4, 2, 32, BT>
-                 : (g >= 16 ? k_tri1<SMEM_BM, K4, 2, 16, BT> : k_tri1<SMEM_BM, K4, 2, 8, BT>);
+  // the global-bitmap class scans with 32-lane groups (one scratch row per warp)
+  if constexpr (!SMEM_BM) {
+    return loads >= 4 ? k_tri1<SMEM_BM, K4, 4, 32, BT> : k_tri1<SMEM_BM, K4, 2, 32, BT>;
+  } else {
+    if (loads >= 4)
+      return g >= 32 ? k_tri1<SMEM_BM, K4, 4, 32, BT>
+                     : (g >= 16 ? k_tri1<SMEM_BM, K4, 4, 16, BT> : k_tri1<SMEM_BM, K4, 4, 8, BT>);
+    return g >= 32 ? k_tri1<SMEM_BM, K4, 2, 32, BT>
+                   : (g >= 16 ? k_tri1<SMEM_BM, K4, 2, 16, BT> : k_tri1<SMEM_BM, K4, 2, 8, BT>);
+  }
 }
 
 template <bool SMEM_BM, int BT>
