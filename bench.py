@@ -626,11 +626,12 @@ def roofline_of(stage_ms: dict, work: dict, workload: str) -> dict:
 LIMITERS = {
     ("rmat-s24-ef32", "cyc"): "shared-memory counter updates (pass A atomics, pass B gathers; loading the "
                               "wedges alone costs about a tenth of pass A, timed with work removed) and, in "
-                              "the class with the global spill table, DRAM re-reads of each bottom vertex's "
-                              "segments in pass B plus spill-table atomics (5.9 TB of DRAM traffic against "
-                              "3.1 TB of algorithmic bytes, a quarter of the copy peak)",
-    ("rmat-s24-ef32", "tri1"): "hash probes of the streamed out-lists; the clique phase of the largest class "
-                               "runs on the tensor cores (tcgen05, E4M3)",
+                              "the spill class, DRAM re-reads of each bottom vertex's segments in pass B "
+                              "plus spill-table atomics (5.2 TB of DRAM traffic against 3.1 TB of "
+                              "algorithmic bytes, a fifth of the copy peak)",
+    ("rmat-s24-ef32", "tri1"): "hash probes of the out-lists streamed from DRAM (3.0 TB at a fifth of the copy "
+                               "peak); the clique phase of the largest class runs on the tensor cores "
+                               "(tcgen05, E4M3)",
     ("rmat-s20-ef16", "cyc"): "shared-memory atomics and instruction issue; lists and tables stay in L2 "
                               "(DRAM traffic a few percent of the algorithmic bytes)",
 }
