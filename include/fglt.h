@@ -124,8 +124,8 @@ typedef struct {
      *   instead of a hash-table class (1 .. 4096; default 2048). */
     int cyc_dense_min;
     /* cyc_long_segment: in the block classes of the 4-cycle stage, a
-     *   middle's segment of tops at least this long is walked by one warp
-     *   (coalesced); shorter ones are concatenated and split evenly over the
+     *   middle's segment of tops at least this long is cut into pieces, each
+     *   walked by one warp (coalesced); shorter ones are walked by groups of 8
      *   lanes (2 .. 512; default 32). */
     int cyc_long_segment;
     /* cyc_spill_bits: the dense-window class keeps the tops outside its window
@@ -154,6 +154,12 @@ typedef struct {
      *   tail of N+(a) after b scanned for every in-entry a of b: at most
      *   sum_a binom(d+(a), 2) entries), 0 = the default, 2. */
     int tri_pass2_from;
+    /* device_wait_limit_ns: limit of each bounded wait of a kernel on the
+     *   completion of its tensor-core work (0 selects 2 s; 1 gives up after
+     *   the first unsuccessful test, which exercises the error path). A wait
+     *   that runs out ends the kernel's work cleanly, and the call returns
+     *   FGLT_ERR_TIMEOUT; its outputs are then unspecified. */
+    long long device_wait_limit_ns;
 } fglt_options;
 
 /* dictionary_mask of Sigma5 = {sigma_0 .. sigma_4}. */

@@ -76,6 +76,7 @@ class fglt_options(ctypes.Structure):
         ("dictionary_mask", ctypes.c_uint),
         ("batch_small_max", ctypes.c_int),
         ("tri_pass2_from", ctypes.c_int),
+        ("device_wait_limit_ns", ctypes.c_longlong),
     ]
 
     def tuning(self) -> dict:
@@ -342,7 +343,8 @@ class Handle:
                  cyc_mid_threads=(0, 0, 0), cyc_heavy_threads: int = 0, dictionary: int = 0,
                  tri_probe_loads: int = 0, tri_hash_factor: int = 0, cyc_dense_min: int = 0,
                  tri_group_lanes: int = 0, cyc_long_segment: int = 0, tri_warp_max: int = 0,
-                 cyc_spill_bits: int = 0, batch_small_max: int = 0, tri_pass2_from: int = 0):
+                 cyc_spill_bits: int = 0, batch_small_max: int = 0, tri_pass2_from: int = 0,
+                 device_wait_limit_ns: int = 0):
         """dictionary: sub-dictionary bit mask (0 = Sigma16; DICT_SIGMA5 = Sigma5)."""
         opt = fglt_options_default()
         opt.dictionary_mask = int(dictionary)
@@ -362,6 +364,7 @@ class Handle:
         opt.cyc_spill_bits = int(cyc_spill_bits)
         opt.batch_small_max = int(batch_small_max)
         opt.tri_pass2_from = int(tri_pass2_from)
+        opt.device_wait_limit_ns = int(device_wait_limit_ns)
         opt.validate = int(validate)
         opt.profile_stages = int(profile_stages)
         opt.serve_memory_budget = int(serve_memory_budget)

@@ -139,6 +139,7 @@ fglt_status run_on_handle(fglt_t h, const Csr& g, int64_t* out_raw, int64_t* out
   ro.tuning = tuning ? *tuning : h->tuning;
   ro.validate = h->opt.validate != 0;
   ro.dict_mask = h->opt.dictionary_mask;
+  ro.wait_ns = h->opt.device_wait_limit_ns;
   ro.bounds = b;
   ro.capturing = capturing;
   const bool prof = (h->opt.profile_stages != 0 || force_profile) && !capturing;
@@ -460,6 +461,7 @@ fglt_status batched_small(fglt_t h, const void* rowptr, int rp64, const int32_t*
   h->work_valid = false;
   h->stages_valid = false;
   if (e & (ERR_BAD_GRAPH | ERR_BAD_ROWPTR)) return FGLT_ERR_INVALID_GRAPH;
+  if (e & ERR_TIMEOUT) return FGLT_ERR_TIMEOUT;
   return e ? FGLT_ERR_INTERNAL : FGLT_OK;
 }
 
@@ -496,6 +498,7 @@ fglt_status fglt_create(fglt_t* out, const fglt_options* opt, int device) {
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FGLT_ERR_INVALID_ARG;
   Tuning tu;
+  if (opt && opt->device_wait_limit_ns < 0) return FGLT_ERR_INVALID_ARG;
   if (opt) {
     fglt_status ts = tuning_from_options(*opt, &tu);
     if (ts != FGLT_OK) return ts;
@@ -661,6 +664,7 @@ fglt_status fglt_transform_batched(fglt_t h, const void* rowptr, int rowptr_is_6
     h->work_valid = false;
     h->stages_valid = false;
     if (e & (ERR_BAD_GRAPH | ERR_BAD_ROWPTR)) return finish(FGLT_ERR_INVALID_GRAPH);
+    if (e & ERR_TIMEOUT) return finish(FGLT_ERR_TIMEOUT);
     return finish(e ? FGLT_ERR_INTERNAL : FGLT_OK);
   }
   s = run_on_handle(h, g, out_raw, out_net, cs, &b, false);

@@ -96,7 +96,7 @@ int tri_grid_blocks();
 cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm,
                         u64* work_ctr, int* err, cudaStream_t st, bool cliques = true, int loads = 2, int hf = 2,
-                        int group = 32);
+                        int group = 32, long long wait_ns = 0);
 size_t tri1_gbm_bytes(int dpmax, int hf = 2);
 // The same two passes for vertices of out-degree at most tri_warp_max(): one
 // warp per vertex, everything in shared memory.

@@ -394,7 +394,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
       else
         CK(launch_tri1(orp, ocol, twork + c * n, cnt + C_NTRI0 + c, cnt + C_NEXT1_0 + c, tri_cap[c], C3o, c3r, k4r,
                        tri1_gbm_bytes(tri_cap[c], tri_hf[c]) ? gbm : nullptr, ctr + W_PROBES, err, st, need_k4,
-                       tu.tri_loads, tri_hf[c], tu.tri_group));
+                       tu.tri_loads, tri_hf[c], tu.tri_group, ro.wait_ns));
       sub(CYC_CLASSES + c, 1);
     }
 

@@ -92,6 +92,7 @@ struct RunOptions {
   cudaEvent_t* sub_events = nullptr;    // 2 * NUM_SUB events (start, stop per sub-stage), or NULL
   bool* sub_recorded = nullptr;         // NUM_SUB flags set for the sub-stages that ran
   int64_t* work = nullptr;              // O_NUM counters out, or NULL
+  long long wait_ns = 0;                // limit of a bounded device wait (0 = the kernels' default)
 };
 
 // Index of the device error word in the B_CNT buffer (any set bit is a

@@ -164,16 +164,17 @@ constexpr int TC_A_BYTES = TC_M * TC_KC, TC_B_BYTES = TC_SPAN * TC_KC;
 constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
 constexpr int TC_REGION_WORDS = 2 * TC_STAGE_BYTES / 4;
 constexpr uint32_t TC_COLS = 512;                     // tensor-memory columns: two f32 accumulators of 256
-constexpr uint64_t TC_WAIT_NS = 2000000000ull;        // limit of one barrier wait (2 s)
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;        // default limit of one barrier wait (2 s)
 constexpr uint32_t TC_IDESC = tc::idesc_e4m3_f32(TC_M, TC_N);
 constexpr int TC_SEG_CHUNKS = 4096 / TC_KC;            // K chunks per accumulator read-out
 constexpr int TC_ITEMS = (TC_M + TC_SPAN) * (TC_KC / 32);  // (operand row, bitmap word) pairs per chunk
 
 struct TcState {
-  uint64_t* bar;  // [2] stage barriers (one phase per committed chunk)
-  uint32_t tmem;  // accumulator base address in tensor memory
-  uint32_t g;     // chunks committed by this block so far
-  int* abort;     // shared: a barrier wait ran out
+  uint64_t* bar;     // [2] stage barriers (one phase per committed chunk)
+  uint32_t tmem;     // accumulator base address in tensor memory
+  uint32_t g;        // chunks committed by this block so far
+  int* abort;        // shared: a barrier wait ran out
+  uint64_t wait_ns;  // limit of one barrier wait
 };
 
 // 16 bits of a bitmap row -> 16 bytes, bit b -> byte b (0 or 0x38 = 1.0 in E4M3).
@@ -262,7 +263,7 @@ __device__ __forceinline__ bool hub_cliques_tc(const uint32_t* __restrict__ bm, 
         for (int c = c0; c < c1; ++c, ++T.g) {
           const int s = T.g & 1;
           // the stage's previous chunk must be consumed before it is overwritten
-          if (T.g >= 2 && !tc::mbar_wait(&T.bar[s], ((T.g - 2) >> 1) & 1u, TC_WAIT_NS)) *T.abort = 1;
+          if (T.g >= 2 && !tc::mbar_wait(&T.bar[s], ((T.g - 2) >> 1) & 1u, T.wait_ns)) *T.abort = 1;
           store(v, smem + s * TC_STAGE_BYTES);
           if (c + 1 < c1) load(v, c + 1);
           tc::fence_async_smem();
@@ -287,7 +288,12 @@ __device__ __forceinline__ bool hub_cliques_tc(const uint32_t* __restrict__ bm, 
         }
         // the last commit completes after every MMA of the segment
         const uint32_t gl = T.g - 1;
-        if (!tc::mbar_wait(&T.bar[gl & 1], (gl >> 1) & 1u, TC_WAIT_NS)) *T.abort = 1;
+        // every thread leaves before reading the accumulators if any wait ran out
+        const bool done = tc::mbar_wait(&T.bar[gl & 1], (gl >> 1) & 1u, T.wait_ns);
+        if (__syncthreads_or(!done)) {
+          *T.abort = 1;
+          return false;
+        }
         tc::fence_after_sync();
         const int q = warp & 3, cb = warp >> 2;
         const int x = x0 + 32 * q + lane;
@@ -352,7 +358,7 @@ template <bool SMEM_BM, bool K4, int PL, int G, int BT>
 __global__ void __launch_bounds__(BT)
     k_tri1(const int64_t* __restrict__ orp, const int32_t* __restrict__ ocol, const int32_t* __restrict__ work,
            const int32_t* __restrict__ nwork, int* next, int Dmax, int Hbits, int hf, int32_t* C3o, u64* c3r,
-           u64* k4r, uint32_t* gbm, u64* work_ctr, int* err) {
+           u64* k4r, uint32_t* gbm, u64* work_ctr, int* err, uint64_t wait_ns) {
   static_assert(SMEM_BM || G == 32, "the global-bitmap class keeps one scratch row per warp");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(BT)
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
-  TcState T{s_bar, 0u, 0u, &s_abort};
+  TcState T{s_bar, 0u, 0u, &s_abort, wait_ns};
   if (TCP) {
     if (tid == 0) {
       tc::mbar_init(&s_bar[0], 1);
@@ -1159,7 +1165,7 @@ size_t tri1_gbm_bytes(int dpmax, int hf) {
 
 cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* work, const int32_t* nwork,
                         int* next, int dpmax, int32_t* C3o, u64* c3r, u64* k4r, uint32_t* gbm, u64* work_ctr,
-                        int* err, cudaStream_t st, bool cliques, int loads, int hf, int group) {
+                        int* err, cudaStream_t st, bool cliques, int loads, int hf, int group, long long wait_ns) {
   if (dpmax < 2) return cudaSuccess;
   const bool smem_bm = tri1_bitmap_fits_smem(dpmax, hf);
   const int bt = tri1_threads(dpmax, smem_bm, hf);
@@ -1173,7 +1179,7 @@ cudaError_t launch_tri1(const int64_t* orp, const int32_t* ocol, const int32_t* 
                      : (cliques ? tri1_fn<false, true, TRI_T_BIG>(loads, group)
                                 : tri1_fn<false, false, TRI_T_BIG>(loads, group));
   fn<<<grid, bt, smem, st>>>(orp, ocol, work, nwork, next, dpmax, hb, hf, C3o, c3r, k4r, smem_bm ? nullptr : gbm,
-                             work_ctr, err);
+                             work_ctr, err, wait_ns > 0 ? (uint64_t)wait_ns : TC_WAIT_NS);
   note_launch();
   return cudaGetLastError();
 }

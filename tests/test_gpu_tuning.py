@@ -81,7 +81,8 @@ def test_invalid_settings_rejected():
                 dict(cyc_hub_span=-1), dict(cyc_hub_span=90113), dict(tri_probe_loads=3),
                 dict(tri_hash_factor=3), dict(cyc_mid_threads=(64, 256, 256)), dict(cyc_dense_min=5000),
                 dict(tri_group_lanes=4), dict(cyc_long_segment=1), dict(tri_warp_max=33), dict(cyc_spill_bits=14),
-                dict(tri_warp_max=-2), dict(tri_pass2_from=3), dict(tri_pass2_from=-1)):
+                dict(tri_warp_max=-2), dict(tri_pass2_from=3), dict(tri_pass2_from=-1),
+                dict(device_wait_limit_ns=-1)):
         with pytest.raises(fg.FgltError) as e:
             fg.Handle(device=0, **bad)
         assert e.value.status == fg.FGLT_ERR_INVALID_ARG
@@ -164,3 +165,32 @@ def test_complete_multipartite_beyond_one_accumulator_segment():
     assert net[0, 4] == comb(k - 1, 2) * s ** 2
     assert net[0, 15] == comb(k - 1, 3) * s ** 3
     np.testing.assert_array_equal(raw, net @ oracle.u16().T)
+
+
+def test_device_wait_that_runs_out_returns_timeout():
+    """With a device wait limit of 1 (give up after the first unsuccessful
+    test), the global-bitmap triangle class's first wait on its tensor-core
+    work runs out (the MMAs were issued a moment before): the kernel leaves,
+    after waiting for its own MMAs and freeing its tensor memory, and the call
+    returns FGLT_ERR_TIMEOUT. The handle stays usable for a graph without that
+    class, and a handle with the default limit gets K_1200 exact."""
+    import paper_2007_11111_gb300 as fg
+    from math import comb
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    n = 1200
+    g = gg.complete(n)
+    small = gg.rmat(12, 16, seed=21)
+    want_small = oracle.fglt(small)
+    with fg.Handle(device=0, device_wait_limit_ns=1) as h:
+        with pytest.raises(fg.FgltError) as e:
+            _run(h, g)
+        assert e.value.status == fg.FGLT_ERR_TIMEOUT
+        raw, net = _run(h, small)  # out-degrees below the global-bitmap class: no tensor-core waits
+        np.testing.assert_array_equal(raw, want_small[0])
+        np.testing.assert_array_equal(net, want_small[1])
+    with fg.Handle(device=0) as h:
+        _, net = _run(h, g)
+    want = np.zeros(16, np.int64)
+    want[0], want[1], want[4], want[15] = 1, n - 1, comb(n - 1, 2), comb(n - 1, 3)
+    np.testing.assert_array_equal(net, np.tile(want, (n, 1)))
