@@ -767,7 +767,8 @@ def run_gpu(args, rank, world, local_rank):
             tl.append(time.perf_counter() - t0)
         e2e = {"value": g.m / statistics.mean(tl), "unit": UNIT,
                "h2d_bytes_per_step": int(prp.nbytes + pci.nbytes),
-               "d2h_bytes_per_step": int(hraw.nbytes + hnet.nbytes)}
+               "d2h_bytes_per_step": int(hraw.nbytes + hnet.nbytes),
+               "step_s": [round(t, 4) for t in tl]}
 
     if rank != 0:
         h.close()

@@ -188,7 +188,10 @@ const char* fglt_last_cuda_error(fglt_t handle);
  *   colidx          device pointer, rowptr[n] int32 entries (NULL allowed if no edges)
  *   n               number of vertices (0 allowed: nothing is written)
  *   out_raw/out_net device pointers to n*C int64 (C = 16 for Sigma16), or NULL to skip one
- *   stream          cudaStream_t to order the work on, or NULL for the handle's stream
+ *   stream          cudaStream_t to order the work on (cudaStreamLegacy for the legacy
+ *                   default stream), or NULL for the handle's stream, which is a
+ *                   non-blocking stream: work the caller queued elsewhere is not
+ *                   ordered before it
  * Computes Table I (raw) and Table II's inverse (net) for every vertex:
  * degrees and the SpMV chains of Sec. 3-4 (p1, p2, p3, d^7, d^9, d^10),
  * per-edge triangle counts C3 = A o A^2 (Lemma 2), the 4-cycle term c4 (Lemma

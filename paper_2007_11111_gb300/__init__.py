@@ -192,12 +192,30 @@ def _ptr(x) -> Optional[int]:
     raise TypeError(f"cannot take the address of {type(x)}")
 
 
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream as an explicit handle
+
+
 def _stream_ptr(stream) -> Optional[int]:
+    """None -> NULL (the library uses the handle's own stream); a torch.cuda.Stream
+    -> its handle, where torch's default stream (handle 0, the legacy default
+    stream) is passed as cudaStreamLegacy so that the library orders its work
+    after the caller's instead of taking NULL as "the handle's stream"."""
     if stream is None:
         return None
     if isinstance(stream, int):
         return stream
-    return stream.cuda_stream  # torch.cuda.Stream
+    s = stream.cuda_stream  # torch.cuda.Stream
+    return s if s != 0 else CUDA_STREAM_LEGACY
+
+
+def _torch_stream(stream, tensor):
+    """The stream a Handle method runs on: the caller's, else torch's current
+    stream on the tensor's device (so that work queued there on the inputs
+    comes first)."""
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream(tensor.device)
 
 
 # ---------------------------------------------------------------------------
@@ -397,7 +415,7 @@ class Handle:
         if out_net is None:
             out_net = torch.empty((n, self.cols), dtype=torch.int64, device=rowptr.device)
         rp64 = 1 if rowptr.dtype == torch.int64 else 0
-        fglt_transform(self.h, rowptr, rp64, colidx, n, out_raw, out_net, stream)
+        fglt_transform(self.h, rowptr, rp64, colidx, n, out_raw, out_net, _torch_stream(stream, rowptr))
         return out_raw, out_net
 
     def transform_host(self, rowptr: np.ndarray, colidx: np.ndarray, n: int):
@@ -420,7 +438,8 @@ class Handle:
         if out_net is None:
             out_net = torch.empty((n, self.cols), dtype=torch.int64, device=rowptr.device)
         rp64 = 1 if rowptr.dtype == torch.int64 else 0
-        fglt_transform_batched(self.h, rowptr, rp64, colidx, off, len(off) - 1, out_raw, out_net, stream)
+        fglt_transform_batched(self.h, rowptr, rp64, colidx, off, len(off) - 1, out_raw, out_net,
+                               _torch_stream(stream, rowptr))
         return out_raw, out_net
 
     def csr_from_edges(self, src, dst, n: int, stream=None):
@@ -430,7 +449,7 @@ class Handle:
         import torch
         rowptr = torch.empty(n + 1, dtype=torch.int64, device=src.device)
         colidx = torch.empty(max(2 * src.numel(), 1), dtype=torch.int32, device=src.device)
-        nnz = fglt_csr_from_edges(self.h, src, dst, src.numel(), n, rowptr, colidx, stream)
+        nnz = fglt_csr_from_edges(self.h, src, dst, src.numel(), n, rowptr, colidx, _torch_stream(stream, src))
         return rowptr, colidx[:nnz]
 
     def relabel_by_degree(self, rowptr, colidx, n: int, descending: bool = True, stream=None):
@@ -444,7 +463,7 @@ class Handle:
         out_ci = torch.empty(max(nnz, 1), dtype=torch.int32, device=rowptr.device)
         perm = torch.empty(max(n, 1), dtype=torch.int32, device=rowptr.device)
         fglt_csr_relabel_by_degree(self.h, rowptr, rp64, colidx, n, 1 if descending else 0, out_rp, out_ci, perm,
-                                   stream)
+                                   _torch_stream(stream, rowptr))
         return out_rp, out_ci[:nnz], perm[:n]
 
     def autotune(self, rowptr, colidx, n: int, reps: int = 1, stream=None):
@@ -452,7 +471,7 @@ class Handle:
         tuned ms, default ms). Later calls on this handle use the result."""
         import torch
         rp64 = 1 if rowptr.dtype == torch.int64 else 0
-        opt, tuned, default = fglt_autotune(self.h, rowptr, rp64, colidx, n, reps, stream)
+        opt, tuned, default = fglt_autotune(self.h, rowptr, rp64, colidx, n, reps, _torch_stream(stream, rowptr))
         return opt.tuning(), tuned, default
 
     def stage_times(self) -> dict:
