@@ -52,3 +52,26 @@ def test_status_strings():
 def test_options_default_zeroes():
     opt = fg.fglt_options_default()
     assert opt.validate == 0 and opt.profile_stages == 0 and opt.serve_memory_budget == 0
+
+
+def test_options_layout_matches_header(tmp_path):
+    """The ctypes mirror of fglt_options has the C struct's size and field
+    offsets (a small C program compiled against include/fglt.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [name for name, _ in fg.fglt_options._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fglt.h"', 'int main(void) {',
+             '  printf("%zu\\n", sizeof(fglt_options));']
+    lines += [f'  printf("%zu\\n", offsetof(fglt_options, {f}));' for f in fields]
+    lines += ['  return 0;', '}']
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(fg.fglt_options)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(fg.fglt_options, f).offset == off, f
