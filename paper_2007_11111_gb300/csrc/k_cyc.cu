@@ -34,8 +34,8 @@
 //  - or a global-memory hash table alone (fallback).
 // Wedges are walked cooperatively: in the warp class the segments of N+(v) of
 // many middles v are concatenated and split evenly over the lanes; in the block
-// classes long segments are walked one warp each and short ones one group of
-// lanes each.
+// classes long segments are cut into pieces walked one warp each and short ones
+// are walked by groups of lanes.
 #include "fglt_device.cuh"
 #include "fglt_kernels.h"
 
