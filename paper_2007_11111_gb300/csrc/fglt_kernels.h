@@ -174,7 +174,7 @@ struct CycArgs {
   int wbits;              // warp-class table slots (log2, at most cyc_warp_bits_max())
   int mid_threads[3];     // block sizes of the three hash-table classes (128 .. 1024)
   int heavy_threads;      // block size of the dense and global classes
-  int long_seg;           // block classes: segments at least this long are walked warp-per-segment
+  int long_seg;           // block classes: segments at least this long are cut into warp-walked pieces
   int spill_bits;         // dense class: shared spill table of 2^spill_bits slots
   int gbits;              // global tables: cyc_gmem_blocks() << gbits slots each
   uint32_t* gkeys;        // 2 words (key, count) per slot; NULL when both global-table classes are empty

@@ -427,9 +427,10 @@ __device__ __forceinline__ long long block_excl_scan(long long x, long long* scr
   return r;
 }
 
-// Segments of the middles c0 .. c0 + chunk of w: long ones listed for
-// warp-per-segment walks, short non-empty ones compacted with their wedge
-// prefix for the group walk (one packed block scan).
+// Segments of the middles c0 .. c0 + chunk of w: long ones listed with the
+// prefix sums of their pieces for the warp-per-piece walk, short non-empty
+// ones compacted with their wedge prefix for the group walk (one packed block
+// scan).
 template <int PIECE>
 __device__ __forceinline__ void build_chunk(const Segs& S, const Mids& M, int64_t c0, int64_t n, int chunk,
                                             int long_seg) {
