@@ -429,7 +429,7 @@ fglt_status run_pipeline(Workspace& ws, const Csr& in, int64_t* out_raw, int64_t
   const int64_t span = tu.cyc_hub_span > 0 ? tu.cyc_hub_span : (n > (1 << 22) ? 65536 : 32768);
   const int32_t hub_lo = (int32_t)std::max<int64_t>(0, n - span);
   int64_t *wc = nullptr, *wcn = nullptr, *irp = nullptr;
-  int32_t *hc, *indeg, *icur;
+  int32_t *hc = nullptr, *indeg = nullptr, *icur = nullptr;
   int2* iin = nullptr;
   // Pass 2 from the middle vertex unless the lowest is requested.
   const bool tri2_mid = tu.tri_pass2 != 1;

@@ -158,7 +158,7 @@ __global__ void k_rebase_pack(int64_t* __restrict__ rowptr, int32_t* __restrict_
 }
 
 // Runs one pack on a lane. Returns the status of the whole pack.
-fglt_status run_pack(Server* S, Lane* L, const std::vector<Request*>& pack) {
+fglt_status run_pack(Lane* L, const std::vector<Request*>& pack) {
   int64_t n = 0, nnz = 0;
   for (Request* r : pack) {
     n += r->n;
@@ -271,10 +271,10 @@ void lane_loop(Server* S, Lane* L) {
         S->cv_work.wait(lock);
       }
     }
-    fglt_status s = run_pack(S, L, pack);
+    fglt_status s = run_pack(L, pack);
     std::vector<fglt_status> each(pack.size(), s);
     if (s != FGLT_OK && pack.size() > 1) {
-      for (size_t i = 0; i < pack.size(); ++i) each[i] = run_pack(S, L, std::vector<Request*>{pack[i]});
+      for (size_t i = 0; i < pack.size(); ++i) each[i] = run_pack(L, std::vector<Request*>{pack[i]});
     }
     const auto now = clk::now();
     {
