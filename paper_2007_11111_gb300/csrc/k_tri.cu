@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(BT)
     // Triangles {a, b, c}: c in N+(b) ∩ N+(a); N+(b) is sorted, so the scan
     // stops at the first step beyond the largest element of N+(a).
     const int32_t lastA = ocol[base + D - 1];
-    u64 probes = 0;
+    uint32_t probes = 0;  // this vertex's scanned entries (32 bits: bounded by D times an out-degree)
     const Groups<G> grp(warp, nwarps, lane);
     for (int ib = grp.first; ib < D; ib += grp.stride) {
       const int32_t b = ocol[base + ib];
@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(BT)
     }
     const u64 tri_sum = block_sum(tri2x, red) / 2;
     const u64 k4_sum = block_sum(k4_6x, red) / 6;
-    const u64 probe_sum = block_sum(probes, red);
+    const u64 probe_sum = block_sum((u64)probes, red);
     if (tid == 0) {
       if (tri_sum) atomicAdd(&c3r[a], tri_sum);
       if (k4_sum) atomicAdd(&k4r[a], k4_sum);
@@ -793,12 +793,13 @@ __global__ void __launch_bounds__(TW_T) k_tri1_warp(const int64_t* __restrict__ 
     w.k2[lane] = 0u;
     __syncwarp();
     const int32_t lastA = __shfl_sync(0xffffffffu, x, D - 1);
+    uint32_t vprobes = 0;  // this vertex's scanned entries
     for (int ib = 0; ib < D; ++ib) {
       const int32_t b = __shfl_sync(0xffffffffu, x, ib);
       const int64_t bb = orp[b], be = orp[b + 1];
       auto probe = [&](int32_t c, int64_t k) {
         if (c <= lastA) {
-          ++probes;
+          ++vprobes;
           if (filter_test(w.filt, (uint32_t)c, TW_FBITS)) {
             const int ic = table_find(w.keys, w.vals, (uint32_t)c, hb);
             if (ic >= 0) {
@@ -811,6 +812,7 @@ __global__ void __launch_bounds__(TW_T) k_tri1_warp(const int64_t* __restrict__ 
       };
       scan_sorted<PL, 32>(ocol, bb, be, lastA, lane, 0xffffffffu, probe);
     }
+    probes += vprobes;
     __syncwarp();
     const uint32_t Sx = lane < D ? w.S[lane] : 0u;
     const int deg = __popc(Sx);
