@@ -1,13 +1,15 @@
 """R-MAT scale 24, edge factor 32 (n = 16.8 M, ~5.1e8 undirected edges, max degree
 ~6.7e5): the largest single-graph configuration, generated on the device and
 transformed in the benchmark's launch configuration. Every row is checked
-against identities that hold at any size; a sample of vertices whose
-neighbourhoods the oracle can afford is checked element by element."""
+against identities that hold at any size; the four largest hubs against the
+Table I columns that follow from their neighbourhoods alone; a sample of
+vertices whose neighbourhoods the oracle can afford element by element."""
 import numpy as np
 import pytest
 
 import graphgen as gg
 import oracle
+from conftest import TABLE1_LOCAL_COLUMNS, table1_local_terms
 
 pytestmark = pytest.mark.gpu
 
@@ -71,6 +73,15 @@ def test_rmat_s24_full_size_sampled():
     assert s[1] == dg.nnz and s[2] == 2 * s[3] and s[5] == s[6] and s[7] == 3 * s[8]
     assert s[10] == 2 * s[9] and s[9] == s[11] and s[13] == s[14]
     assert s[4] % 3 == 0 and s[12] % 4 == 0 and s[15] % 4 == 0
+    # the four largest hubs (degrees up to 6.7e5, beyond the oracle's reach):
+    # the raw columns that need only their neighbourhoods, from the
+    # definitions (plain torch operations on the CSR, independent of the library)
+    top = torch.topk(deg, 4).indices.tolist()
+    for v in top:
+        t = table1_local_terms(dg.rowptr, dg.colidx, v)
+        got = raw_d[v].cpu().numpy()
+        for c in TABLE1_LOCAL_COLUMNS:
+            assert got[c] == t[c], (v, c, int(got[c]), t[c])
     # sampled rows vs the oracle: vertices from every degree range whose
     # neighbourhoods the oracle can intersect within a bounded budget
     d, rc = _row_costs(dg)

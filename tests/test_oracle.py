@@ -365,3 +365,23 @@ def test_stored_hub_rows_are_consistent():
         assert raw[0] == 1 and raw[1] == deg[v]
         assert (net >= 0).all()
         np.testing.assert_array_equal(u @ net, raw)
+
+
+def test_table1_local_terms_match_the_oracle():
+    """The definition-based columns used for the largest hubs of the full-size
+    graph (tests/conftest.py) agree with the oracle's raw rows, on the hubs and
+    on low-degree vertices of a power-law graph and on small special graphs,
+    with a chunk size small enough that the gathers are split."""
+    torch = pytest.importorskip("torch")
+    from conftest import TABLE1_LOCAL_COLUMNS, table1_local_terms
+    for g in (gg.rmat(11, 16, seed=3), gg.complete(40), gg.star(30)):
+        deg = np.diff(g.rowptr)
+        verts = np.unique(np.concatenate([np.argsort(-deg, kind="stable")[:4], np.flatnonzero(deg == 1)[:2],
+                                          np.flatnonzero(deg == 0)[:1]]))
+        raw, _ = oracle.fglt(g, vertices=verts)
+        rp = torch.from_numpy(g.rowptr.astype(np.int64))
+        ci = torch.from_numpy(g.colidx.astype(np.int32))
+        for row, v in zip(raw, verts):
+            t = table1_local_terms(rp, ci, int(v), chunk=97)
+            for c in TABLE1_LOCAL_COLUMNS:
+                assert t[c] == row[c], (g.n, int(v), c, t[c], row[c])
