@@ -73,6 +73,19 @@ def test_rmat_s24_full_size_sampled():
     assert s[1] == dg.nnz and s[2] == 2 * s[3] and s[5] == s[6] and s[7] == 3 * s[8]
     assert s[10] == 2 * s[9] and s[9] == s[11] and s[13] == s[14]
     assert s[4] % 3 == 0 and s[12] % 4 == 0 and s[15] % 4 == 0
+    # per-row relations of the SpMV chains (Sec. 4.2), every row: d2 = A (p1 - 1),
+    # d7 = A C(p1 - 1, 2) from the degrees alone; d5 = A d2 - p1 (p1 - 1) - 2 d4
+    # and d9 = A d4 - 2 d4 between the output columns
+    rows = torch.repeat_interleave(torch.arange(dg.n, device=deg.device), deg)
+    nbr = dg.colidx.long()
+    def spmv(x):
+        return torch.zeros(dg.n, dtype=torch.int64, device=deg.device).index_add_(0, rows, x[nbr])
+    p1 = deg
+    assert torch.equal(raw_d[:, 2], spmv(p1 - 1))
+    assert torch.equal(raw_d[:, 7], spmv((p1 - 1) * (p1 - 2) // 2))
+    assert torch.equal(raw_d[:, 5], spmv(raw_d[:, 2]) - p1 * (p1 - 1) - 2 * raw_d[:, 4])
+    assert torch.equal(raw_d[:, 9], spmv(raw_d[:, 4]) - 2 * raw_d[:, 4])
+    del rows, nbr
     # the four largest hubs (degrees up to 6.7e5, beyond the oracle's reach):
     # the raw columns that need only their neighbourhoods, from the
     # definitions (plain torch operations on the CSR, independent of the library)
