@@ -385,3 +385,25 @@ def test_table1_local_terms_match_the_oracle():
             t = table1_local_terms(rp, ci, int(v), chunk=97)
             for c in TABLE1_LOCAL_COLUMNS:
                 assert t[c] == row[c], (g.n, int(v), c, t[c], row[c])
+
+
+def test_spmv_chain_relations_hold_on_the_oracle():
+    """The per-row relations the full-size GPU test checks on every row
+    (Sec. 4.2: d2 = A (p1 - 1), d7 = A C(p1 - 1, 2), d5 = A d2 - p1 (p1 - 1) - 2 d4,
+    d9 = A d4 - 2 d4) hold on the oracle's rows of power-law and random graphs."""
+    for g in (gg.rmat(10, 8, seed=1), gg.erdos_renyi(300, 6, seed=2), gg.barabasi_albert(400, 4, seed=3)):
+        raw, _ = oracle.fglt(g)
+        deg = np.diff(g.rowptr).astype(np.int64)
+        rows = np.repeat(np.arange(g.n), deg)
+        nbr = g.colidx.astype(np.int64)
+
+        def spmv(x):  # (A x)_i = sum of x over N(i)
+            out = np.zeros(g.n, dtype=np.int64)
+            np.add.at(out, rows, x[nbr])
+            return out
+
+        p1 = deg
+        np.testing.assert_array_equal(raw[:, 2], spmv(p1 - 1))
+        np.testing.assert_array_equal(raw[:, 7], spmv((p1 - 1) * (p1 - 2) // 2))
+        np.testing.assert_array_equal(raw[:, 5], spmv(raw[:, 2]) - p1 * (p1 - 1) - 2 * raw[:, 4])
+        np.testing.assert_array_equal(raw[:, 9], spmv(raw[:, 4]) - 2 * raw[:, 4])
